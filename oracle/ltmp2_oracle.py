@@ -1,0 +1,312 @@
+"""Plain FP64 CPU oracle: closed-shell Gamma-point MP2 with explicit sums over
+occupied (i, j) and virtual (a, b) orbitals.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module.  It shares no code with
+the CUDA path.
+
+What it computes (Schaefer, Ramberger, Kresse, "Quartic scaling MP2 for
+solids", arXiv:1611.06797):
+
+* Overlap densities, Eq. (SCHovrlp):  rho_mn(G) = <m| e^{-iGr} |n>, on the FFT
+  grid.  With phi_n(r_t) = Omega^{-1/2} sum_p c_n(p) e^{i G_p r_t} this is the
+  wrapped plane-wave convolution  sum_p conj(c_m(p)) c_n((G_p + G) mod grid).
+  Three independent routes are provided: that convolution (``_conv``), a numpy
+  FFT of the real-space product (``_fft``) and an explicit O(N_FFT^2) DFT
+  (``_dft``).
+* Two-electron integrals in reciprocal space, Eq. (SCH2EI):
+  <ij|ab> = (1/Omega) sum_{G in A} 4 pi / G^2  rho_ia(G) rho_jb(-G),
+  A = {G != 0 : G^2/2 <= E_cut^aux} (Sec. II A: the auxiliary cutoff).
+* Closed-shell MP2, Eq. (CanMP2) with the spin sums of Eqs. (MP2direct) and
+  (MP2exchange) done (sum_{ss'} -> 4, sum_s -> 2, prefactor 1/2):
+     E_d = 2 sum_ijab |<ij|ab>|^2 D(e_i + e_j - e_a - e_b)
+     E_x = - sum_ijab <ij|ab> <ab|ji> D(e_i + e_j - e_a - e_b)
+  with D(Delta) = 1/Delta (canonical) or, Eq. (SCHLT) / Eq. (LTMP2) with a
+  quadrature, D(Delta) = - sum_k w_k exp(Delta tau_k).
+  The pair energy e_ij is the (i, j) term of E_d + E_x; it is symmetric.
+
+Readings where the paper is silent (each is listed in the design notes):
+* the G = 0 Coulomb term is dropped (v(0) := 0);
+* integrals use the grid-discrete overlap densities (aliasing included);
+* the quadrature is an input; ``sinc_laplace_quadrature`` is this oracle's
+  own, simple, exponentially convergent rule for 1/x (trapezoid rule in
+  t = ln tau), used only by its tests.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable, Iterable, Optional, Sequence, Tuple
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class OracleSystem:
+    """Gamma-point, closed-shell mean-field input.
+
+    lattice (3,3) rows = cell vectors; grid (3,); miller (N_pw,3);
+    coeff (N_orb, N_pw) complex; eps (N_orb,) ascending; n_occ; ecut_aux (Ha).
+    """
+    lattice: np.ndarray
+    grid: np.ndarray
+    miller: np.ndarray
+    coeff: np.ndarray
+    eps: np.ndarray
+    n_occ: int
+    ecut_aux: float
+
+    @property
+    def omega(self) -> float:
+        return abs(float(np.linalg.det(self.lattice)))
+
+    @property
+    def recip(self) -> np.ndarray:
+        # rows b_k with a_i . b_k = 2 pi delta_ik
+        return 2.0 * math.pi * np.linalg.inv(self.lattice).T
+
+    @classmethod
+    def from_solid(cls, solid, ecut_aux: Optional[float] = None) -> "OracleSystem":
+        if ecut_aux is None:
+            ecut_aux = 2.0 * solid.ecut / 3.0   # "commonly 2/3 E_cut" (Sec. II A)
+        return cls(np.asarray(solid.lattice, float), np.asarray(solid.grid, int),
+                   np.asarray(solid.miller, int), np.asarray(solid.coeff, complex),
+                   np.asarray(solid.eps, float), int(solid.n_occ), float(ecut_aux))
+
+
+# ---------------------------------------------------------------------------
+# Auxiliary G set and Coulomb kernel (Sec. II A; Eq. SCH2EI; Eq. CoulombFourier)
+# ---------------------------------------------------------------------------
+def aux_set(sys: OracleSystem):
+    """A = {G != 0 : |G|^2 / 2 <= E_cut^aux} as integer indices, |G|^2 and v(G) = 4 pi / G^2."""
+    B = sys.recip
+    # bound the search box by the shortest reciprocal direction
+    gmax = math.sqrt(2.0 * sys.ecut_aux)
+    # |m_k| <= gmax * |a_k| / (2 pi)
+    lim = [int(math.floor(gmax * np.linalg.norm(sys.lattice[k]) / (2 * math.pi))) + 1
+           for k in range(3)]
+    rng = [np.arange(-l, l + 1) for l in lim]
+    m = np.stack(np.meshgrid(*rng, indexing="ij"), -1).reshape(-1, 3)
+    G = m @ B
+    g2 = (G ** 2).sum(1)
+    keep = (0.5 * g2 <= sys.ecut_aux) & (g2 > 0)
+    m, g2 = m[keep], g2[keep]
+    n = sys.grid
+    flat = _flat(m, n)
+    if len(np.unique(flat)) != len(flat):
+        raise ValueError("auxiliary sphere does not fit the FFT grid")
+    v = 4.0 * math.pi / g2
+    return m, g2, v
+
+
+def _flat(m: np.ndarray, grid: np.ndarray) -> np.ndarray:
+    """Flat index of (m mod grid) in C order (axis 0 slowest)."""
+    w = np.mod(m, grid)
+    return (w[:, 0] * grid[1] + w[:, 1]) * grid[2] + w[:, 2]
+
+
+def _neg_index(m: np.ndarray) -> np.ndarray:
+    """Position of -m in the list m."""
+    key = {tuple(r): k for k, r in enumerate(m.tolist())}
+    return np.array([key[(-r[0], -r[1], -r[2])] for r in m.tolist()])
+
+
+# ---------------------------------------------------------------------------
+# Overlap densities, Eq. (SCHovrlp), three independent routes
+# ---------------------------------------------------------------------------
+def overlap_densities_conv(sys: OracleSystem, left: Sequence[int], right: Sequence[int],
+                           gvec: np.ndarray) -> np.ndarray:
+    """rho[l, r, g] = sum_p conj(c_l(p)) c_r((G_p + G_g) mod grid): wrapped convolution."""
+    n = sys.grid
+    ngrid = int(np.prod(n))
+    cgrid = np.zeros((len(right), ngrid), dtype=np.complex128)
+    fp = _flat(sys.miller, n)
+    cgrid[:, fp] = sys.coeff[list(right)]
+    cl = np.conj(sys.coeff[list(left)])                       # (L, N_pw)
+    out = np.empty((len(left), len(right), len(gvec)), dtype=np.complex128)
+    for g, G in enumerate(gvec):
+        idx = _flat(sys.miller + G[None, :], n)               # (N_pw,)
+        shifted = cgrid[:, idx]                               # (R, N_pw)
+        out[:, :, g] = cl @ shifted.T
+    return out
+
+
+def _real_space(sys: OracleSystem, orbs: Sequence[int]) -> np.ndarray:
+    """u_n(r_t) = sum_p c_n(p) exp(i G_p r_t)  (= Omega^{1/2} phi_n), shape (len, n1, n2, n3)."""
+    n = tuple(int(x) for x in sys.grid)
+    grid = np.zeros((len(orbs),) + n, dtype=np.complex128)
+    w = np.mod(sys.miller, sys.grid)
+    grid[:, w[:, 0], w[:, 1], w[:, 2]] = sys.coeff[list(orbs)]
+    return np.fft.ifftn(grid, axes=(1, 2, 3)) * float(np.prod(n))
+
+
+def overlap_densities_fft(sys: OracleSystem, left: Sequence[int], right: Sequence[int],
+                          gvec: np.ndarray, chunk: int = 256) -> np.ndarray:
+    """rho[l, r, g] = (Omega/N) sum_t phi_l*(r_t) phi_r(r_t) e^{-i G r_t}  via numpy's FFT."""
+    n = sys.grid
+    N = float(np.prod(n))
+    ul = _real_space(sys, left)
+    w = np.mod(gvec, n)
+    out = np.empty((len(left), len(right), len(gvec)), dtype=np.complex128)
+    right = list(right)
+    for s in range(0, len(right), chunk):
+        ur = _real_space(sys, right[s:s + chunk])
+        for li in range(len(left)):
+            prod = np.conj(ul[li])[None] * ur
+            F = np.fft.fftn(prod, axes=(1, 2, 3)) / N
+            out[li, s:s + len(ur)] = F[:, w[:, 0], w[:, 1], w[:, 2]]
+    return out
+
+
+def overlap_densities_dft(sys: OracleSystem, left: Sequence[int], right: Sequence[int],
+                          gvec: np.ndarray) -> np.ndarray:
+    """Same quantity by an explicit real-space sum with exp(-i G r_t): O(N_FFT) per value, no FFT."""
+    n = sys.grid
+    t = np.stack(np.meshgrid(*[np.arange(k) for k in n], indexing="ij"), -1).reshape(-1, 3)
+    frac = t / n[None, :]                                      # r_t in lattice coordinates
+    # orbitals in real space by explicit plane-wave sums
+    ph = np.exp(2j * math.pi * (frac @ sys.miller.T))          # (N_FFT, N_pw)
+    ul = ph @ sys.coeff[list(left)].T                          # (N_FFT, L)
+    ur = ph @ sys.coeff[list(right)].T
+    eg = np.exp(-2j * math.pi * (frac @ gvec.T))               # (N_FFT, N_G)
+    N = float(np.prod(n))
+    prod = np.conj(ul)[:, :, None] * ur[:, None, :]            # (N_FFT, L, R)
+    return np.einsum("tlr,tg->lrg", prod, eg) / N
+
+
+# ---------------------------------------------------------------------------
+# Two-electron integrals, Eq. (SCH2EI)
+# ---------------------------------------------------------------------------
+def pair_integrals(rho_i: np.ndarray, rho_j_neg: np.ndarray, v: np.ndarray,
+                   omega: float) -> np.ndarray:
+    """K[a, b] = <ij|ab> = (1/Omega) sum_G v(G) rho_ia(G) rho_jb(-G).
+
+    rho_i[a, G] = rho_ia(G); rho_j_neg[b, G] = rho_jb(-G).
+    """
+    return (rho_i * (v / omega)[None, :]) @ rho_j_neg.T
+
+
+# ---------------------------------------------------------------------------
+# Energy denominators: canonical (Eq. CanMP2) and Laplace quadrature (Eq. SCHLT)
+# ---------------------------------------------------------------------------
+def canonical_denominator(delta: np.ndarray) -> np.ndarray:
+    return 1.0 / delta
+
+
+def laplace_denominator(tau: np.ndarray, w: np.ndarray) -> Callable[[np.ndarray], np.ndarray]:
+    """D(Delta) = - sum_k w_k exp(Delta tau_k)  (1/Delta = -int_0^inf exp(Delta tau) dtau)."""
+    tau = np.asarray(tau, float)
+    w = np.asarray(w, float)
+
+    def D(delta: np.ndarray) -> np.ndarray:
+        out = np.zeros_like(delta)
+        for tk, wk in zip(tau, w):
+            out -= wk * np.exp(delta * tk)
+        return out
+    return D
+
+
+def mp2_pair_energy(K: np.ndarray, eps_i: float, eps_j: float, eps_v: np.ndarray,
+                    D: Callable[[np.ndarray], np.ndarray]) -> Tuple[float, float, float]:
+    """(i, j) term of the closed-shell direct and exchange energies.
+
+    K[a, b] = <ij|ab>.  <ab|ij> = conj(<ij|ab>) and <ab|ji> = conj(<ij|ba>), so
+      e_d = 2 sum_ab |K_ab|^2 D_ab,    e_x = - sum_ab K_ab conj(K_ba) D_ab.
+    Returns (e_d, e_x, imaginary residue of e_x).
+    """
+    Dab = D(eps_i + eps_j - eps_v[:, None] - eps_v[None, :])
+    ed = 2.0 * float(np.sum((K.real ** 2 + K.imag ** 2) * Dab))
+    xsum = np.sum(K * np.conj(K.T) * Dab)
+    return ed, -float(xsum.real), float(xsum.imag)
+
+
+def mp2_energy(sys: OracleSystem, D: Callable[[np.ndarray], np.ndarray],
+               pairs: Optional[Iterable[Tuple[int, int]]] = None, method: str = "auto",
+               rho_cache: Optional[dict] = None):
+    """Closed-shell MP2 with explicit sums over i, j, a, b.
+
+    Returns dict with E_d, E_x, E, and e_d / e_x pair matrices (only the
+    requested ordered pairs are filled; NaN elsewhere).
+    """
+    no = sys.n_occ
+    virt = list(range(no, sys.coeff.shape[0]))
+    mG, _, v = aux_set(sys)
+    neg = _neg_index(mG)
+    if pairs is None:
+        pairs = [(i, j) for i in range(no) for j in range(no)]
+    pairs = list(pairs)
+    occ_needed = sorted({p for pr in pairs for p in pr})
+    if method == "auto":
+        method = "conv" if sys.coeff.shape[1] * len(mG) * len(virt) < 4e8 else "fft"
+    rho = {} if rho_cache is None else rho_cache
+    missing = [i for i in occ_needed if i not in rho]
+    if missing:
+        fn = {"conv": overlap_densities_conv, "fft": overlap_densities_fft,
+              "dft": overlap_densities_dft}[method]
+        r = fn(sys, missing, virt, mG)
+        for k, i in enumerate(missing):
+            rho[i] = r[k]
+    eps_v = sys.eps[no:]
+    ed = np.full((no, no), np.nan)
+    ex = np.full((no, no), np.nan)
+    exi = np.full((no, no), np.nan)
+    for (i, j) in pairs:
+        K = pair_integrals(rho[i], rho[j][:, neg], v, sys.omega)
+        d, x, xi = mp2_pair_energy(K, sys.eps[i], sys.eps[j], eps_v, D)
+        ed[i, j], ex[i, j], exi[i, j] = d, x, xi
+    full = len(pairs) == no * no
+    out = {"e_d": ed, "e_x": ex, "e_x_imag": exi}
+    if full:
+        out["E_d"] = float(np.sum(ed))
+        out["E_x"] = float(np.sum(ex))
+        out["E"] = out["E_d"] + out["E_x"]
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Quadrature for 1/x (the oracle's own; the paper cites a minimax grid, Sec. II C)
+# ---------------------------------------------------------------------------
+def denominator_range(sys: OracleSystem) -> Tuple[float, float]:
+    """[min, max] of -(e_i + e_j - e_a - e_b) over the system."""
+    no = sys.n_occ
+    lo = 2.0 * (sys.eps[no] - sys.eps[no - 1])
+    hi = 2.0 * (sys.eps[-1] - sys.eps[0])
+    return lo, hi
+
+
+def sinc_laplace_quadrature(n: int, xmin: float, xmax: float) -> Tuple[np.ndarray, np.ndarray]:
+    """Exponential-sum rule for 1/x on [xmin, xmax] (the oracle's own).
+
+    1/x = int_0^inf exp(-x tau) dtau = int_{-inf}^{inf} exp(-x e^t) e^t dt.  The
+    t-integrand is analytic in the strip |Im t| < pi/2, so the trapezoid rule with
+    step h has relative error ~ exp(-pi^2 / h).  The infinite sum is cut where
+    the dropped tails are of the same size: t_lo = ln(eps / xmax) (the left tail
+    contributes ~ x e^{t_lo}) and t_hi = ln(C / xmin) with exp(-C) = eps (the
+    right tail contributes ~ exp(-x e^{t_hi})).  n nodes then fix h by the
+    fixed point L(h) = n h.
+    """
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    R = xmax / xmin
+    h = 1.0
+    for _ in range(200):
+        C = math.pi ** 2 / h
+        L = math.log(C * R) + C
+        h_new = L / n
+        if abs(h_new - h) < 1e-14 * h:
+            break
+        h = 0.5 * (h + h_new)
+    C = math.pi ** 2 / h
+    t_lo = math.log(math.exp(-C) / xmax)
+    t = t_lo + h * (np.arange(n) + 0.5)
+    tau = np.exp(t)
+    w = h * tau
+    return tau, w
+
+
+def quadrature_max_error(tau: np.ndarray, w: np.ndarray, xmin: float, xmax: float,
+                         samples: int = 10000) -> float:
+    """max over log-spaced x in [xmin, xmax] of |1 - x sum_k w_k exp(-x tau_k)|."""
+    x = np.geomspace(xmin, xmax, samples)
+    s = np.exp(-np.outer(x, tau)) @ w
+    return float(np.max(np.abs(1.0 - x * s)))

@@ -1,0 +1,299 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+The paper prints no worked example, so every pin is a closed form, a brute-force
+recount, an identity or an invariant (Eqs. CanMP2, SCH2EI, SCHovrlp, SCHLT,
+SCHnewstate, SCHfocklike, dLTMP2Compact of arXiv:1611.06797).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import (OracleSystem, aux_set, canonical_denominator, denominator_range,
+                    laplace_denominator, mp2_energy, overlap_densities_conv,
+                    overlap_densities_dft, overlap_densities_fft, pair_integrals,
+                    quadrature_max_error, sinc_laplace_quadrature)
+from synth import SPECS, ModelSolidSpec, build_model_solid, free_electron_solid
+from tests.conftest import solid
+
+
+def _sys(s, **kw):
+    return OracleSystem.from_solid(s, **kw)
+
+
+# ---------------------------------------------------------------- overlap densities
+@pytest.mark.parametrize("phases", [False, True])
+def test_overlap_density_routes_agree(phases):
+    """Eq. SCHovrlp three ways: wrapped convolution, numpy FFT, explicit DFT sum."""
+    s = solid("tiny2", random_phases=phases)
+    o = _sys(s)
+    mG, _, _ = aux_set(o)
+    left = [0, 3]
+    right = list(range(s.n_occ, s.n_orb, 7))
+    a = overlap_densities_conv(o, left, right, mG)
+    b = overlap_densities_fft(o, left, right, mG)
+    c = overlap_densities_dft(o, left, right, mG)
+    scale = np.abs(a).max()
+    assert np.abs(a - b).max() < 1e-13 * max(1.0, scale)
+    assert np.abs(a - c).max() < 1e-12 * max(1.0, scale)
+
+
+def test_overlap_density_orthogonality_at_g0():
+    """rho_ia(0) = <i|a> = 0 for occupied/virtual pairs, = delta for i = a."""
+    s = solid("tiny2")
+    o = _sys(s)
+    g0 = np.zeros((1, 3), dtype=int)
+    r = overlap_densities_conv(o, range(s.n_occ), range(s.n_orb), g0)[:, :, 0]
+    assert np.abs(r - np.eye(s.n_occ, s.n_orb)).max() < 1e-12
+
+
+def test_integral_symmetries():
+    """<ij|ab> = <ji|ba> and <ab|ij> = conj(<ij|ab>) from independently indexed densities."""
+    s = solid("tiny2", random_phases=True)
+    o = _sys(s)
+    mG, _, v = aux_set(o)
+    key = {tuple(m): k for k, m in enumerate(mG.tolist())}
+    neg = np.array([key[tuple(-np.array(m))] for m in mG.tolist()])
+    occ = list(range(s.n_occ))
+    virt = list(range(s.n_occ, s.n_orb))
+    rho_ov = overlap_densities_conv(o, occ, virt, mG)          # rho_ia(G)
+    rho_vo = overlap_densities_conv(o, virt, occ, mG)          # rho_ai(G)
+    i, j = 0, 2
+    K_ij = pair_integrals(rho_ov[i], rho_ov[j][:, neg], v, o.omega)   # <ij|ab>
+    K_ji = pair_integrals(rho_ov[j], rho_ov[i][:, neg], v, o.omega)   # <ji|ab>
+    assert np.abs(K_ij - K_ji.T).max() < 1e-14
+    # <ab|ij> = (1/Omega) sum_G v(G) rho_ai(G) rho_bj(-G)
+    K_abij = (rho_vo[:, i, :] * (v / o.omega)[None]) @ rho_vo[:, j, neg].T
+    assert np.abs(K_abij - np.conj(K_ij)).max() < 1e-14
+
+
+# ---------------------------------------------------------------- free electrons
+def _box_aux(a, grid, ecut_aux):
+    """Brute-force aux set for a cubic cell, no use of the oracle."""
+    b = 2 * math.pi / a
+    R = int(math.sqrt(2 * ecut_aux) / b) + 1
+    out = []
+    for mx in range(-R, R + 1):
+        for my in range(-R, R + 1):
+            for mz in range(-R, R + 1):
+                g2 = (mx * mx + my * my + mz * mz) * b * b
+                if 0 < g2 and 0.5 * g2 <= ecut_aux:
+                    out.append(((mx, my, mz), g2))
+    return out
+
+
+def test_free_electron_one_orbital_closed_form():
+    """V = 0, N_o = 1: <00|ab> = v(k_a)/Omega delta_{k_b,-k_a}, so
+    E_d = -(32 pi^2 / Omega^2) sum_{G in A} 1/|G|^6 and E_x = -E_d / 2 (Eq. CanMP2)."""
+    a, grid, r2 = 5.5, 12, 9
+    s = free_electron_solid(a, grid, r2, n_occ=1)
+    o = _sys(s)
+    omega = a ** 3
+    A = _box_aux(a, grid, o.ecut_aux)
+    Ed_cf = -(32 * math.pi ** 2 / omega ** 2) * sum(1.0 / g2 ** 3 for _, g2 in A)
+    r = mp2_energy(o, canonical_denominator)
+    assert abs(r["E_d"] - Ed_cf) < 1e-12 * abs(Ed_cf)
+    assert abs(r["E_x"] + 0.5 * Ed_cf) < 1e-12 * abs(Ed_cf)
+    # Laplace mode has its own closed form: Delta = -|G|^2
+    tau, w = sinc_laplace_quadrature(6, *denominator_range(o))
+    Ed_lt = -2.0 * sum((4 * math.pi / g2 / omega) ** 2 * float(np.sum(w * np.exp(-g2 * tau)))
+                       for _, g2 in A)
+    rl = mp2_energy(o, laplace_denominator(tau, w))
+    assert abs(rl["E_d"] - Ed_lt) < 1e-12 * abs(Ed_lt)
+    assert abs(rl["E_x"] + 0.5 * Ed_lt) < 1e-12 * abs(Ed_lt)
+
+
+def test_free_electron_seven_orbitals_brute_force():
+    """Closed-shell HEG, occupied = k=0 plus the first shell (7 orbitals).
+
+    Independent O(N_o^2 N_v) recount with crystal-momentum conservation
+    k_i + k_j = k_a + k_b: <ij|ab> = v(k_a - k_i)/Omega when k_a - k_i is in A.
+    """
+    a, grid, r2 = 6.0, 16, 9
+    s = free_electron_solid(a, grid, r2, n_occ=7)
+    o = _sys(s)
+    b = 2 * math.pi / a
+    omega = a ** 3
+    ecut_aux = o.ecut_aux
+    m = s.miller[np.argmax(np.abs(s.coeff), axis=1)]           # k of each orbital
+    eps = s.eps
+    occ = [tuple(x) for x in m[:7]]
+    virt = [tuple(x) for x in m[7:]]
+    vset = {k: n for n, k in enumerate(virt)}
+
+    def v_of(g):
+        g2 = (g[0] ** 2 + g[1] ** 2 + g[2] ** 2) * b * b
+        return 4 * math.pi / g2 if (g2 > 0 and 0.5 * g2 <= ecut_aux) else 0.0
+
+    Ed = Ex = 0.0
+    for i, ki in enumerate(occ):
+        for j, kj in enumerate(occ):
+            for an, ka in enumerate(virt):
+                kb = (ki[0] + kj[0] - ka[0], ki[1] + kj[1] - ka[1], ki[2] + kj[2] - ka[2])
+                bn = vset.get(kb)
+                if bn is None:
+                    continue
+                g = (ka[0] - ki[0], ka[1] - ki[1], ka[2] - ki[2])
+                g2 = (kb[0] - kj[0], kb[1] - kj[1], kb[2] - kj[2])  # = -g
+                vij = v_of(g) / omega
+                vji = v_of((ka[0] - kj[0], ka[1] - kj[1], ka[2] - kj[2])) / omega
+                D = 1.0 / (eps[i] + eps[j] - eps[7 + an] - eps[7 + bn])
+                Ed += 2 * vij * vij * D
+                Ex += -vij * vji * D
+    r = mp2_energy(o, canonical_denominator)
+    assert abs(r["E_d"] - Ed) < 1e-11 * abs(Ed)
+    assert abs(r["E_x"] - Ex) < 1e-11 * abs(Ex)
+    assert Ex != 0.0
+
+
+def test_degenerate_virtual_rotation_invariance():
+    """A unitary rotation inside an exactly degenerate virtual shell leaves E unchanged."""
+    s = free_electron_solid(5.5, 12, 9, n_occ=7)
+    o = _sys(s)
+    E0 = mp2_energy(o, canonical_denominator)
+    eps = s.eps
+    # shell |m|^2 = 2 (12 degenerate plane waves)
+    shell = np.where(np.abs(eps - eps[7]) < 1e-12)[0]
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(len(shell),) * 2) + 1j * rng.normal(size=(len(shell),) * 2)
+    U, _ = np.linalg.qr(X)
+    c2 = s.coeff.copy()
+    c2[shell] = U.T @ s.coeff[shell]
+    o2 = OracleSystem(o.lattice, o.grid, o.miller, c2, o.eps, o.n_occ, o.ecut_aux)
+    E1 = mp2_energy(o2, canonical_denominator)
+    assert abs(E1["E"] - E0["E"]) < 1e-12 * abs(E0["E"])
+
+
+# ---------------------------------------------------------------- model solids
+def test_one_occupied_orbital_exchange_is_minus_half_direct():
+    spec = ModelSolidSpec("one", a=5.0, grid=8, r2=9, wells=1, n_occ=1, n_tau=6, seed=7)
+    s = build_model_solid(spec, random_phases=True)
+    o = _sys(s)
+    for D in (canonical_denominator,
+              laplace_denominator(*sinc_laplace_quadrature(8, *denominator_range(o)))):
+        r = mp2_energy(o, D)
+        assert r["E_d"] < 0
+        assert abs(r["E_x"] + 0.5 * r["E_d"]) < 1e-13 * abs(r["E_d"])
+
+
+@pytest.mark.parametrize("name", ["tiny", "tiny2"])
+def test_invariants(name):
+    """Random orbital phases, e_ij = e_ji, E_d <= 0, sum e_ij = E, real exchange."""
+    s0 = solid(name)
+    s1 = solid(name, random_phases=True)
+    r0 = mp2_energy(_sys(s0), canonical_denominator)
+    r1 = mp2_energy(_sys(s1), canonical_denominator)
+    assert abs(r0["E"] - r1["E"]) < 1e-12 * abs(r0["E"])
+    assert np.abs(r0["e_d"] - r1["e_d"]).max() < 1e-12
+    assert np.abs(r0["e_x"] - r1["e_x"]).max() < 1e-12
+    e = r1["e_d"] + r1["e_x"]
+    assert np.abs(e - e.T).max() < 1e-13
+    assert r1["E_d"] < 0 and np.all(np.diag(r1["e_d"]) < 0)
+    assert abs(e.sum() - r1["E"]) < 1e-13
+    assert np.abs(r1["e_x_imag"]).max() < 1e-13
+
+
+def test_laplace_quadrature_error_bound_and_convergence():
+    """Eq. SCHLT with a quadrature: delta(n) falls with n, and since every direct
+    numerator is >= 0, |E_d^LT - E_d| <= delta |E_d|; exchange obeys
+    |E_x^LT - E_x| <= delta sum |N_x| / |Delta|."""
+    s = solid("tiny2")
+    o = _sys(s)
+    lo, hi = denominator_range(o)
+    can = mp2_energy(o, canonical_denominator)
+    # sum |N_x| / |Delta| from the canonical pieces: recompute with |.| numerators
+    from oracle.ltmp2_oracle import _neg_index
+    mG, _, v = aux_set(o)
+    neg = _neg_index(mG)
+    virt = list(range(s.n_occ, s.n_orb))
+    rho = overlap_densities_conv(o, range(s.n_occ), virt, mG)
+    ev = s.eps[s.n_occ:]
+    xbound = 0.0
+    for i in range(s.n_occ):
+        for j in range(s.n_occ):
+            K = pair_integrals(rho[i], rho[j][:, neg], v, o.omega)
+            Dab = s.eps[i] + s.eps[j] - ev[:, None] - ev[None, :]
+            xbound += float(np.sum(np.abs(K * np.conj(K.T)) / np.abs(Dab)))
+    prev_delta, errs = None, []
+    for n in (4, 8, 12, 16, 24):
+        tau, w = sinc_laplace_quadrature(n, lo, hi)
+        delta = quadrature_max_error(tau, w, lo, hi, samples=20000)
+        lt = mp2_energy(o, laplace_denominator(tau, w))
+        assert abs(lt["E_d"] - can["E_d"]) <= delta * abs(can["E_d"]) * (1 + 1e-6) + 1e-15
+        assert abs(lt["E_x"] - can["E_x"]) <= delta * xbound * (1 + 1e-6) + 1e-15
+        if prev_delta is not None:
+            assert delta < prev_delta
+        prev_delta = delta
+        errs.append(abs(lt["E"] - can["E"]))
+    assert errs[-1] < 1e-3 * errs[0]
+
+
+def test_ltmp2_converges_to_canonical():
+    s = solid("cfg1")
+    o = _sys(s)
+    lo, hi = denominator_range(o)
+    can = mp2_energy(o, canonical_denominator)
+    errs = []
+    for n in (8, 16, 32, 48):
+        tau, w = sinc_laplace_quadrature(n, lo, hi)
+        errs.append(abs(mp2_energy(o, laplace_denominator(tau, w))["E"] - can["E"]))
+    assert errs[-1] < 1e-7
+    assert errs[-1] < errs[0] * 1e-3
+
+
+# ---------------------------------------------------------------- the working form
+def _working_form(o, tau, w, gp_subset=None):
+    """LTMP2 by transformed states (Eqs. SCHnewstate, SCHtransmatrix, SCHfocklike,
+    dLTMP2Compact at q = 0), written with plain numpy and no sum over virtuals
+    inside the final contraction:
+       M_ij(G;G') = sum_a rho_ia(G) rho_aj(G') e^{(e_j - e_a) tau}  = <i|e^{-iGr}|w_j^{G'}>
+       E_x = sum_k w_k / Omega^2 sum_{G,G'} v v sum_ij M_ij(G;G') M_ji(-G;-G')
+       E_d = -2 sum_k w_k / Omega^2 sum_{G,G'} v v sum_ij M_ii(G;G') M_jj(-G;-G')
+    """
+    from oracle.ltmp2_oracle import _neg_index
+    mG, _, v = aux_set(o)
+    neg = _neg_index(mG)
+    no = o.n_occ
+    virt = list(range(no, o.coeff.shape[0]))
+    rho_ov = overlap_densities_conv(o, range(no), virt, mG)   # [i, a, G]
+    rho_vo = overlap_densities_conv(o, virt, range(no), mG)   # [a, j, G']
+    ev = o.eps[no:]
+    eo = o.eps[:no]
+    gp = range(len(mG)) if gp_subset is None else gp_subset
+    Ex = Ed = 0.0
+    for tk, wk in zip(tau, w):
+        E = np.exp((eo[None, :] - ev[:, None]) * tk)           # [a, j]
+        for g in gp:
+            # M[i, j, G] for this G'
+            M = np.einsum("iaG,aj->ijG", rho_ov, rho_vo[:, :, g] * E)
+            Mn = np.einsum("iaG,aj->ijG", rho_ov, rho_vo[:, :, neg[g]] * E)
+            pref = wk * v[g] / o.omega ** 2
+            Ex += pref * np.einsum("G,ijG,jiG->", v, M, Mn[:, :, neg]).real
+            d = np.einsum("iiG->iG", M)
+            dn = np.einsum("iiG->iG", Mn)[:, neg]
+            Ed += -2 * pref * np.einsum("G,iG,jG->", v, d, dn).real
+    return Ed, Ex
+
+
+def test_working_form_equals_laplace_canonical_sum():
+    """The virtual presummation is an exact regrouping (Sec. II B): the transformed-
+    state form equals canonical MP2 with the same quadrature, to rounding."""
+    s = solid("tiny2", random_phases=True)
+    o = _sys(s)
+    tau, w = sinc_laplace_quadrature(5, *denominator_range(o))
+    ref = mp2_energy(o, laplace_denominator(tau, w))
+    Ed, Ex = _working_form(o, tau, w)
+    assert abs(Ed - ref["E_d"]) < 1e-12 * abs(ref["E_d"])
+    assert abs(Ex - ref["E_x"]) < 1e-12 * abs(ref["E_x"])
+
+
+def test_working_form_is_additive_over_gprime_subsets():
+    """The outer G' loop splits into independent additive pieces (Sec. III B)."""
+    s = solid("tiny")
+    o = _sys(s)
+    tau, w = sinc_laplace_quadrature(3, *denominator_range(o))
+    n = len(aux_set(o)[0])
+    full = _working_form(o, tau, w)
+    parts = [_working_form(o, tau, w, range(k, n, 3)) for k in range(3)]
+    assert abs(sum(p[0] for p in parts) - full[0]) < 1e-13 * abs(full[0])
+    assert abs(sum(p[1] for p in parts) - full[1]) < 1e-13 * abs(full[1])
