@@ -1,0 +1,188 @@
+/*
+ * ltmp2.h -- C ABI of the GB300 (sm_103a) Laplace-transformed MP2 hot path.
+ *
+ * Method: Schaefer, Ramberger, Kresse, "Quartic scaling MP2 for solids: a highly
+ * parallelized algorithm in the plane wave basis" (arXiv:1611.06797).  Gamma
+ * point, closed shell, spin restricted (Sec. II B: sum over spins -> 2).
+ *
+ * For each Laplace point tau (Eq. SCHLT) the library builds the tau-scaled
+ * virtual Green's function P_v(tau) = sum_a |a> e^{-(e_a - mu) tau} <a| in the
+ * plane-wave basis, the transformed occupied states
+ *     w_j^{(G' tau)} = e^{(e_j - mu) tau} P_v(tau) e^{-iG'r} |j>       (Eqs. SCHnewstate, SCHtransmatrix)
+ * forms the pair co-densities <i| e^{-iGr} |w_j^{(G' tau)}> with batched 3D FFTs,
+ * weights them with the Coulomb kernel v(G) = 4 pi / G^2 (Eq. SCH2EI) and
+ * contracts the exchange (Fock-like, Eq. SCHfocklike) and direct (Hartree-like,
+ * Eq. dLTMP2Compact at q = 0) terms.  No sum over virtual orbitals is done
+ * after P_v is built.  The energies are
+ *     E_x = sum_k w_k/Omega^2 sum_{G,G' in A} v(G) v(G') sum_ij M_ij(G;G') M_ji(-G;-G')
+ *     E_d = -2 sum_k w_k/Omega^2 sum_{G,G' in A} v(G) v(G') sum_ij M_ii(G;G') M_jj(-G;-G')
+ * with M_ij(G;G') = <i|e^{-iGr}|w_j^{(G' tau_k)}> and A the auxiliary set
+ * {G != 0 : |G|^2/2 <= E_cut^aux} (Sec. II A).  This equals closed-shell MP2
+ * (Eq. CanMP2 with Eqs. MP2direct, MP2exchange) with 1/Delta replaced by
+ * -sum_k w_k exp(Delta tau_k).
+ *
+ * Conventions
+ *   - Hartree atomic units; energies are per simulation cell.
+ *   - Overlap densities are grid-discrete: phi_n(r_t) = Omega^{-1/2} sum_p c_n(p)
+ *     e^{i G_p r_t} on the FFT grid and rho_mn(G) = (Omega/N_FFT) sum_t
+ *     phi_m^*(r_t) phi_n(r_t) e^{-i G r_t} (aliasing included).
+ *   - The G = 0 Coulomb term is dropped (rho_ia(0) = 0 for occupied/virtual pairs).
+ *   - Every function returns LTMP2_OK (0) or a negative status; ltmp2_strerror()
+ *     names it.  Nothing is printed.  On error no output is written.
+ *   - A context is thread-compatible, not thread-safe: calls on one context must
+ *     not overlap.  Different contexts are independent.
+ *   - All pointers in these signatures are HOST pointers unless stated.
+ */
+#ifndef LTMP2_H
+#define LTMP2_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define LTMP2_OK 0
+#define LTMP2_ERR_INVALID_ARG (-1)     /* NULL pointer, size <= 0, NaN, unsorted eigenvalues ... */
+#define LTMP2_ERR_GAP (-2)             /* e_LUMO - e_HOMO < 1e-6 Ha: the Laplace transform needs a gap */
+#define LTMP2_ERR_NOT_ORTHONORMAL (-3) /* sampled <m|n> deviates from delta_mn by more than 1e-8 */
+#define LTMP2_ERR_GRID (-4)            /* grid not cubic/5-smooth/supported, or a sphere does not fit it */
+#define LTMP2_ERR_OOM (-5)             /* device allocation failed */
+#define LTMP2_ERR_CUDA (-6)            /* a CUDA call failed (no device, launch error ...) */
+#define LTMP2_ERR_TIMEOUT (-7)         /* a bounded device wait ran out (persistent batch kernel) */
+#define LTMP2_ERR_UNSUPPORTED (-8)     /* option not available for these sizes */
+#define LTMP2_ERR_NO_CONVERGENCE (-9)  /* Laplace-grid fit did not converge */
+#define LTMP2_ERR_NOT_REAL (-10)       /* LTMP2_FLAG_REAL_ORBITALS set but c(-G) != conj c(G) */
+
+/* ---------------------------------------------------------------- precision */
+/* LTMP2_FP64: complex128 FFTs, FP64 GEMMs, FP64 accumulation (the plain path).   */
+/* LTMP2_FP32: complex64 FFTs; Green's-function and transformed-state GEMMs on   */
+/*             tcgen05 tensor cores in BF16 3-term split precision with FP32     */
+/*             accumulation; per-pair, per-tau and final sums in FP64.           */
+#define LTMP2_FP64 0
+#define LTMP2_FP32 1
+
+/* ---------------------------------------------------------------- flags */
+/* Orbitals are real in real space, c_n(-G) = conj(c_n(G)) (time-reversal symmetry,
+ * Sec. II D, at k = 0).  Then w_j^{(-G')} = conj(w_j^{(G')}) in real space and only
+ * half of the G' set is transformed; the library checks the property in setup.  */
+#define LTMP2_FLAG_REAL_ORBITALS 1
+
+typedef struct ltmp2_ctx ltmp2_ctx; /* opaque; owns all device memory of one system */
+
+/* Mean-field input of one system (Sec. II A; the paper takes HF orbitals, Fig. SerialGamma).
+ *   lattice   [9]  rows a1, a2, a3 of the cell (bohr), row-major; Omega = |det|.
+ *   grid      [3]  FFT grid n1, n2, n3.  Must be cubic (n1 = n2 = n3) with
+ *                  n in {8,10,12,16,18,20,24,25,27,30,32,36,40}.
+ *   n_pw           number of plane waves of the orbital basis (|G|^2/2 <= E_cut).
+ *   miller    [n_pw][3] int: G_p = m1 b1 + m2 b2 + m3 b3.  The set must be
+ *                  inversion symmetric, each |m_k| < n_k/2, and for every (m1, m2)
+ *                  its m3 values must form one contiguous range (true for a sphere).
+ *   n_orb, n_occ   orbitals (ascending energy); the first n_occ are doubly occupied,
+ *                  all others virtual.  1 <= n_occ < n_orb <= n_pw.
+ *   coeff     [n_orb][n_pw] complex128 as interleaved (re, im) doubles, row-major,
+ *                  orthonormal rows (the library samples <m|n>).
+ *   eps       [n_orb] orbital energies in Hartree, non-decreasing.
+ *   ecut_aux       E_cut^aux in Hartree; <= 0 selects 2/3 of the largest |G_p|^2/2
+ *                  ("commonly chosen as 2/3 E_cut", Sec. II A).
+ *   precision      LTMP2_FP64 or LTMP2_FP32.
+ *   flags          0 or LTMP2_FLAG_REAL_ORBITALS.
+ */
+typedef struct {
+  double lattice[9];
+  int grid[3];
+  int n_pw;
+  const int *miller;
+  int n_orb;
+  int n_occ;
+  const double *coeff;
+  const double *eps;
+  double ecut_aux;
+  int precision;
+  int flags;
+} ltmp2_system;
+
+/* Validate the input, copy it to the current CUDA device and precompute the
+ * tau-independent parts (occupied orbitals on the grid, the aux set A and v(G),
+ * index tables).  The caller keeps ownership of every array in *sys; nothing is
+ * retained.  On success *out owns the device memory until ltmp2_destroy().
+ * Errors: INVALID_ARG, GAP, NOT_ORTHONORMAL, GRID, NOT_REAL, OOM, CUDA.           */
+int ltmp2_setup(const ltmp2_system *sys, ltmp2_ctx **out);
+
+/* Run all later work of ctx on this CUDA stream (a cudaStream_t passed as void*;
+ * NULL = the legacy default stream).  The stream must belong to the device that
+ * was current at setup and must outlive the calls that use it.                  */
+int ltmp2_set_stream(ltmp2_ctx *ctx, void *stream);
+
+/* Laplace quadrature for the energy denominator (Eq. SCHLT; the paper uses a
+ * minimax grid, Sec. II C and Sec. III A, without printing it):
+ *     1/x ~= sum_{k<n_tau} w_k exp(-x tau_k)   on  x in [2 gap, 2 width],
+ * fitted to minimise max_x |1 - x sum_k w_k exp(-x tau_k)| (relative error).
+ *   gap   = e_LUMO - e_HOMO > 0,  width = e_max - e_min >= gap  (Hartree).
+ *   n_tau in [1, 24].  tau, w: caller arrays of n_tau doubles, ascending tau.
+ *   max_err (may be NULL): the achieved maximum relative error, measured on
+ *   20000 log-spaced points.  Host only; no device is touched.
+ * Errors: INVALID_ARG, NO_CONVERGENCE.                                          */
+int ltmp2_laplace_grid(double gap, double width, int n_tau, double *tau, double *w,
+                       double *max_err);
+
+/* E_direct and E_exchange (and per-pair energies) for the quadrature (tau, w).
+ *   n_tau >= 1; tau[k] > 0, w[k] finite (host arrays, copied).
+ *   e_direct, e_exchange: one double each (host).
+ *   e_pair: NULL or [n_occ][n_occ] doubles (host, row-major) receiving
+ *           e_ij = e^d_ij + e^x_ij, symmetric, summing to E_d + E_x.
+ * The call is synchronous: it returns after the results are on the host.
+ * Errors: INVALID_ARG, OOM, CUDA.                                               */
+int ltmp2_energy(ltmp2_ctx *ctx, int n_tau, const double *tau, const double *w,
+                 double *e_direct, double *e_exchange, double *e_pair);
+
+/* The contribution of the outer-loop plane waves G' in the half-open range
+ * [gp_begin, gp_end) of the ordered primary set (Sec. III B: the G' loop splits
+ * into independent, communication-free pieces).  Primary G' are the aux vectors
+ * whose first non-zero Miller index is positive; each carries its partner -G'.
+ * Summing the outputs over a partition of [0, ltmp2_num_primary_gprime()) gives
+ * exactly the ltmp2_energy() result up to summation order.
+ *   e_pair_direct, e_pair_exchange: NULL or [n_occ][n_occ] doubles (host).
+ * Errors: INVALID_ARG, OOM, CUDA.                                               */
+int ltmp2_energy_partial(ltmp2_ctx *ctx, int n_tau, const double *tau, const double *w,
+                         int gp_begin, int gp_end, double *e_direct, double *e_exchange,
+                         double *e_pair_direct, double *e_pair_exchange);
+
+/* Primary G' vectors processed per slab (one pass of the transformed-state GEMM,
+ * the FFT kernels and the contraction).  Setup picks the largest slab that fits a
+ * share of the free device memory; n in [1, that capacity] lowers it (smaller
+ * launches, same result up to summation order), n <= 0 restores it.  Returns the
+ * slab size in effect, or a negative status.                                     */
+int ltmp2_set_slab_size(ltmp2_ctx *ctx, int n);
+
+/* Number of primary G' vectors (half of |A|); returns < 0 on a NULL ctx.        */
+int ltmp2_num_primary_gprime(const ltmp2_ctx *ctx);
+
+/* Sizes of a set-up system: n_aux = |A| (G = 0 excluded), n_pw, n_occ, grid n. */
+int ltmp2_sizes(const ltmp2_ctx *ctx, int *n_aux, int *n_pw, int *n_occ, int *grid_n);
+
+/* Imaginary residues of the last ltmp2_energy* call: the exact sums are real, so
+ * these measure rounding (and, for LTMP2_FLAG_REAL_ORBITALS, the symmetry).       */
+int ltmp2_last_imag(const ltmp2_ctx *ctx, double *im_direct, double *im_exchange);
+
+/* Per-stage device timing.  When enabled (on != 0), every later ltmp2_energy*
+ * call records CUDA events around each kernel launch on the context's stream and
+ * accumulates, per stage, the number of launches and their summed duration (ms).
+ * Stages: 0 Green's-function GEMM, 1 transformed-state GEMM, 2 gather and
+ * w z-transform, 3 plane FFT kernel, 4 column FFT + exchange contraction,
+ * 5 direct-term contraction, 6 accumulation.  ltmp2_stage_times() copies
+ * min(n, 7) entries and resets nothing; ltmp2_reset_stage_times() zeroes them.   */
+#define LTMP2_NUM_STAGES 7
+int ltmp2_set_profiling(ltmp2_ctx *ctx, int on);
+int ltmp2_stage_times(const ltmp2_ctx *ctx, int n, double *ms, long long *launches);
+int ltmp2_reset_stage_times(ltmp2_ctx *ctx);
+
+/* Free all device memory of ctx.  NULL is ignored.                              */
+void ltmp2_destroy(ltmp2_ctx *ctx);
+
+/* Static description of a status code (never NULL).                             */
+const char *ltmp2_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LTMP2_H */

@@ -1,0 +1,447 @@
+// Kernel templates of the LTMP2 hot path, templated on the real type T
+// (double for the plain path, float for the precision form) and on the grid
+// size N.  Step names follow Sec. III A of arXiv:1611.06797:
+//   (iii) transformed states w_j^{(G' tau)} (Eqs. SCHnewstate, SCHtransmatrix),
+//         built as e^{(e_j-mu)tau} P_v(tau) e^{-iG'r}|j>;
+//   (iv)  Fock-like (Eq. SCHfocklike) and Hartree-like (Eq. dLTMP2Compact)
+//         contractions of the co-densities <i|e^{-iGr}|w_j^{(G' tau)}>.
+#pragma once
+#include "fft.cuh"
+#include "plan.h"
+
+namespace ltmp2 {
+
+template <typename T> __device__ __forceinline__ const T *vtab(const Plan &p);
+template <> __device__ __forceinline__ const double *vtab<double>(const Plan &p) { return p.v_aux64; }
+template <> __device__ __forceinline__ const float *vtab<float>(const Plan &p) { return p.v_aux32; }
+
+__device__ __forceinline__ int wrapn(int m, int n) {
+  int r = m % n;
+  return r < 0 ? r + n : r;
+}
+// frequency of storage slot k on an N-point axis (|m| < N/2 for every used slot)
+template <int N> __device__ __forceinline__ constexpr int freq_of(int k) { return k > N / 2 ? k - N : k; }
+
+// position in A of the G' carried by a slot of the current slab
+__device__ __forceinline__ int slot_aux(const Plan &p, int gp0, int np, int slot) {
+  return slot < np ? p.prim[gp0 + slot] : p.aux_neg[p.prim[gp0 + slot - np]];
+}
+
+// ---------------------------------------------------------------- scale factors
+// virtual a: e^{-(e_a - mu) tau} (Green's function weights); occupied j: e^{(e_j - mu) tau}
+template <typename T>
+__global__ void k_dscale(int n_orb, int n_occ, const double *__restrict__ eps, double mu, double tau,
+                         T *__restrict__ d) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_orb) return;
+  double x = (eps[a] - mu) * tau;
+  d[a] = (T)exp(a < n_occ ? x : -x);
+}
+
+// ---------------------------------------------------------------- SIMT complex GEMM
+// C[m][n] = sum_k opA(m,k) * B[k][n] * s_k,  opA(m,k) = A[m*lda+k] (A_KM) or A[k*lda+m],
+// conjugated if A_CONJ; s_k = kscale[k] or 1.  64x64 tile, 256 threads, 4x4 per thread.
+template <typename T, bool A_KM, bool A_CONJ>
+__global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cpx<T> *__restrict__ A, int lda,
+                                               const cpx<T> *__restrict__ B, int ldb,
+                                               const T *__restrict__ kscale, cpx<T> *__restrict__ C,
+                                               int ldc) {
+  constexpr int BM = 64, BN = 64, BK = 8;
+  __shared__ cpx<T> As[BK][BM];
+  __shared__ cpx<T> Bs[BK][BN];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  cpx<T> acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = {T(0), T(0)};
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int e = threadIdx.x; e < BM * BK; e += 256) {
+      int mm, kk;
+      if (A_KM) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      cpx<T> v = {T(0), T(0)};
+      if (gm < M && gk < K) v = A_KM ? A[(size_t)gm * lda + gk] : A[(size_t)gk * lda + gm];
+      if (A_CONJ) v.y = -v.y;
+      As[kk][mm] = v;
+    }
+    for (int e = threadIdx.x; e < BN * BK; e += 256) {
+      const int nn = e % BN, kk = e / BN;
+      const int gn = n0 + nn, gk = k0 + kk;
+      cpx<T> v = {T(0), T(0)};
+      if (gn < N && gk < K) {
+        v = B[(size_t)gk * ldb + gn];
+        if (kscale) v = cscale(v, kscale[gk]);
+      }
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      cpx<T> a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fma(a[i].x, b[j].x, fma(-a[i].y, b[j].y, acc[i][j].x));
+          acc[i][j].y = fma(a[i].x, b[j].y, fma(a[i].y, b[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+      if (gm < M && gn < N) C[(size_t)gm * ldc + gn] = acc[i][j];
+    }
+}
+
+// ---------------------------------------------------------------- gather S^T
+// S^T[(slot, j)][q] = e^{(e_j - mu) tau} c_j((G_q + G'_slot) mod grid): the plane-wave
+// coefficients of e^{-iG'r} phi_j restricted to the orbital sphere, scaled.
+template <typename T>
+__global__ void k_gather_s(Plan p, int gp0, int np, cpx<T> *__restrict__ st) {
+  const int col = blockIdx.y;
+  const int slot = col / p.n_occ, j = col % p.n_occ;
+  const int g = slot_aux(p, gp0, np, slot);
+  const int gx = p.aux_m[3 * g], gy = p.aux_m[3 * g + 1], gz = p.aux_m[3 * g + 2];
+  const T dj = ((const T *)p.dscale)[j];
+  const int n = p.n;
+  const cpx<T> *cg = (const cpx<T> *)p.cgrid + (size_t)j * n * n * n;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < p.n_pw; q += gridDim.x * blockDim.x) {
+    const int wx = wrapn(p.pw_m[3 * q] + gx, n), wy = wrapn(p.pw_m[3 * q + 1] + gy, n),
+              wz = wrapn(p.pw_m[3 * q + 2] + gz, n);
+    st[(size_t)col * p.n_pw + q] = cscale(cg[((size_t)wz * n + wy) * n + wx], dj);
+  }
+}
+
+// scatter rows of coefficients (internal order) onto the full grid, layout [row][z][y][x]
+template <typename T>
+__global__ void k_scatter_grid(Plan p, int rows, const cpx<T> *__restrict__ c, cpx<T> *__restrict__ grid) {
+  const int r = blockIdx.y;
+  const int n = p.n;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < p.n_pw; q += gridDim.x * blockDim.x) {
+    const int wx = wrapn(p.pw_m[3 * q], n), wy = wrapn(p.pw_m[3 * q + 1], n), wz = wrapn(p.pw_m[3 * q + 2], n);
+    grid[(size_t)r * n * n * n + ((size_t)wz * n + wy) * n + wx] = c[(size_t)r * p.n_pw + q];
+  }
+}
+
+// ---------------------------------------------------------------- inverse z transform
+// For column vector col of W^T (plane-wave coefficients of one w_j^{G'}, internal order)
+// and orbital-disk column d: place the m3 range on the z axis and inverse-transform.
+// Output z1[col][t3][d].
+template <typename T, int N>
+__global__ void k_w_zinv(Plan p, int ld_in, const cpx<T> *__restrict__ wt, cpx<T> *__restrict__ z1) {
+  const int col = blockIdx.y;
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= p.n_dorb) return;
+  const int4 c = p.dorb[d];
+  const cpx<T> *w = wt + (size_t)col * ld_in + p.dorb_off[d];
+  cpx<T> a[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const int m = freq_of<N>(k);
+    a[k] = (m >= c.z && m <= c.w) ? w[m - c.z] : cpx<T>{T(0), T(0)};
+  }
+  LineFFT<T, N, +1>::run(a);
+  cpx<T> *z = z1 + (size_t)col * N * p.n_dorb + d;
+#pragma unroll
+  for (int k = 0; k < N; ++k) z[(size_t)k * p.n_dorb] = a[k];
+}
+
+// ---------------------------------------------------------------- plane kernel
+// Block (z, col).  Phase 1: the orbital-disk values of plane z -> inverse y then x
+// transform = w_j^{G'}(x, y, z) in shared memory.  Phase 2, for each occupied i:
+// conj(phi_i) * w_j^{G'} -> forward x then y transform, keep the aux disk, write
+// tbuf[(col, i)][z][d_aux].  IB occupied planes are transformed together.
+template <typename T, int N>
+__device__ __forceinline__ void plane_inverse(const Plan &p, const cpx<T> *__restrict__ zrow, cpx<T> *xp) {
+  constexpr int P = N + 1;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int e = tid; e < N * P; e += nth) xp[e] = {T(0), T(0)};
+  __syncthreads();
+  for (int d = tid; d < p.n_dorb; d += nth) {
+    const int4 c = p.dorb[d];
+    xp[wrapn(c.y, N) * P + wrapn(c.x, N)] = zrow[d];
+  }
+  __syncthreads();
+  const int nxo = p.mxhi_orb - p.mxlo_orb + 1;
+  for (int t = tid; t < nxo; t += nth) {
+    const int x = wrapn(p.mxlo_orb + t, N);
+    cpx<T> a[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) a[k] = xp[k * P + x];
+    LineFFT<T, N, +1>::run(a);
+#pragma unroll
+    for (int k = 0; k < N; ++k) xp[k * P + x] = a[k];
+  }
+  __syncthreads();
+  for (int t = tid; t < N; t += nth) {
+    cpx<T> a[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) a[k] = xp[t * P + k];
+    LineFFT<T, N, +1>::run(a);
+#pragma unroll
+    for (int k = 0; k < N; ++k) xp[t * P + k] = a[k];
+  }
+  __syncthreads();
+}
+
+template <typename T, int N>
+__global__ void k_planes(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> *__restrict__ tbuf) {
+  constexpr int P = N + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T> *xp = reinterpret_cast<cpx<T> *>(smem_raw);
+  cpx<T> *wk = xp + N * P;
+  const int z = blockIdx.x, col = blockIdx.y;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int no = p.n_occ;
+  plane_inverse<T, N>(p, z1 + ((size_t)col * N + z) * p.n_dorb, xp);
+  const cpx<T> *u = (const cpx<T> *)p.u;
+  const int nxa = p.mxhi_aux - p.mxlo_aux + 1;
+  for (int i0 = 0; i0 < no; i0 += ib) {
+    const int nb = min(ib, no - i0);
+    for (int e = tid; e < nb * N * N; e += nth) {
+      const int il = e / (N * N), r = e % (N * N), y = r / N, x = r % N;
+      const cpx<T> uu = u[((size_t)(i0 + il) * N + z) * N * N + r];
+      wk[(il * N + y) * P + x] = cmul(cconj(uu), xp[y * P + x]);
+    }
+    __syncthreads();
+    for (int t = tid; t < nb * N; t += nth) {
+      cpx<T> *row = wk + t * P;  // (il * N + y) * P
+      cpx<T> a[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) a[k] = row[k];
+      LineFFT<T, N, -1>::run(a);
+#pragma unroll
+      for (int k = 0; k < N; ++k) row[k] = a[k];
+    }
+    __syncthreads();
+    for (int t = tid; t < nb * nxa; t += nth) {
+      const int il = t / nxa, x = wrapn(p.mxlo_aux + t % nxa, N);
+      cpx<T> *base = wk + il * N * P;
+      cpx<T> a[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) a[k] = base[k * P + x];
+      LineFFT<T, N, -1>::run(a);
+#pragma unroll
+      for (int k = 0; k < N; ++k) base[k * P + x] = a[k];
+    }
+    __syncthreads();
+    for (int e = tid; e < nb * p.n_daux; e += nth) {
+      const int il = e / p.n_daux, d = e % p.n_daux;
+      const int4 c = p.daux[d];
+      const size_t item = (size_t)col * no + i0 + il;
+      tbuf[(item * N + z) * p.n_daux + d] = wk[(il * N + wrapn(c.y, N)) * P + wrapn(c.x, N)];
+    }
+    __syncthreads();
+  }
+}
+
+// setup: real-space occupied orbitals u[j][z][y][x] from z1 (cols = occupied orbitals)
+template <typename T, int N>
+__global__ void k_planes_store(Plan p, const cpx<T> *__restrict__ z1, cpx<T> *__restrict__ out) {
+  constexpr int P = N + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T> *xp = reinterpret_cast<cpx<T> *>(smem_raw);
+  const int z = blockIdx.x, col = blockIdx.y;
+  plane_inverse<T, N>(p, z1 + ((size_t)col * N + z) * p.n_dorb, xp);
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int y = e / N, x = e % N;
+    out[((size_t)col * N + z) * N * N + e] = xp[y * P + x];
+  }
+}
+
+// ---------------------------------------------------------------- column kernel
+// Block = one pair of co-density items.  Forward z transform of every aux-disk column
+// of item A (kept in shared memory, indexed like A) and of the partner item B, then
+//   general: X = sum_G v(G) M_A(-G) M_B(G)   (A = (i,j,G'), B = (j,i,-G'))
+//   real   : X = sum_G v(G) M_A(G) conj(M_B(G))   (A = (i,j,G'), B = (j,i,G'))
+// M values are unnormalised (N^3 times the co-density).  Diagonal items also store
+// M_ii(G;G') in mdiag[slot][G][i] for the direct term.
+template <typename T>
+__device__ __forceinline__ void block_reduce_store(double ax, double ay, double2 *dst, double2 *dst_t) {
+  __shared__ double red[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+  }
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32, nw = (blockDim.x + 31) / 32;
+  if (l == 0) { red[0][w] = ax; red[1][w] = ay; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sx = 0, sy = 0;
+    for (int k = 0; k < nw; ++k) { sx += red[0][k]; sy += red[1][k]; }
+    *dst = make_double2(sx, sy);
+    if (dst_t) *dst_t = make_double2(sx, -sy);
+  }
+}
+
+template <typename T, int N>
+__global__ void k_zcol(Plan p, int gp0, int np, const cpx<T> *__restrict__ tbuf, cpx<T> *__restrict__ mdiag,
+                       double2 *__restrict__ sx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T> *MA = reinterpret_cast<cpx<T> *>(smem_raw);
+  const int no = p.n_occ;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  int i, j, gpl, slotA, slotB;
+  bool self = false;
+  if (!p.real_orb) {
+    gpl = blockIdx.x / (no * no);
+    const int r = blockIdx.x % (no * no);
+    i = r / no; j = r % no;
+    slotA = gpl; slotB = gpl + np;
+  } else {
+    const int npairs = no * (no + 1) / 2;
+    gpl = blockIdx.x / npairs;
+    int t = blockIdx.x % npairs;
+    i = 0;
+    while (t >= no - i) { t -= no - i; ++i; }
+    j = i + t;
+    slotA = slotB = gpl;
+    self = (i == j);
+  }
+  const bool diag = (i == j);
+  const size_t itemA = ((size_t)slotA * no + j) * no + i;   // (i, j, slotA)
+  const size_t itemB = ((size_t)slotB * no + i) * no + j;   // (j, i, slotB)
+  const T *v = vtab<T>(p);
+  const int nd = p.n_daux;
+  T accx = T(0), accy = T(0);
+  for (int d = tid; d < nd; d += nth) {
+    const int4 c = p.daux[d];
+    const int off = p.daux_off[d];
+    const cpx<T> *src = tbuf + itemA * N * nd + d;
+    cpx<T> a[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) a[k] = src[(size_t)k * nd];
+    LineFFT<T, N, -1>::run(a);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int m = freq_of<N>(k);
+      if (m >= c.z && m <= c.w) {
+        const int g = off + m - c.z;
+        MA[g] = a[k];
+        if (diag) mdiag[((size_t)slotA * p.n_aux + g) * no + i] = a[k];
+        if (self) accx += v[g] * (a[k].x * a[k].x + a[k].y * a[k].y);
+      }
+    }
+  }
+  __syncthreads();
+  if (!self) {
+    for (int d = tid; d < nd; d += nth) {
+      const int4 c = p.daux[d];
+      const int off = p.daux_off[d];
+      const cpx<T> *src = tbuf + itemB * N * nd + d;
+      cpx<T> a[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) a[k] = src[(size_t)k * nd];
+      LineFFT<T, N, -1>::run(a);
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int m = freq_of<N>(k);
+        if (m >= c.z && m <= c.w) {
+          const int g = off + m - c.z;
+          cpx<T> prod;
+          if (!p.real_orb) {
+            prod = cmul(MA[p.aux_neg[g]], a[k]);
+            if (diag) mdiag[((size_t)slotB * p.n_aux + g) * no + i] = a[k];
+          } else {
+            prod = cmulconj(MA[g], a[k]);
+          }
+          accx += v[g] * prod.x;
+          accy += v[g] * prod.y;
+        }
+      }
+    }
+  }
+  double2 *dst = sx + ((size_t)gpl * no + i) * no + j;
+  double2 *dst_t = (p.real_orb && i != j) ? sx + ((size_t)gpl * no + j) * no + i : nullptr;
+  block_reduce_store<T>((double)accx, (double)accy, dst, dst_t);
+}
+
+// ---------------------------------------------------------------- direct term
+// Y_ij(G') = sum_G v(G) M_ii(G;G') M_jj(-G;-G')  (general)  or  M_ii(G;G') conj(M_jj(G;G')) (real)
+template <typename T>
+__global__ void k_direct(Plan p, int np, const cpx<T> *__restrict__ mdiag, double2 *__restrict__ yd) {
+  const int gpl = blockIdx.x, i = blockIdx.y;
+  const int no = p.n_occ;
+  const int slotA = gpl, slotB = p.real_orb ? gpl : gpl + np;
+  const T *v = vtab<T>(p);
+  const cpx<T> *MA = mdiag + (size_t)slotA * p.n_aux * no;
+  const cpx<T> *MB = mdiag + (size_t)slotB * p.n_aux * no;
+  for (int j = threadIdx.x; j < no; j += blockDim.x) {
+    double ax = 0, ay = 0;
+    T cx = T(0), cy = T(0);
+    for (int g = 0; g < p.n_aux; ++g) {
+      const cpx<T> x = MA[(size_t)g * no + i];
+      cpx<T> prod;
+      if (!p.real_orb) prod = cmul(x, MB[(size_t)p.aux_neg[g] * no + j]);
+      else prod = cmulconj(x, MB[(size_t)g * no + j]);
+      cx += v[g] * prod.x;
+      cy += v[g] * prod.y;
+      if ((g & 31) == 31) { ax += (double)cx; ay += (double)cy; cx = cy = T(0); }
+    }
+    ax += (double)cx; ay += (double)cy;
+    yd[((size_t)gpl * no + i) * no + j] = make_double2(ax, ay);
+  }
+}
+
+// ---------------------------------------------------------------- accumulation (FP64)
+//   e^x_ij += coef v(G') (X_ij + X_ji),   e^d_ij += -2 coef v(G') (Y_ij + Y_ji)
+// coef = w_k / (Omega^2 N_FFT^2); the sum over the slab runs in a fixed order.
+static __global__ void k_accum(Plan p, int gp0, int np, double coef, const double2 *__restrict__ sx,
+                        const double2 *__restrict__ yd) {
+  const int no = p.n_occ;
+  const int ij = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ij >= no * no) return;
+  const int i = ij / no, j = ij % no;
+  double ex = 0, exi = 0, ed = 0, edi = 0;
+  for (int gpl = 0; gpl < np; ++gpl) {
+    const double vv = coef * p.v_aux64[p.prim[gp0 + gpl]];
+    const double2 a = sx[((size_t)gpl * no + i) * no + j], b = sx[((size_t)gpl * no + j) * no + i];
+    const double2 c = yd[((size_t)gpl * no + i) * no + j], d = yd[((size_t)gpl * no + j) * no + i];
+    ex += vv * (a.x + b.x);
+    exi += vv * (a.y + b.y);
+    ed += -2.0 * vv * (c.x + d.x);
+    edi += -2.0 * vv * (c.y + d.y);
+  }
+  p.ex[ij] += ex;
+  p.exi[ij] += exi;
+  p.ed[ij] += ed;
+  p.edi[ij] += edi;
+}
+
+static __global__ void k_zero_acc(Plan p) {
+  const int no2 = p.n_occ * p.n_occ;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < no2; k += gridDim.x * blockDim.x) {
+    p.ex[k] = 0; p.exi[k] = 0; p.ed[k] = 0; p.edi[k] = 0;
+  }
+}
+
+// fixed-order final sums: esum = {E_d, E_x, Im E_d, Im E_x}; one block of 256 threads
+static __global__ void k_finish(Plan p) {
+  __shared__ double red[4][256];
+  const int no2 = p.n_occ * p.n_occ;
+  double s[4] = {0, 0, 0, 0};
+  for (int k = threadIdx.x; k < no2; k += blockDim.x) {
+    s[0] += p.ed[k]; s[1] += p.ex[k]; s[2] += p.edi[k]; s[3] += p.exi[k];
+  }
+  for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = s[q];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 4; ++q) p.esum[q] = red[q][0];
+}
+
+}  // namespace ltmp2

@@ -1,0 +1,5 @@
+// FP64 (plain path) instantiation of the hot-path kernels.
+#include "path_impl.cuh"
+namespace ltmp2 {
+template struct Path<double>;
+}

@@ -1,0 +1,620 @@
+// C ABI of the LTMP2 hot path: input validation, index tables, device memory,
+// the tau / G'-slab driver loop and per-stage timing.  The arithmetic of the
+// path runs in the kernels of kernels_f64.cu / kernels_f32.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <type_traits>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/ltmp2.h"
+#include "fft.cuh"
+#include "plan.h"
+
+using namespace ltmp2;
+
+namespace {
+
+struct EventTimer final : StageTimer {
+  bool on = false;
+  cudaStream_t stream = nullptr;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> pending;
+  std::vector<cudaEvent_t> open;  // begin events by stage
+  double ms[LTMP2_NUM_STAGES] = {0};
+  long long launches[LTMP2_NUM_STAGES] = {0};
+  EventTimer() : open(LTMP2_NUM_STAGES, nullptr) {}
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void begin(int stage) override {
+    if (!on) return;
+    cudaEvent_t e = get();
+    cudaEventRecord(e, stream);
+    open[stage] = e;
+  }
+  void end(int stage) override {
+    if (!on || !open[stage]) return;
+    cudaEvent_t e = get();
+    cudaEventRecord(e, stream);
+    pending.emplace_back(stage, open[stage], e);
+    open[stage] = nullptr;
+  }
+  void collect() {
+    for (auto &t : pending) {
+      float x = 0.f;
+      cudaEventSynchronize(std::get<2>(t));
+      if (cudaEventElapsedTime(&x, std::get<1>(t), std::get<2>(t)) == cudaSuccess) {
+        ms[std::get<0>(t)] += x;
+        launches[std::get<0>(t)] += 1;
+      }
+      pool.push_back(std::get<1>(t));
+      pool.push_back(std::get<2>(t));
+    }
+    pending.clear();
+  }
+  ~EventTimer() override {
+    for (auto e : pool) cudaEventDestroy(e);
+    for (auto &t : pending) {
+      cudaEventDestroy(std::get<1>(t));
+      cudaEventDestroy(std::get<2>(t));
+    }
+  }
+};
+
+}  // namespace
+
+struct ltmp2_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Plan p;
+  std::vector<void *> allocs;
+  EventTimer timer;
+  double last_imag[2] = {0, 0};
+  int slab_capacity = 0;
+  ~ltmp2_ctx() {
+    for (void *q : allocs) cudaFree(q);
+  }
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return LTMP2_OK;
+  if (e == cudaErrorMemoryAllocation) return LTMP2_ERR_OOM;
+  return LTMP2_ERR_CUDA;
+}
+
+template <typename X> int dalloc(ltmp2_ctx *c, X **ptr, size_t count) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(X));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? LTMP2_ERR_OOM : LTMP2_ERR_CUDA;
+  }
+  c->allocs.push_back(q);
+  *ptr = static_cast<X *>(q);
+  return LTMP2_OK;
+}
+
+int dalloc_bytes(ltmp2_ctx *c, void **ptr, size_t bytes) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? LTMP2_ERR_OOM : LTMP2_ERR_CUDA;
+  }
+  c->allocs.push_back(q);
+  *ptr = q;
+  return LTMP2_OK;
+}
+
+struct Col {
+  int m1, m2, zlo, zhi, off;
+};
+
+// Group a set of Miller indices into (m1, m2) columns with contiguous m3 ranges.
+// order[k] = original index of the k-th point in column order.  false if a column
+// has a gap.
+bool build_columns(const std::vector<std::array<int, 3>> &m, std::vector<Col> &cols,
+                   std::vector<int> &order) {
+  const int n = (int)m.size();
+  order.resize(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return m[a] < m[b]; });
+  cols.clear();
+  for (int k = 0; k < n; ++k) {
+    const auto &q = m[order[k]];
+    if (cols.empty() || cols.back().m1 != q[0] || cols.back().m2 != q[1]) {
+      cols.push_back({q[0], q[1], q[2], q[2], k});
+    } else {
+      if (q[2] != cols.back().zhi + 1) return false;
+      cols.back().zhi = q[2];
+    }
+  }
+  return true;
+}
+
+void reciprocal(const double *A, double B[9], double *omega) {
+  // rows a_i; B rows b_k with a_i . b_k = 2 pi delta_ik: B = 2 pi (A^{-1})^T
+  const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                     A[2] * (A[3] * A[7] - A[4] * A[6]);
+  *omega = std::fabs(det);
+  double inv[9];
+  inv[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+  inv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+  inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+  inv[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+  inv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+  inv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+  inv[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+  inv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+  inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  const double tp = 6.283185307179586476925286766559;
+  for (int k = 0; k < 3; ++k)
+    for (int c = 0; c < 3; ++c) B[k * 3 + c] = tp * inv[c * 3 + k];
+}
+
+double g2_of(const double B[9], int m1, int m2, int m3) {
+  const double gx = m1 * B[0] + m2 * B[3] + m3 * B[6];
+  const double gy = m1 * B[1] + m2 * B[4] + m3 * B[7];
+  const double gz = m1 * B[2] + m2 * B[5] + m3 * B[8];
+  return gx * gx + gy * gy + gz * gz;
+}
+
+template <typename T> struct CT { T x, y; };
+
+template <typename T>
+int upload_coeff(ltmp2_ctx *c, const double *coeff, int n_pw, int row0, int rows,
+                 const std::vector<int> &order, void **dst) {
+  std::vector<CT<T>> h((size_t)rows * n_pw);
+  for (int r = 0; r < rows; ++r)
+    for (int q = 0; q < n_pw; ++q) {
+      const double *src = coeff + ((size_t)(row0 + r) * n_pw + order[q]) * 2;
+      h[(size_t)r * n_pw + q] = {(T)src[0], (T)src[1]};
+    }
+  int rc = dalloc_bytes(c, dst, h.size() * sizeof(CT<T>));
+  if (rc) return rc;
+  return cuda_status(cudaMemcpy(*dst, h.data(), h.size() * sizeof(CT<T>), cudaMemcpyHostToDevice));
+}
+
+template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys, const std::vector<int> &order) {
+  Plan &p = c->p;
+  cudaError_t e = Path<T>::init_device();
+  if (e != cudaSuccess) return cuda_status(e);
+  const size_t cs = sizeof(CT<T>);
+  const size_t n3 = (size_t)p.n * p.n * p.n;
+  int rc;
+  if ((rc = upload_coeff<T>(c, sys->coeff, p.n_pw, p.n_occ, p.n_v, order, &p.cv))) return rc;
+  void *cocc = nullptr;
+  if ((rc = upload_coeff<T>(c, sys->coeff, p.n_pw, 0, p.n_occ, order, &cocc))) return rc;
+  if ((rc = dalloc_bytes(c, &p.cgrid, cs * n3 * p.n_occ))) return rc;
+  if ((rc = dalloc_bytes(c, &p.u, cs * n3 * p.n_occ))) return rc;
+  if ((rc = dalloc_bytes(c, &p.dscale, sizeof(T) * p.n_orb))) return rc;
+  if ((rc = dalloc_bytes(c, &p.pt, cs * (size_t)p.n_pw * p.n_pw))) return rc;
+  // slab capacity from the free memory
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const int spp = p.slots_per_prim();
+  const size_t cols_pp = (size_t)spp * p.n_occ;
+  const size_t per_prim = cs * cols_pp * (2 * (size_t)p.n_pw + (size_t)p.n * p.n_dorb +
+                                          (size_t)p.n_occ * p.n * p.n_daux) +
+                          cs * spp * (size_t)p.n_aux * p.n_occ + 2 * sizeof(double2) * (size_t)p.n_occ * p.n_occ;
+  size_t budget = std::min<size_t>(free_b / 3, (size_t)16 << 30);
+  long long mp = (long long)(budget / std::max<size_t>(per_prim, 1));
+  const long long by_cols = std::max<long long>(1, 4096 / (long long)cols_pp);
+  mp = std::min<long long>(mp, by_cols);
+  mp = std::min<long long>(mp, p.n_prim);
+  if (mp < 1) mp = 1;
+  p.max_prim = (int)mp;
+  c->slab_capacity = p.max_prim;
+  const size_t max_cols = cols_pp * p.max_prim;
+  if ((rc = dalloc_bytes(c, &p.st, cs * max_cols * p.n_pw))) return rc;
+  if ((rc = dalloc_bytes(c, &p.wt, cs * max_cols * p.n_pw))) return rc;
+  if ((rc = dalloc_bytes(c, &p.z1, cs * std::max(max_cols, (size_t)p.n_occ) * p.n * p.n_dorb))) return rc;
+  if ((rc = dalloc_bytes(c, &p.tbuf, cs * max_cols * p.n_occ * p.n * p.n_daux))) return rc;
+  if ((rc = dalloc_bytes(c, &p.mdiag, cs * (size_t)spp * p.max_prim * p.n_aux * p.n_occ))) return rc;
+  if ((rc = dalloc(c, &p.sx, (size_t)p.max_prim * p.n_occ * p.n_occ))) return rc;
+  if ((rc = dalloc(c, &p.yd, (size_t)p.max_prim * p.n_occ * p.n_occ))) return rc;
+  e = Path<T>::setup_occupied(p, cocc, c->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaStreamSynchronize(c->stream);
+  return cuda_status(e);
+}
+
+template <typename T>
+int run_energy(ltmp2_ctx *c, int n_tau, const double *tau, const double *w, int gp_begin, int gp_end) {
+  Plan &p = c->p;
+  StageTimer *tm = c->timer.on ? &c->timer : nullptr;
+  c->timer.stream = c->stream;
+  cudaError_t e = Path<T>::zero_acc(p, c->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  const double nfft = (double)p.n * p.n * p.n;
+  for (int k = 0; k < n_tau; ++k) {
+    e = Path<T>::green(p, tau[k], c->stream, tm);
+    if (e != cudaSuccess) return cuda_status(e);
+    const double coef = w[k] / (p.omega * p.omega * nfft * nfft);
+    for (int g0 = gp_begin; g0 < gp_end; g0 += p.max_prim) {
+      const int np = std::min(p.max_prim, gp_end - g0);
+      e = Path<T>::slab(p, g0, np, coef, c->stream, tm);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+  }
+  e = Path<T>::finish(p, c->stream, tm);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaStreamSynchronize(c->stream);
+  if (tm) c->timer.collect();
+  return cuda_status(e);
+}
+
+int check_tau(int n_tau, const double *tau, const double *w) {
+  if (n_tau < 1 || !tau || !w) return LTMP2_ERR_INVALID_ARG;
+  for (int k = 0; k < n_tau; ++k)
+    if (!(tau[k] > 0.0) || !std::isfinite(tau[k]) || !std::isfinite(w[k])) return LTMP2_ERR_INVALID_ARG;
+  return LTMP2_OK;
+}
+
+int energy_common(ltmp2_ctx *ctx, int n_tau, const double *tau, const double *w, int gp_begin, int gp_end,
+                  double *e_d, double *e_x, std::vector<double> *ed_pair, std::vector<double> *ex_pair) {
+  if (!ctx) return LTMP2_ERR_INVALID_ARG;
+  int rc = check_tau(n_tau, tau, w);
+  if (rc) return rc;
+  if (gp_begin < 0 || gp_end > ctx->p.n_prim || gp_begin > gp_end) return LTMP2_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  rc = ctx->p.precision == LTMP2_FP64 ? run_energy<double>(ctx, n_tau, tau, w, gp_begin, gp_end)
+                                      : run_energy<float>(ctx, n_tau, tau, w, gp_begin, gp_end);
+  if (rc) return rc;
+  double es[4];
+  cudaError_t e = cudaMemcpy(es, ctx->p.esum, sizeof(es), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  const size_t no2 = (size_t)ctx->p.n_occ * ctx->p.n_occ;
+  if (ed_pair) {
+    ed_pair->resize(no2);
+    e = cudaMemcpy(ed_pair->data(), ctx->p.ed, no2 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  if (ex_pair) {
+    ex_pair->resize(no2);
+    e = cudaMemcpy(ex_pair->data(), ctx->p.ex, no2 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  ctx->last_imag[0] = es[2];
+  ctx->last_imag[1] = es[3];
+  if (e_d) *e_d = es[0];
+  if (e_x) *e_x = es[1];
+  return LTMP2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ltmp2_strerror(int code) {
+  switch (code) {
+    case LTMP2_OK: return "success";
+    case LTMP2_ERR_INVALID_ARG: return "invalid argument";
+    case LTMP2_ERR_GAP: return "HOMO-LUMO gap below 1e-6 Ha";
+    case LTMP2_ERR_NOT_ORTHONORMAL: return "orbitals are not orthonormal";
+    case LTMP2_ERR_GRID: return "unsupported FFT grid or plane-wave set";
+    case LTMP2_ERR_OOM: return "device memory exhausted";
+    case LTMP2_ERR_CUDA: return "CUDA error";
+    case LTMP2_ERR_TIMEOUT: return "device wait timed out";
+    case LTMP2_ERR_UNSUPPORTED: return "unsupported option";
+    case LTMP2_ERR_NO_CONVERGENCE: return "Laplace grid fit did not converge";
+    case LTMP2_ERR_NOT_REAL: return "orbitals are not real in real space";
+    default: return "unknown status";
+  }
+}
+
+int ltmp2_setup(const ltmp2_system *sys, ltmp2_ctx **out) {
+  if (!sys || !out) return LTMP2_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!sys->miller || !sys->coeff || !sys->eps) return LTMP2_ERR_INVALID_ARG;
+  if (sys->n_pw < 2 || sys->n_orb < 2 || sys->n_occ < 1 || sys->n_occ >= sys->n_orb || sys->n_orb > sys->n_pw)
+    return LTMP2_ERR_INVALID_ARG;
+  if (sys->precision != LTMP2_FP64 && sys->precision != LTMP2_FP32) return LTMP2_ERR_INVALID_ARG;
+  if (sys->flags & ~LTMP2_FLAG_REAL_ORBITALS) return LTMP2_ERR_INVALID_ARG;
+  for (int k = 0; k < 9; ++k)
+    if (!std::isfinite(sys->lattice[k])) return LTMP2_ERR_INVALID_ARG;
+  const int n = sys->grid[0];
+  if (sys->grid[1] != n || sys->grid[2] != n || !fft_size_supported(n)) return LTMP2_ERR_GRID;
+  // eigenvalues
+  for (int k = 0; k < sys->n_orb; ++k) {
+    if (!std::isfinite(sys->eps[k])) return LTMP2_ERR_INVALID_ARG;
+    if (k > 0 && sys->eps[k] < sys->eps[k - 1]) return LTMP2_ERR_INVALID_ARG;
+  }
+  const int no = sys->n_occ, npw = sys->n_pw, norb = sys->n_orb;
+  if (sys->eps[no] - sys->eps[no - 1] < 1e-6) return LTMP2_ERR_GAP;
+  double B[9], omega;
+  reciprocal(sys->lattice, B, &omega);
+  if (!(omega > 0.0) || !std::isfinite(omega)) return LTMP2_ERR_INVALID_ARG;
+  // plane-wave set
+  std::vector<std::array<int, 3>> m(npw);
+  std::map<std::array<int, 3>, int> where;
+  double g2max = 0.0;
+  for (int q = 0; q < npw; ++q) {
+    for (int k = 0; k < 3; ++k) {
+      m[q][k] = sys->miller[3 * q + k];
+      if (2 * std::abs(m[q][k]) >= n) return LTMP2_ERR_GRID;
+    }
+    if (!where.emplace(m[q], q).second) return LTMP2_ERR_INVALID_ARG;
+    g2max = std::max(g2max, g2_of(B, m[q][0], m[q][1], m[q][2]));
+  }
+  std::vector<int> negpw(npw);
+  for (int q = 0; q < npw; ++q) {
+    auto it = where.find({-m[q][0], -m[q][1], -m[q][2]});
+    if (it == where.end()) return LTMP2_ERR_GRID;
+    negpw[q] = it->second;
+  }
+  std::vector<Col> ocols;
+  std::vector<int> order;
+  if (!build_columns(m, ocols, order)) return LTMP2_ERR_GRID;
+  // orthonormality on a deterministic sample of orbitals
+  {
+    std::vector<int> pick;
+    const int S = std::min(norb, 40);
+    for (int s = 0; s < S; ++s) pick.push_back((int)((long long)s * (norb - 1) / std::max(1, S - 1)));
+    pick.push_back(no - 1);
+    pick.push_back(no);
+    std::sort(pick.begin(), pick.end());
+    pick.erase(std::unique(pick.begin(), pick.end()), pick.end());
+    for (size_t a = 0; a < pick.size(); ++a)
+      for (size_t b = a; b < pick.size(); ++b) {
+        const double *ca = sys->coeff + (size_t)pick[a] * npw * 2, *cb = sys->coeff + (size_t)pick[b] * npw * 2;
+        double re = 0, im = 0;
+        for (int q = 0; q < npw; ++q) {
+          re += ca[2 * q] * cb[2 * q] + ca[2 * q + 1] * cb[2 * q + 1];
+          im += ca[2 * q] * cb[2 * q + 1] - ca[2 * q + 1] * cb[2 * q];
+        }
+        if (!std::isfinite(re) || !std::isfinite(im)) return LTMP2_ERR_INVALID_ARG;
+        if (std::fabs(re - (a == b ? 1.0 : 0.0)) > 1e-8 || std::fabs(im) > 1e-8) return LTMP2_ERR_NOT_ORTHONORMAL;
+      }
+  }
+  const bool real_orb = (sys->flags & LTMP2_FLAG_REAL_ORBITALS) != 0;
+  if (real_orb) {
+    for (int r = 0; r < norb; ++r) {
+      const double *c = sys->coeff + (size_t)r * npw * 2;
+      for (int q = 0; q < npw; ++q) {
+        const int qn = negpw[q];
+        if (std::fabs(c[2 * q] - c[2 * qn]) > 1e-10 || std::fabs(c[2 * q + 1] + c[2 * qn + 1]) > 1e-10)
+          return LTMP2_ERR_NOT_REAL;
+      }
+    }
+  }
+  // auxiliary set A (Sec. II A) in column order, v(G) = 4 pi / |G|^2 (Eq. SCH2EI)
+  const double ecut_aux = sys->ecut_aux > 0.0 ? sys->ecut_aux : (2.0 / 3.0) * 0.5 * g2max;
+  std::vector<std::array<int, 3>> am;
+  {
+    const double gmax = std::sqrt(2.0 * ecut_aux);
+    int lim[3];
+    for (int k = 0; k < 3; ++k) {
+      const double an = std::sqrt(sys->lattice[3 * k] * sys->lattice[3 * k] +
+                                  sys->lattice[3 * k + 1] * sys->lattice[3 * k + 1] +
+                                  sys->lattice[3 * k + 2] * sys->lattice[3 * k + 2]);
+      lim[k] = (int)std::floor(gmax * an / 6.283185307179586476925286766559) + 1;
+    }
+    for (int a = -lim[0]; a <= lim[0]; ++a)
+      for (int b = -lim[1]; b <= lim[1]; ++b)
+        for (int d = -lim[2]; d <= lim[2]; ++d) {
+          const double g2 = g2_of(B, a, b, d);
+          // G = 0 is kept as a table entry with v(0) := 0 so that every column of the
+          // sphere is one contiguous m3 range; it never contributes.
+          if (0.5 * g2 <= ecut_aux) {
+            if (2 * std::abs(a) >= n || 2 * std::abs(b) >= n || 2 * std::abs(d) >= n) return LTMP2_ERR_GRID;
+            am.push_back({a, b, d});
+          }
+        }
+  }
+  if (am.size() < 3) return LTMP2_ERR_INVALID_ARG;
+  std::vector<Col> acols;
+  std::vector<int> aorder;
+  if (!build_columns(am, acols, aorder)) return LTMP2_ERR_GRID;
+  const int naux = (int)am.size();
+  std::vector<std::array<int, 3>> amo(naux);
+  for (int k = 0; k < naux; ++k) amo[k] = am[aorder[k]];
+  std::map<std::array<int, 3>, int> awhere;
+  for (int k = 0; k < naux; ++k) awhere[amo[k]] = k;
+  std::vector<int> aneg(naux), prim;
+  std::vector<double> v64(naux);
+  std::vector<float> v32(naux);
+  for (int k = 0; k < naux; ++k) {
+    auto it = awhere.find({-amo[k][0], -amo[k][1], -amo[k][2]});
+    if (it == awhere.end()) return LTMP2_ERR_GRID;
+    aneg[k] = it->second;
+    const double g2 = g2_of(B, amo[k][0], amo[k][1], amo[k][2]);
+    v64[k] = (g2 > 0.0) ? 12.566370614359172953850573533118 / g2 : 0.0;
+    v32[k] = (float)v64[k];
+    const int first = amo[k][0] != 0 ? amo[k][0] : (amo[k][1] != 0 ? amo[k][1] : amo[k][2]);
+    if (first > 0) prim.push_back(k);
+  }
+
+  ltmp2_ctx *c = new (std::nothrow) ltmp2_ctx();
+  if (!c) return LTMP2_ERR_OOM;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return LTMP2_ERR_CUDA;
+  }
+  Plan &p = c->p;
+  p.n = n;
+  p.n_occ = no;
+  p.n_orb = norb;
+  p.n_pw = npw;
+  p.n_v = norb - no;
+  p.n_dorb = (int)ocols.size();
+  p.n_daux = (int)acols.size();
+  p.n_aux = naux;
+  p.n_prim = (int)prim.size();
+  p.real_orb = real_orb;
+  p.precision = sys->precision;
+  p.omega = omega;
+  p.mu = 0.5 * (sys->eps[no - 1] + sys->eps[no]);
+  p.mxlo_orb = ocols.front().m1;
+  p.mxhi_orb = ocols.back().m1;
+  p.mxlo_aux = acols.front().m1;
+  p.mxhi_aux = acols.back().m1;
+  std::vector<int4> hdorb(p.n_dorb), hdaux(p.n_daux);
+  std::vector<int> hdorb_off(p.n_dorb), hdaux_off(p.n_daux), hpw(3 * (size_t)npw), haux(3 * (size_t)naux);
+  for (int d = 0; d < p.n_dorb; ++d) {
+    hdorb[d] = make_int4(ocols[d].m1, ocols[d].m2, ocols[d].zlo, ocols[d].zhi);
+    hdorb_off[d] = ocols[d].off;
+  }
+  for (int d = 0; d < p.n_daux; ++d) {
+    hdaux[d] = make_int4(acols[d].m1, acols[d].m2, acols[d].zlo, acols[d].zhi);
+    hdaux_off[d] = acols[d].off;
+  }
+  for (int q = 0; q < npw; ++q)
+    for (int k = 0; k < 3; ++k) hpw[3 * q + k] = m[order[q]][k];
+  for (int q = 0; q < naux; ++q)
+    for (int k = 0; k < 3; ++k) haux[3 * q + k] = amo[q][k];
+  int rc = LTMP2_OK;
+  auto up = [&](auto **dptr, const auto &vec) -> int {
+    using X = typename std::remove_reference<decltype(vec)>::type::value_type;
+    int r = dalloc(c, dptr, vec.size());
+    if (r) return r;
+    return cuda_status(cudaMemcpy(*dptr, vec.data(), vec.size() * sizeof(X), cudaMemcpyHostToDevice));
+  };
+  std::vector<double> heps(sys->eps, sys->eps + norb);
+  if (!rc) rc = up(&p.dorb, hdorb);
+  if (!rc) rc = up(&p.dorb_off, hdorb_off);
+  if (!rc) rc = up(&p.daux, hdaux);
+  if (!rc) rc = up(&p.daux_off, hdaux_off);
+  if (!rc) rc = up(&p.pw_m, hpw);
+  if (!rc) rc = up(&p.aux_m, haux);
+  if (!rc) rc = up(&p.aux_neg, aneg);
+  if (!rc) rc = up(&p.prim, prim);
+  if (!rc) rc = up(&p.v_aux64, v64);
+  if (!rc) rc = up(&p.v_aux32, v32);
+  if (!rc) rc = up(&p.eps, heps);
+  const size_t no2 = (size_t)no * no;
+  if (!rc) rc = dalloc(c, &p.ex, no2);
+  if (!rc) rc = dalloc(c, &p.ed, no2);
+  if (!rc) rc = dalloc(c, &p.exi, no2);
+  if (!rc) rc = dalloc(c, &p.edi, no2);
+  if (!rc) rc = dalloc(c, &p.esum, 4);
+  if (!rc)
+    rc = (sys->precision == LTMP2_FP64) ? setup_precision<double>(c, sys, order)
+                                        : setup_precision<float>(c, sys, order);
+  if (rc) {
+    cudaGetLastError();
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return LTMP2_OK;
+}
+
+int ltmp2_set_stream(ltmp2_ctx *ctx, void *stream) {
+  if (!ctx) return LTMP2_ERR_INVALID_ARG;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return LTMP2_OK;
+}
+
+int ltmp2_energy(ltmp2_ctx *ctx, int n_tau, const double *tau, const double *w, double *e_direct,
+                 double *e_exchange, double *e_pair) {
+  if (!ctx || !e_direct || !e_exchange) return LTMP2_ERR_INVALID_ARG;
+  std::vector<double> ed, ex;
+  int rc = energy_common(ctx, n_tau, tau, w, 0, ctx->p.n_prim, e_direct, e_exchange, e_pair ? &ed : nullptr,
+                         e_pair ? &ex : nullptr);
+  if (rc) return rc;
+  if (e_pair)
+    for (size_t k = 0; k < ed.size(); ++k) e_pair[k] = ed[k] + ex[k];
+  return LTMP2_OK;
+}
+
+int ltmp2_energy_partial(ltmp2_ctx *ctx, int n_tau, const double *tau, const double *w, int gp_begin,
+                         int gp_end, double *e_direct, double *e_exchange, double *e_pair_direct,
+                         double *e_pair_exchange) {
+  if (!ctx || !e_direct || !e_exchange) return LTMP2_ERR_INVALID_ARG;
+  std::vector<double> ed, ex;
+  int rc = energy_common(ctx, n_tau, tau, w, gp_begin, gp_end, e_direct, e_exchange,
+                         e_pair_direct ? &ed : nullptr, e_pair_exchange ? &ex : nullptr);
+  if (rc) return rc;
+  if (e_pair_direct) std::memcpy(e_pair_direct, ed.data(), ed.size() * sizeof(double));
+  if (e_pair_exchange) std::memcpy(e_pair_exchange, ex.data(), ex.size() * sizeof(double));
+  return LTMP2_OK;
+}
+
+int ltmp2_set_slab_size(ltmp2_ctx *ctx, int n) {
+  if (!ctx) return LTMP2_ERR_INVALID_ARG;
+  if (n > ctx->slab_capacity) return LTMP2_ERR_INVALID_ARG;
+  ctx->p.max_prim = (n <= 0) ? ctx->slab_capacity : n;
+  return ctx->p.max_prim;
+}
+
+int ltmp2_num_primary_gprime(const ltmp2_ctx *ctx) { return ctx ? ctx->p.n_prim : LTMP2_ERR_INVALID_ARG; }
+
+int ltmp2_sizes(const ltmp2_ctx *ctx, int *n_aux, int *n_pw, int *n_occ, int *grid_n) {
+  if (!ctx) return LTMP2_ERR_INVALID_ARG;
+  if (n_aux) *n_aux = ctx->p.n_aux - 1;  // the internal table carries G = 0 with v = 0
+  if (n_pw) *n_pw = ctx->p.n_pw;
+  if (n_occ) *n_occ = ctx->p.n_occ;
+  if (grid_n) *grid_n = ctx->p.n;
+  return LTMP2_OK;
+}
+
+int ltmp2_last_imag(const ltmp2_ctx *ctx, double *im_direct, double *im_exchange) {
+  if (!ctx) return LTMP2_ERR_INVALID_ARG;
+  if (im_direct) *im_direct = ctx->last_imag[0];
+  if (im_exchange) *im_exchange = ctx->last_imag[1];
+  return LTMP2_OK;
+}
+
+int ltmp2_set_profiling(ltmp2_ctx *ctx, int on) {
+  if (!ctx) return LTMP2_ERR_INVALID_ARG;
+  ctx->timer.on = (on != 0);
+  return LTMP2_OK;
+}
+
+int ltmp2_stage_times(const ltmp2_ctx *ctx, int n, double *ms, long long *launches) {
+  if (!ctx || n < 0) return LTMP2_ERR_INVALID_ARG;
+  for (int s = 0; s < std::min(n, LTMP2_NUM_STAGES); ++s) {
+    if (ms) ms[s] = ctx->timer.ms[s];
+    if (launches) launches[s] = ctx->timer.launches[s];
+  }
+  return LTMP2_OK;
+}
+
+int ltmp2_reset_stage_times(ltmp2_ctx *ctx) {
+  if (!ctx) return LTMP2_ERR_INVALID_ARG;
+  for (int s = 0; s < LTMP2_NUM_STAGES; ++s) {
+    ctx->timer.ms[s] = 0;
+    ctx->timer.launches[s] = 0;
+  }
+  return LTMP2_OK;
+}
+
+void ltmp2_destroy(ltmp2_ctx *ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// Launchers of the hot path for one real type T.  Included once per precision by
+// kernels_f64.cu / kernels_f32.cu, which explicitly instantiate Path<T>.
+#pragma once
+#include "kernels.cuh"
+
+namespace ltmp2 {
+
+#define LTMP2_FOR_EACH_N(X) X(8) X(10) X(12) X(16) X(18) X(20) X(24) X(25) X(27) X(30) X(32) X(36) X(40)
+
+template <typename T> static int plane_ib(int n, int n_occ) {
+  // occupied planes per plane-kernel block: about 96 KB of shared memory
+  const size_t plane = (size_t)n * (n + 1) * sizeof(cpx<T>);
+  int ib = (int)((96 * 1024) / plane) - 1;
+  if (ib < 1) ib = 1;
+  if (ib > 8) ib = 8;
+  if (ib > n_occ) ib = n_occ;
+  return ib;
+}
+
+struct ScopedStage {
+  StageTimer *tm;
+  int st;
+  ScopedStage(StageTimer *t, int s) : tm(t), st(s) { if (tm) tm->begin(st); }
+  ~ScopedStage() { if (tm) tm->end(st); }
+};
+
+template <typename T> cudaError_t Path<T>::init_device() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && done[dev]) return cudaSuccess;
+  e = upload_twiddles();
+  if (e != cudaSuccess) return e;
+  // dynamic shared memory limits of the FFT kernels
+#define LTMP2_SET_SMEM(NN)                                                                          \
+  e = cudaFuncSetAttribute(k_planes<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
+  if (e != cudaSuccess) return e;                                                                   \
+  e = cudaFuncSetAttribute(k_zcol<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);   \
+  if (e != cudaSuccess) return e;
+  LTMP2_FOR_EACH_N(LTMP2_SET_SMEM)
+#undef LTMP2_SET_SMEM
+  if (dev < 64) done[dev] = true;
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t Path<T>::setup_occupied(const Plan &p, const void *c_occ_dev, cudaStream_t st) {
+  const int n = p.n;
+  const size_t n3 = (size_t)n * n * n;
+  cudaError_t e = cudaMemsetAsync(p.cgrid, 0, sizeof(cpx<T>) * n3 * p.n_occ, st);
+  if (e != cudaSuccess) return e;
+  const cpx<T> *c = (const cpx<T> *)c_occ_dev;
+  k_scatter_grid<T><<<dim3((p.n_pw + 255) / 256, p.n_occ), 256, 0, st>>>(p, p.n_occ, c, (cpx<T> *)p.cgrid);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // z1 scratch: reuse p.z1 when it is large enough (max_cols >= n_occ always holds)
+  cpx<T> *z1 = (cpx<T> *)p.z1;
+  const size_t smem = (size_t)n * (n + 1) * sizeof(cpx<T>);
+  switch (n) {
+#define LTMP2_CASE(NN)                                                                            \
+  case NN:                                                                                        \
+    k_w_zinv<T, NN><<<dim3((p.n_dorb + 127) / 128, p.n_occ), 128, 0, st>>>(p, p.n_pw, c, z1);     \
+    k_planes_store<T, NN><<<dim3(NN, p.n_occ), 128, smem, st>>>(p, z1, (cpx<T> *)p.u);            \
+    break;
+    LTMP2_FOR_EACH_N(LTMP2_CASE)
+#undef LTMP2_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Path<T>::green(const Plan &p, double tau, cudaStream_t st, StageTimer *tm) {
+  ScopedStage s(tm, kStageGreen);
+  k_dscale<T><<<(p.n_orb + 255) / 256, 256, 0, st>>>(p.n_orb, p.n_occ, p.eps, p.mu, tau, (T *)p.dscale);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // P^T[q][p] = sum_a conj(c_a(q)) e^{-(e_a-mu)tau} c_a(p)
+  const int M = p.n_pw, N = p.n_pw, K = p.n_v;
+  dim3 grid((N + 63) / 64, (M + 63) / 64);
+  k_cgemm<T, false, true><<<grid, 256, 0, st>>>(M, N, K, (const cpx<T> *)p.cv, p.n_pw,
+                                                (const cpx<T> *)p.cv, p.n_pw,
+                                                (const T *)p.dscale + p.n_occ, (cpx<T> *)p.pt, p.n_pw);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStream_t st, StageTimer *tm) {
+  const int n = p.n, no = p.n_occ;
+  const int nslots = np * p.slots_per_prim();
+  const int ncols = nslots * no;
+  cudaError_t e;
+  {
+    ScopedStage s(tm, kStageGatherZ);
+    k_gather_s<T><<<dim3((p.n_pw + 255) / 256, ncols), 256, 0, st>>>(p, gp0, np, (cpx<T> *)p.st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  {
+    ScopedStage s(tm, kStageWGemm);
+    dim3 grid((p.n_pw + 63) / 64, (ncols + 63) / 64);
+    k_cgemm<T, true, false><<<grid, 256, 0, st>>>(ncols, p.n_pw, p.n_pw, (const cpx<T> *)p.st, p.n_pw,
+                                                  (const cpx<T> *)p.pt, p.n_pw, nullptr,
+                                                  (cpx<T> *)p.wt, p.n_pw);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const int ib = plane_ib<T>(n, no);
+  const size_t smem_plane = (size_t)n * (n + 1) * sizeof(cpx<T>) * (1 + ib);
+  const size_t smem_col = (size_t)p.n_aux * sizeof(cpx<T>);
+  const int npairs = p.real_orb ? np * (no * (no + 1) / 2) : np * no * no;
+  int col_threads = ((p.n_daux + 31) / 32) * 32;
+  if (col_threads > 512) col_threads = 512;
+  int plane_threads = ib * n;
+  if (plane_threads < 64) plane_threads = 64;
+  switch (n) {
+#define LTMP2_CASE(NN)                                                                                  \
+  case NN: {                                                                                            \
+    {                                                                                                   \
+      ScopedStage s(tm, kStageGatherZ);                                                                 \
+      k_w_zinv<T, NN><<<dim3((p.n_dorb + 127) / 128, ncols), 128, 0, st>>>(p, p.n_pw,                    \
+                                                                          (const cpx<T> *)p.wt,          \
+                                                                          (cpx<T> *)p.z1);               \
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;                                            \
+    }                                                                                                   \
+    {                                                                                                   \
+      ScopedStage s(tm, kStagePlane);                                                                   \
+      k_planes<T, NN><<<dim3(NN, ncols), plane_threads, smem_plane, st>>>(p, ib, (const cpx<T> *)p.z1,  \
+                                                                          (cpx<T> *)p.tbuf);            \
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;                                            \
+    }                                                                                                   \
+    {                                                                                                   \
+      ScopedStage s(tm, kStageColumn);                                                                  \
+      k_zcol<T, NN><<<npairs, col_threads, smem_col, st>>>(p, gp0, np, (const cpx<T> *)p.tbuf,          \
+                                                           (cpx<T> *)p.mdiag, p.sx);                    \
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;                                            \
+    }                                                                                                   \
+  } break;
+    LTMP2_FOR_EACH_N(LTMP2_CASE)
+#undef LTMP2_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  {
+    ScopedStage s(tm, kStageDirect);
+    int th = no < 128 ? ((no + 31) / 32) * 32 : 128;
+    k_direct<T><<<dim3(np, no), th, 0, st>>>(p, np, (const cpx<T> *)p.mdiag, p.yd);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  {
+    ScopedStage s(tm, kStageAccum);
+    k_accum<<<(no * no + 127) / 128, 128, 0, st>>>(p, gp0, np, coef, p.sx, p.yd);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T> cudaError_t Path<T>::zero_acc(const Plan &p, cudaStream_t st) {
+  k_zero_acc<<<(p.n_occ * p.n_occ + 255) / 256, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename T> cudaError_t Path<T>::finish(const Plan &p, cudaStream_t st, StageTimer *tm) {
+  ScopedStage s(tm, kStageAccum);
+  k_finish<<<1, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace ltmp2

@@ -1,0 +1,83 @@
+// Internal description of one set-up system: sizes, device index tables and
+// device buffers.  Shared by the host driver and the per-precision kernel units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+
+namespace ltmp2 {
+
+// One column of a plane-wave sphere at fixed (m1, m2): m3 runs over [zlo, zhi].
+// Columns are stored in order; the sphere's points follow column by column
+// (m3 ascending), starting at col_off[c].
+struct Plan {
+  int n = 0;                 // FFT grid points per axis (cubic grid)
+  int n_occ = 0, n_orb = 0, n_pw = 0, n_v = 0;
+  int n_dorb = 0;            // orbital-sphere columns
+  int n_daux = 0;            // aux-sphere columns
+  int n_aux = 0;             // |A|
+  int n_prim = 0;            // primary G' (first non-zero Miller index > 0)
+  int mxlo_orb = 0, mxhi_orb = 0, mxlo_aux = 0, mxhi_aux = 0;
+  bool real_orb = false;
+  int precision = 0;         // 0 = FP64, 1 = FP32
+  double omega = 0.0, mu = 0.0;
+
+  // device index tables
+  int4 *dorb = nullptr;      // [n_dorb] (m1, m2, zlo, zhi)
+  int *dorb_off = nullptr;   // [n_dorb]
+  int4 *daux = nullptr;      // [n_daux]
+  int *daux_off = nullptr;   // [n_daux]
+  int *pw_m = nullptr;       // [n_pw * 3] Miller indices of the orbital sphere, internal order
+  int *aux_m = nullptr;      // [n_aux * 3]
+  int *aux_neg = nullptr;    // [n_aux] position of -G in A
+  int *prim = nullptr;       // [n_prim] position in A of each primary G'
+  double *v_aux64 = nullptr; // [n_aux] 4 pi / |G|^2
+  float *v_aux32 = nullptr;
+  double *eps = nullptr;     // [n_orb] (device)
+
+  // precision-dependent device data (cpx<T>)
+  void *cv = nullptr;        // [n_v][n_pw] virtual coefficients, internal order
+  void *cgrid = nullptr;     // [n_occ][n^3] occupied coefficients scattered on the grid
+  void *u = nullptr;         // [n_occ][n^3] occupied orbitals in real space, [z][y][x]
+  void *dscale = nullptr;    // [n_orb] T: virtual e^{-(e_a-mu)tau}, occupied e^{(e_j-mu)tau}
+  void *pt = nullptr;        // [n_pw][n_pw] transposed Green's function P^T
+  void *st = nullptr;        // [max_cols][n_pw] gathered, scaled e^{-iG'r}|j> (S^T)
+  void *wt = nullptr;        // [max_cols][n_pw] transformed states W^T
+  void *z1 = nullptr;        // [max_cols][n][n_dorb] W after the inverse z transform
+  void *tbuf = nullptr;      // [max_cols * n_occ][n][n_daux] co-densities after the xy transform
+  void *mdiag = nullptr;     // [max_slots][n_aux][n_occ] diagonal co-densities M_ii(G;G')
+  double2 *sx = nullptr;     // [max_prim][n_occ][n_occ] exchange pair sums X_ij(G')
+  double2 *yd = nullptr;     // [max_prim][n_occ][n_occ] direct pair sums Y_ij(G')
+  double *ex = nullptr, *ed = nullptr, *exi = nullptr, *edi = nullptr;  // [n_occ][n_occ]
+  double *esum = nullptr;    // [4]: E_d, E_x, imag parts
+  int max_prim = 0;          // primary G' per slab (capacity)
+  int slots_per_prim() const { return real_orb ? 1 : 2; }
+};
+
+// Per-stage profiler hooks (host).  begin/end bracket one kernel launch.
+struct StageTimer {
+  virtual void begin(int stage) = 0;
+  virtual void end(int stage) = 0;
+  virtual ~StageTimer() {}
+};
+
+enum Stage {
+  kStageGreen = 0, kStageWGemm = 1, kStageGatherZ = 2, kStagePlane = 3,
+  kStageColumn = 4, kStageDirect = 5, kStageAccum = 6
+};
+
+// Per-precision entry points (kernels_f64.cu / kernels_f32.cu)
+template <typename T> struct Path {
+  static cudaError_t init_device();
+  // setup: occupied orbitals -> u (real space) and cgrid
+  static cudaError_t setup_occupied(const Plan &p, const void *c_occ_dev, cudaStream_t st);
+  // one tau: scale factors and Green's function P^T
+  static cudaError_t green(const Plan &p, double tau, cudaStream_t st, StageTimer *tm);
+  // one slab of primary G' [gp0, gp0 + np): everything up to the pair sums, then accumulate
+  static cudaError_t slab(const Plan &p, int gp0, int np, double coef, cudaStream_t st,
+                          StageTimer *tm);
+  // zero accumulators / final reduction
+  static cudaError_t zero_acc(const Plan &p, cudaStream_t st);
+  static cudaError_t finish(const Plan &p, cudaStream_t st, StageTimer *tm);
+};
+
+}  // namespace ltmp2

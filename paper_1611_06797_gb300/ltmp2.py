@@ -1,0 +1,234 @@
+"""ctypes binding of libltmp2 (include/ltmp2.h), one Python function per C entry point.
+
+Argument marshalling only.  A missing library raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libltmp2.so")
+
+FP64 = 0
+FP32 = 1
+FLAG_REAL_ORBITALS = 1
+NUM_STAGES = 7
+STAGE_NAMES = ["green_gemm", "w_gemm", "gather_ztransform", "plane_fft", "column_fft_contract",
+               "direct_contract", "accumulate"]
+HARTREE_TO_MEV = 27211.386245988
+
+_ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "GAP", -3: "NOT_ORTHONORMAL", -4: "GRID", -5: "OOM",
+           -6: "CUDA", -7: "TIMEOUT", -8: "UNSUPPORTED", -9: "NO_CONVERGENCE", -10: "NOT_REAL"}
+
+
+class Ltmp2Error(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        self.name = _ERRORS.get(code, str(code))
+        super().__init__(f"{where}: {self.name} ({ltmp2_strerror(code)})")
+
+
+class _System(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_double * 9), ("grid", ctypes.c_int * 3), ("n_pw", ctypes.c_int),
+                ("miller", ctypes.POINTER(ctypes.c_int)), ("n_orb", ctypes.c_int), ("n_occ", ctypes.c_int),
+                ("coeff", ctypes.POINTER(ctypes.c_double)), ("eps", ctypes.POINTER(ctypes.c_double)),
+                ("ecut_aux", ctypes.c_double), ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library():
+    """Load libltmp2.so (built in-tree by ``paper_1611_06797_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    dp = P(ctypes.c_double)
+    vp = ctypes.c_void_p
+    sig = {
+        "ltmp2_setup": (ctypes.c_int, [P(_System), P(vp)]),
+        "ltmp2_set_stream": (ctypes.c_int, [vp, vp]),
+        "ltmp2_laplace_grid": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, dp]),
+        "ltmp2_energy": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, dp, dp, dp]),
+        "ltmp2_energy_partial": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int,
+                                                dp, dp, dp, dp]),
+        "ltmp2_num_primary_gprime": (ctypes.c_int, [vp]),
+        "ltmp2_set_slab_size": (ctypes.c_int, [vp, ctypes.c_int]),
+        "ltmp2_sizes": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
+        "ltmp2_last_imag": (ctypes.c_int, [vp, dp, dp]),
+        "ltmp2_set_profiling": (ctypes.c_int, [vp, ctypes.c_int]),
+        "ltmp2_stage_times": (ctypes.c_int, [vp, ctypes.c_int, dp, P(ctypes.c_longlong)]),
+        "ltmp2_reset_stage_times": (ctypes.c_int, [vp]),
+        "ltmp2_destroy": (None, [vp]),
+        "ltmp2_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise Ltmp2Error(code, where)
+
+
+def ltmp2_strerror(code: int) -> str:
+    return load_library().ltmp2_strerror(int(code)).decode()
+
+
+class Context:
+    """Owns one ltmp2_ctx.  Freed by ltmp2_destroy() or when garbage collected."""
+
+    def __init__(self, handle: int, n_occ: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.n_occ = n_occ
+        self._stream = None
+
+    def __del__(self):
+        try:
+            ltmp2_destroy(self)
+        except Exception:
+            pass
+
+
+def ltmp2_setup(lattice, grid, miller, coeff, eps, n_occ: int, ecut_aux: float = 0.0,
+                precision: int = FP64, flags: int = 0) -> Context:
+    lib = load_library()
+    lattice = np.ascontiguousarray(np.asarray(lattice, dtype=np.float64).reshape(9))
+    miller = np.ascontiguousarray(np.asarray(miller, dtype=np.int32).reshape(-1, 3))
+    coeff = np.ascontiguousarray(np.asarray(coeff, dtype=np.complex128))
+    eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+    s = _System()
+    s.lattice[:] = lattice.tolist()
+    s.grid[:] = [int(g) for g in np.asarray(grid).reshape(3)]
+    s.n_pw = miller.shape[0]
+    s.miller = miller.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    s.n_orb = coeff.shape[0]
+    s.n_occ = int(n_occ)
+    if coeff.shape[1] != miller.shape[0] or eps.shape[0] != coeff.shape[0]:
+        raise ValueError("coeff must be [n_orb][n_pw] and eps [n_orb]")
+    cview = coeff.view(np.float64)
+    s.coeff = _dp(cview)
+    s.eps = _dp(eps)
+    s.ecut_aux = float(ecut_aux)
+    s.precision = int(precision)
+    s.flags = int(flags)
+    h = ctypes.c_void_p()
+    _check(lib.ltmp2_setup(ctypes.byref(s), ctypes.byref(h)), "ltmp2_setup")
+    return Context(h.value, int(n_occ))
+
+
+def setup_from_solid(solid, precision: int = FP64, real: Optional[bool] = None,
+                     ecut_aux: Optional[float] = None) -> Context:
+    """ltmp2_setup for a synth.ModelSolid (E_aux = 2/3 E_cut unless given)."""
+    if ecut_aux is None:
+        ecut_aux = 2.0 * solid.ecut / 3.0
+    flags = FLAG_REAL_ORBITALS if real else 0
+    return ltmp2_setup(solid.lattice, solid.grid, solid.miller, solid.coeff, solid.eps, solid.n_occ,
+                       ecut_aux, precision, flags)
+
+
+def ltmp2_set_stream(ctx: Context, stream) -> None:
+    """stream: an int handle (cudaStream_t) or any object with ``cuda_stream`` (torch.cuda.Stream)."""
+    handle = getattr(stream, "cuda_stream", stream)
+    ctx._stream = stream
+    _check(load_library().ltmp2_set_stream(ctx.handle, ctypes.c_void_p(int(handle) if handle else 0)),
+           "ltmp2_set_stream")
+
+
+def ltmp2_laplace_grid(gap: float, width: float, n_tau: int) -> Tuple[np.ndarray, np.ndarray, float]:
+    tau = np.zeros(n_tau)
+    w = np.zeros(n_tau)
+    err = np.zeros(1)
+    _check(load_library().ltmp2_laplace_grid(float(gap), float(width), int(n_tau), _dp(tau), _dp(w), _dp(err)),
+           "ltmp2_laplace_grid")
+    return tau, w, float(err[0])
+
+
+def ltmp2_energy(ctx: Context, tau, w, pairs: bool = True):
+    """Returns (E_direct, E_exchange, e_pair[n_occ][n_occ] or None)."""
+    tau = np.ascontiguousarray(np.asarray(tau, dtype=np.float64))
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    if tau.shape != w.shape:
+        raise ValueError("tau and w must have the same length")
+    ed = np.zeros(1)
+    ex = np.zeros(1)
+    ep = np.zeros((ctx.n_occ, ctx.n_occ)) if pairs else None
+    _check(load_library().ltmp2_energy(ctx.handle, len(tau), _dp(tau), _dp(w), _dp(ed), _dp(ex),
+                                       _dp(ep) if pairs else None), "ltmp2_energy")
+    return float(ed[0]), float(ex[0]), ep
+
+
+def ltmp2_energy_partial(ctx: Context, tau, w, gp_begin: int, gp_end: int):
+    """Returns (E_d, E_x, e_pair_direct, e_pair_exchange) of primary G' in [gp_begin, gp_end)."""
+    tau = np.ascontiguousarray(np.asarray(tau, dtype=np.float64))
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    ed = np.zeros(1)
+    ex = np.zeros(1)
+    pd = np.zeros((ctx.n_occ, ctx.n_occ))
+    px = np.zeros((ctx.n_occ, ctx.n_occ))
+    _check(load_library().ltmp2_energy_partial(ctx.handle, len(tau), _dp(tau), _dp(w), int(gp_begin), int(gp_end),
+                                               _dp(ed), _dp(ex), _dp(pd), _dp(px)), "ltmp2_energy_partial")
+    return float(ed[0]), float(ex[0]), pd, px
+
+
+def ltmp2_set_slab_size(ctx: Context, n: int) -> int:
+    r = load_library().ltmp2_set_slab_size(ctx.handle, int(n))
+    if r < 0:
+        raise Ltmp2Error(r, "ltmp2_set_slab_size")
+    return r
+
+
+def ltmp2_num_primary_gprime(ctx: Context) -> int:
+    r = load_library().ltmp2_num_primary_gprime(ctx.handle)
+    if r < 0:
+        raise Ltmp2Error(r, "ltmp2_num_primary_gprime")
+    return r
+
+
+def ltmp2_sizes(ctx: Context) -> dict:
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(load_library().ltmp2_sizes(ctx.handle, *[ctypes.byref(x) for x in v]), "ltmp2_sizes")
+    return {"n_aux": v[0].value, "n_pw": v[1].value, "n_occ": v[2].value, "grid": v[3].value}
+
+
+def ltmp2_last_imag(ctx: Context) -> Tuple[float, float]:
+    a, b = np.zeros(1), np.zeros(1)
+    _check(load_library().ltmp2_last_imag(ctx.handle, _dp(a), _dp(b)), "ltmp2_last_imag")
+    return float(a[0]), float(b[0])
+
+
+def ltmp2_set_profiling(ctx: Context, on: bool) -> None:
+    _check(load_library().ltmp2_set_profiling(ctx.handle, 1 if on else 0), "ltmp2_set_profiling")
+
+
+def ltmp2_stage_times(ctx: Context) -> dict:
+    ms = np.zeros(NUM_STAGES)
+    n = (ctypes.c_longlong * NUM_STAGES)()
+    _check(load_library().ltmp2_stage_times(ctx.handle, NUM_STAGES, _dp(ms), n), "ltmp2_stage_times")
+    return {STAGE_NAMES[k]: {"ms": float(ms[k]), "launches": int(n[k])} for k in range(NUM_STAGES)}
+
+
+def ltmp2_reset_stage_times(ctx: Context) -> None:
+    _check(load_library().ltmp2_reset_stage_times(ctx.handle), "ltmp2_reset_stage_times")
+
+
+def ltmp2_destroy(ctx: Context) -> None:
+    if ctx.handle is not None and ctx.handle.value:
+        load_library().ltmp2_destroy(ctx.handle)
+        ctx.handle = ctypes.c_void_p(0)

@@ -1,0 +1,119 @@
+"""Host-side checks of the C ABI: the library loads, exports every declared entry
+point, fits the Laplace grid on the host, and rejects bad input before touching a
+device (host-side fault injection).  No GPU is needed."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1611_06797_gb300 as L
+from oracle import quadrature_max_error, sinc_laplace_quadrature
+from synth import SPECS, ModelSolidSpec, build_model_solid
+from tests.conftest import solid
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(ltmp2_\w+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = L.load_library()
+    names = _declared()
+    assert {"ltmp2_setup", "ltmp2_energy", "ltmp2_laplace_grid", "ltmp2_destroy"} <= names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_strerror_names_every_code():
+    for code in range(0, -11, -1):
+        s = L.ltmp2_strerror(code)
+        assert s and s != "unknown status"
+    assert L.ltmp2_strerror(-99) == "unknown status"
+
+
+@pytest.mark.parametrize("gap,width", [(0.0226, 13.92), (0.256, 7.3), (0.0042, 11.42)])
+def test_laplace_grid_fits_one_over_x(gap, width):
+    """Eq. SCHLT with a quadrature: the reported error is the measured one, it falls with
+    n_tau, and the fit beats the oracle's plain trapezoid rule at the same n_tau."""
+    lo, hi = 2 * gap, 2 * width
+    prev = None
+    for n in (4, 6, 8, 10):
+        tau, w, err = L.ltmp2_laplace_grid(gap, width, n)
+        assert np.all(np.diff(tau) > 0) and np.all(tau > 0)
+        meas = quadrature_max_error(tau, w, lo, hi, samples=20000)
+        assert abs(meas - err) <= 0.05 * err + 1e-12
+        t2, w2 = sinc_laplace_quadrature(n, lo, hi)
+        assert err < quadrature_max_error(t2, w2, lo, hi, samples=20000)
+        if prev is not None:
+            assert err < prev
+        prev = err
+
+
+def test_laplace_grid_rejects_bad_input():
+    for args in [(0.0, 1.0, 6), (-1.0, 1.0, 6), (0.1, 0.05, 6), (0.1, 1.0, 0), (0.1, 1.0, 25),
+                 (float("nan"), 1.0, 6)]:
+        with pytest.raises(L.Ltmp2Error) as e:
+            L.ltmp2_laplace_grid(*args)
+        assert e.value.name == "INVALID_ARG"
+
+
+# ---------------------------------------------------------------- setup validation
+def _setup(s, **over):
+    kw = dict(lattice=s.lattice, grid=s.grid, miller=s.miller, coeff=s.coeff, eps=s.eps,
+              n_occ=s.n_occ, ecut_aux=2 * s.ecut / 3, precision=L.FP64, flags=0)
+    kw.update(over)
+    return L.ltmp2_setup(**kw)
+
+
+def _expect(code, s, **over):
+    with pytest.raises(L.Ltmp2Error) as e:
+        _setup(s, **over)
+    assert e.value.name == code, e.value
+
+
+def test_setup_rejects_bad_input_before_the_device():
+    s = solid("tiny")
+    _expect("GRID", s, grid=[8, 8, 10])           # not cubic
+    _expect("GRID", s, grid=[7, 7, 7])            # not supported
+    _expect("GRID", s, grid=[6, 6, 6], miller=s.miller)  # sphere does not fit
+    eps = s.eps.copy(); eps[s.n_occ] = eps[s.n_occ - 1]
+    _expect("GAP", s, eps=eps)
+    eps = s.eps.copy(); eps[3], eps[4] = eps[4], eps[3]
+    _expect("INVALID_ARG", s, eps=eps)            # unsorted
+    eps = s.eps.copy(); eps[5] = np.nan
+    _expect("INVALID_ARG", s, eps=eps)
+    c = s.coeff.copy(); c[1] *= 1.01
+    _expect("NOT_ORTHONORMAL", s, coeff=c)
+    _expect("INVALID_ARG", s, n_occ=0)
+    _expect("INVALID_ARG", s, n_occ=s.n_orb)
+    _expect("INVALID_ARG", s, precision=7)
+    m = s.miller.copy(); m[1] = m[2]
+    _expect("INVALID_ARG", s, miller=m)           # duplicate plane wave
+    keep = np.array([not (r[0] == 3 and r[1] == 0 and r[2] == 0) for r in s.miller.tolist()])
+    _expect("GRID", s, miller=s.miller[keep], coeff=np.eye(keep.sum(), dtype=complex)[:s.n_orb - 1],
+            eps=np.sort(s.eps[:s.n_orb - 1]))    # not inversion symmetric
+
+
+def test_setup_checks_real_orbital_flag():
+    s = solid("tiny", random_phases=True)
+    _expect("NOT_REAL", s, flags=L.FLAG_REAL_ORBITALS)
+
+
+def test_setup_without_device_reports_cuda():
+    """Valid input on a host without a usable GPU stops with CUDA, never silently."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(L.Ltmp2Error) as e:
+        _setup(solid("tiny"))
+    assert e.value.name == "CUDA"
