@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the LTMP2 hot path on one GB300 (and N replicas under torchrun).
+
+Metric: seconds per E_MP2 and pair-tau contractions per second (unordered
+occupied pairs i <= j times Laplace points, per second of ltmp2_energy), on the
+seeded Gaussian-well model solid with 16 wells, a 24^3 grid, 3071 plane waves,
+32 occupied orbitals and 8 Laplace points, in the plain FP64 path.  The
+precision form (complex64 FFTs, split-precision GEMMs, FP64 sums) is timed on
+the same inputs and its error against the FP64 path is reported in meV/atom.
+
+  python bench.py [--steps K] [--warmup W] [--form fp64|fp32] [--impl ours|reference]
+
+One JSON line on stdout (rank 0).  Everything else goes to stderr.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "s per E_MP2 and pair-tau contractions/s at <=0.1 meV/atom vs FP64 plain path"
+UNIT = "pair-tau contractions/s"
+HARTREE_TO_MEV = 27211.386245988
+# Peaks: HBM and bf16 tensor from MEASURED_PEAKS.json; FP64 / FP32 ALU derived from unit
+# counts at the maximum SM clock (2 FP64 FMA and 128 FP32 FMA per SM per clock).
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+FP64_ALU_TFLOPS = 2 * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12     # 1.259
+FP32_ALU_TFLOPS = 128 * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
+
+WORKLOAD = "cfg2"
+CPU_SAMPLE_ORBITALS = (0, 1)   # oracle sample: pairs (0,0), (0,1), (1,1)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def source_sha():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1611_06797_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken
+    from the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e or e.get("source_sha") != source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU baseline (oracle)
+def cpu_worker(workload: str, orbitals, n_tau: int, reps: int = 1):
+    """Runs in a fresh process: time the FP64 oracle on a bounded sample of the workload,
+    `reps` times (nothing is cached between repetitions)."""
+    import numpy as np
+    from oracle import OracleSystem, denominator_range, laplace_denominator, mp2_energy, sinc_laplace_quadrature
+    from synth import SPECS, build_model_solid
+    s = build_model_solid(SPECS[workload])
+    o = OracleSystem.from_solid(s)
+    tau, w = sinc_laplace_quadrature(n_tau, *denominator_range(o))
+    pairs = [(i, j) for i in orbitals for j in orbitals]
+    secs = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        r = mp2_energy(o, laplace_denominator(tau, w), pairs=pairs, method="fft")
+        secs.append(time.perf_counter() - t0)
+    unordered = len(orbitals) * (len(orbitals) + 1) // 2
+    print(json.dumps({"seconds": secs, "unordered_pairs": unordered, "n_tau": n_tau,
+                      "e00": float(r["e_d"][orbitals[0], orbitals[0]] + r["e_x"][orbitals[0], orbitals[0]])}))
+
+
+def run_cpu_baseline(workload: str, n_tau: int, reps: int = 1, skip: int = 0):
+    """The oracle in a fresh process on all host cores; the first `skip` repetitions are warm-up."""
+    cores = os.cpu_count() or 1
+    env = dict(os.environ, OPENBLAS_NUM_THREADS=str(cores), OMP_NUM_THREADS=str(cores),
+               MKL_NUM_THREADS=str(cores), CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", workload, "--ntau", str(n_tau),
+           "--reps", str(reps)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("cpu baseline failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    secs = d["seconds"][skip:]
+    total = sum(secs)
+    value = d["unordered_pairs"] * d["n_tau"] * len(secs) / total
+    sample = (f"oracle (canonical MP2 with the Laplace denominator, explicit sums over i,j,a,b; numpy "
+              f"FFT overlap densities + BLAS pair integrals) for occupied orbitals {list(CPU_SAMPLE_ORBITALS)}: "
+              f"{d['unordered_pairs']} unordered pairs x {d['n_tau']} tau of the {workload} workload, "
+              f"{total / len(secs):.2f} s per sample")
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "seconds": secs, "unordered_pairs": d["unordered_pairs"]}
+
+
+# ------------------------------------------------------------------ cost model
+def stage_costs(sizes, n_prim, real, n_tau, n_v, cs):
+    """Algorithmic work per ltmp2_energy call, by stage (flops or bytes)."""
+    n_pw, n_occ = sizes["n_pw"], sizes["n_occ"]
+    spp = 1 if real else 2
+    ncols = n_prim * spp * n_occ
+    return {
+        "green_gemm": {"flops": n_tau * 8.0 * n_pw * n_pw * n_v},
+        "w_gemm": {"flops": n_tau * 8.0 * ncols * n_pw * n_pw},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-worker", default=None)
+    ap.add_argument("--ntau", type=int, default=8)
+    ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--slab", type=int, default=0, help="primary G' per slab (0 = library default)")
+    args = ap.parse_args()
+
+    if args.cpu_worker:
+        cpu_worker(args.cpu_worker, CPU_SAMPLE_ORBITALS, args.ntau, args.reps)
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from synth import SPECS
+    spec = SPECS[WORKLOAD]
+    n_tau = spec.n_tau
+    pairs = spec.n_occ * (spec.n_occ + 1) // 2
+
+    if args.impl == "reference":
+        # The reference arm: the FP64 oracle on the host cores, rank 0 only.
+        if rank != 0:
+            return
+        cb = run_cpu_baseline(WORKLOAD, n_tau, reps=args.warmup + args.steps, skip=args.warmup)
+        secs = sum(cb["seconds"])
+        value = cb["value"]
+        vals = [cb]
+        out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": {"workload": _workload_desc(spec)},
+               "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                                "sample": vals[0]["sample"]},
+               "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    import paper_1611_06797_gb300 as L
+    from synth import build_model_solid
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    t0 = time.time()
+    s = build_model_solid(spec)
+    log(f"fixture {time.time() - t0:.1f} s; gap {s.gap:.5f} Ha, width {s.width:.3f} Ha")
+    tau, w, qerr = L.ltmp2_laplace_grid(s.gap, s.width, n_tau)
+    peaks, peak_kind = measured_peaks()
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def time_form(precision):
+        ctx = L.setup_from_solid(s, precision=precision, real=True)
+        L.ltmp2_set_stream(ctx, stream)
+        if args.slab > 0:
+            L.ltmp2_set_slab_size(ctx, args.slab)
+        for _ in range(args.warmup):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            L.ltmp2_energy(ctx, tau, w)
+        barrier()
+        L.ltmp2_reset_stage_times(ctx)
+        L.ltmp2_set_profiling(ctx, True)
+        n0 = L.ltmp2_kernel_launches(ctx)
+        evs = []
+        with ClockSampler(local) as clk:
+            barrier()
+            for _ in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(1.0)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                res = L.ltmp2_energy(ctx, tau, w)
+                b.record(stream)
+                evs.append((a, b))
+            barrier()
+        L.ltmp2_set_profiling(ctx, False)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        launches = L.ltmp2_kernel_launches(ctx) - n0
+        stages = L.ltmp2_stage_times(ctx)
+        sizes = L.ltmp2_sizes(ctx)
+        n_prim = L.ltmp2_num_primary_gprime(ctx)
+        L.ltmp2_destroy(ctx)
+        return {"ms_total": ms, "result": res, "launches": launches, "stages": stages, "sizes": sizes,
+                "n_prim": n_prim, "clocks": clk.summary()}
+
+    primary = L.FP64 if args.form == "fp64" else L.FP32
+    r = time_form(primary)
+    ms_step = r["ms_total"] / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * pairs * n_tau / (ms_step / 1e3)
+    ed, ex, ep = r["result"]
+    sizes = r["sizes"]
+
+    # roofline of the dominant stage
+    cs = 16 if primary == L.FP64 else 8
+    costs = stage_costs(sizes, r["n_prim"], True, n_tau * args.steps, s.n_orb - s.n_occ, cs)
+    st = r["stages"]
+    dom = max(st, key=lambda k: st[k]["ms"])
+    roof = None
+    if dom in costs and st[dom]["launches"] > 0:
+        per_launch_ms = st[dom]["ms"] / st[dom]["launches"]
+        work = costs[dom]["flops"] / st[dom]["launches"]
+        achieved = work / (per_launch_ms / 1e3) / 1e12
+        if primary == L.FP64:
+            peak, bound, pk = FP64_ALU_TFLOPS, "alu", "derived (2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz)"
+        else:
+            peak, bound, pk = FP32_ALU_TFLOPS, "alu", "derived (128 FP32 FMA/clk/SM x 152 SMs x 2070 MHz)"
+        roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "peak_kind": pk, "traffic": traffic_for(dom),
+                "work_per_launch": work, "avg_launch_ms": per_launch_ms}
+    else:
+        roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": traffic_for(dom)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "s_per_E_MP2": ms_step / 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if primary == L.FP64 else "c64/bf16x3/f64-sum",
+        "data": "synthetic: seeded Gaussian-well model solid, orbitals from dense diagonalisation",
+        "config": {"workload": _workload_desc(spec), "n_pw": sizes["n_pw"], "n_aux": sizes["n_aux"],
+                   "n_occ": sizes["n_occ"], "grid": sizes["grid"], "n_tau": n_tau, "pairs": pairs,
+                   "form": "plain FP64" if primary == L.FP64 else "precision (FP32 FFT, split GEMM)",
+                   "time_reversal": True, "l2": "flushed (256 MiB write) before every timed step",
+                   "laplace_max_rel_err": qerr},
+        "energy": {"E_d": ed, "E_x": ex, "E": ed + ex, "meV_per_atom": (ed + ex) * HARTREE_TO_MEV / s.n_atoms},
+        "roofline": roof,
+        "stages": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] // args.steps}
+                   for k, v in st.items()},
+        "clocks": r["clocks"],
+        "gpu_launches": r["launches"],
+        "peaks_source": peak_kind,
+    }
+
+    if rank == 0 and not args.no_forms:
+        other = L.FP32 if primary == L.FP64 else L.FP64
+        ro = time_form(other)
+        ms_o = ro["ms_total"] / args.steps
+        edo, exo, _ = ro["result"]
+        d64 = (ed, ex) if primary == L.FP64 else (edo, exo)
+        d32 = (edo, exo) if primary == L.FP64 else (ed, ex)
+        err = {"E_d": abs(d32[0] - d64[0]) * HARTREE_TO_MEV / s.n_atoms,
+               "E_x": abs(d32[1] - d64[1]) * HARTREE_TO_MEV / s.n_atoms,
+               "E": abs(sum(d32) - sum(d64)) * HARTREE_TO_MEV / s.n_atoms}
+        so = ro["stages"]
+        out["forms"] = {("fp32" if other == L.FP32 else "fp64"): {
+            "value": pairs * n_tau / (ms_o / 1e3), "s_per_E_MP2": ms_o / 1e3,
+            "speedup_vs_fp64": (ms_step / ms_o) if other == L.FP32 else (ms_o / ms_step),
+            "err_vs_fp64_meV_per_atom": err, "within_0.1_meV_per_atom": max(err.values()) <= 0.1,
+            "stages": {k: {"ms_per_step": v["ms"] / args.steps} for k, v in so.items()},
+            "gpu_launches": ro["launches"]}}
+
+    if rank == 0 and not args.no_e2e:
+        # end to end through the public API: host arrays in, host results out, every step
+        times = []
+        h2d = s.coeff.nbytes + s.eps.nbytes + s.miller.nbytes
+        d2h = 8 * (2 + s.n_occ * s.n_occ)
+        for k in range(args.steps):
+            barrier()
+            t1 = time.perf_counter()
+            ctx = L.setup_from_solid(s, precision=primary, real=True)
+            L.ltmp2_set_stream(ctx, stream)
+            L.ltmp2_energy(ctx, tau, w)
+            L.ltmp2_destroy(ctx)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t1)
+        out["e2e"] = {"value": pairs * n_tau / statistics.mean(times), "unit": UNIT,
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                      "s_per_step": statistics.mean(times)}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            out["cpu_baseline"] = run_cpu_baseline(WORKLOAD, n_tau)
+        except Exception as e:  # reported, never fatal
+            out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                   "sample": f"failed: {e}"[:300]}
+
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def _workload_desc(spec):
+    return (f"{spec.name}: cubic cell a={spec.a} bohr, {spec.wells} Gaussian wells (A=2 Ha, s=0.8 bohr) on a "
+            f"jittered {spec.lattice_sites} site lattice, {spec.grid}^3 grid, plane-wave sphere r^2<={spec.r2} "
+            f"(index units), {spec.n_occ} occupied, all other states virtual, {spec.n_tau} Laplace points, "
+            f"E_aux = 2/3 E_cut, Gamma point, closed shell")
+
+
+if __name__ == "__main__":
+    main()

@@ -176,6 +176,9 @@ int ltmp2_set_profiling(ltmp2_ctx *ctx, int on);
 int ltmp2_stage_times(const ltmp2_ctx *ctx, int n, double *ms, long long *launches);
 int ltmp2_reset_stage_times(ltmp2_ctx *ctx);
 
+/* Cumulative number of this library's kernel launches made for ctx (all calls). */
+int ltmp2_kernel_launches(const ltmp2_ctx *ctx, long long *count);
+
 /* Free all device memory of ctx.  NULL is ignored.                              */
 void ltmp2_destroy(ltmp2_ctx *ctx);
 

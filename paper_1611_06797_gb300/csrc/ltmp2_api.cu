@@ -86,6 +86,7 @@ struct ltmp2_ctx {
   EventTimer timer;
   double last_imag[2] = {0, 0};
   int slab_capacity = 0;
+  long long kernel_launches = 0;
   ~ltmp2_ctx() {
     for (void *q : allocs) cudaFree(q);
   }
@@ -255,15 +256,18 @@ int run_energy(ltmp2_ctx *c, int n_tau, const double *tau, const double *w, int 
   c->timer.stream = c->stream;
   cudaError_t e = Path<T>::zero_acc(p, c->stream);
   if (e != cudaSuccess) return cuda_status(e);
+  c->kernel_launches += 2;  // zero + final reduction
   const double nfft = (double)p.n * p.n * p.n;
   for (int k = 0; k < n_tau; ++k) {
     e = Path<T>::green(p, tau[k], c->stream, tm);
     if (e != cudaSuccess) return cuda_status(e);
+    c->kernel_launches += Path<T>::kGreenLaunches;
     const double coef = w[k] / (p.omega * p.omega * nfft * nfft);
     for (int g0 = gp_begin; g0 < gp_end; g0 += p.max_prim) {
       const int np = std::min(p.max_prim, gp_end - g0);
       e = Path<T>::slab(p, g0, np, coef, c->stream, tm);
       if (e != cudaSuccess) return cuda_status(e);
+      c->kernel_launches += Path<T>::kSlabLaunches;
     }
   }
   e = Path<T>::finish(p, c->stream, tm);
@@ -583,6 +587,12 @@ int ltmp2_last_imag(const ltmp2_ctx *ctx, double *im_direct, double *im_exchange
   if (!ctx) return LTMP2_ERR_INVALID_ARG;
   if (im_direct) *im_direct = ctx->last_imag[0];
   if (im_exchange) *im_exchange = ctx->last_imag[1];
+  return LTMP2_OK;
+}
+
+int ltmp2_kernel_launches(const ltmp2_ctx *ctx, long long *count) {
+  if (!ctx || !count) return LTMP2_ERR_INVALID_ARG;
+  *count = ctx->kernel_launches;
   return LTMP2_OK;
 }
 

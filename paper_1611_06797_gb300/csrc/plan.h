@@ -67,6 +67,8 @@ enum Stage {
 
 // Per-precision entry points (kernels_f64.cu / kernels_f32.cu)
 template <typename T> struct Path {
+  static constexpr int kGreenLaunches = 2;  // scale factors + Green's-function GEMM
+  static constexpr int kSlabLaunches = 7;   // gather, GEMM, z transform, plane, column, direct, accumulate
   static cudaError_t init_device();
   // setup: occupied orbitals -> u (real space) and cgrid
   static cudaError_t setup_occupied(const Plan &p, const void *c_occ_dev, cudaStream_t st);

@@ -65,6 +65,7 @@ def load_library():
         "ltmp2_sizes": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
         "ltmp2_last_imag": (ctypes.c_int, [vp, dp, dp]),
         "ltmp2_set_profiling": (ctypes.c_int, [vp, ctypes.c_int]),
+        "ltmp2_kernel_launches": (ctypes.c_int, [vp, P(ctypes.c_longlong)]),
         "ltmp2_stage_times": (ctypes.c_int, [vp, ctypes.c_int, dp, P(ctypes.c_longlong)]),
         "ltmp2_reset_stage_times": (ctypes.c_int, [vp]),
         "ltmp2_destroy": (None, [vp]),
@@ -211,6 +212,12 @@ def ltmp2_last_imag(ctx: Context) -> Tuple[float, float]:
     a, b = np.zeros(1), np.zeros(1)
     _check(load_library().ltmp2_last_imag(ctx.handle, _dp(a), _dp(b)), "ltmp2_last_imag")
     return float(a[0]), float(b[0])
+
+
+def ltmp2_kernel_launches(ctx: Context) -> int:
+    n = ctypes.c_longlong()
+    _check(load_library().ltmp2_kernel_launches(ctx.handle, ctypes.byref(n)), "ltmp2_kernel_launches")
+    return int(n.value)
 
 
 def ltmp2_set_profiling(ctx: Context, on: bool) -> None:
