@@ -138,3 +138,7 @@ def test_cfg2_full_size_sampled_pairs():
         assert abs(ep[i, j] - e) < TOL_FP64, (i, j, ep[i, j], e)
     assert abs(ep.sum() - (ed + ex)) < 1e-10
     assert ed < 0
+    # the precision form on the same inputs stays within 0.1 meV/atom of the plain path
+    d32, x32, _, _ = _gpu(s, tau, w, L.FP32, real=True)
+    tol = MEV_PER_ATOM * s.n_atoms
+    assert abs(d32 - ed) < tol and abs(x32 - ex) < tol and abs(d32 + x32 - ed - ex) < tol
