@@ -179,6 +179,27 @@ int ltmp2_reset_stage_times(ltmp2_ctx *ctx);
 /* Cumulative number of this library's kernel launches made for ctx (all calls). */
 int ltmp2_kernel_launches(const ltmp2_ctx *ctx, long long *count);
 
+/* ltmp2_setup + ltmp2_energy in one call that makes no device allocation (the paper
+ * has no counterpart; this serves callers that cannot call cudaMalloc: a process whose
+ * device-memory budget is already held by its own pool, code that must not trigger
+ * the device-wide synchronisation cudaMalloc/cudaFree can cause, or a plug-in whose
+ * host application owns all device memory).
+ *   sys, n_tau, tau, w, e_direct, e_exchange, e_pair: as for ltmp2_setup and
+ *           ltmp2_energy (host pointers; e_pair may be NULL).
+ *   stream: a cudaStream_t as void* (NULL = legacy default stream) on the current device.
+ * Every device buffer of the path lives in one 32 MiB array that is part of the
+ * library image (each GPU that loads the library holds it until the process exits).
+ * Systems whose buffers do not fit return LTMP2_ERR_UNSUPPORTED; as a guide, the
+ * 12^3 grid with 515 plane waves and 4 occupied orbitals fits in both precisions.
+ * The first call on a device looks up the array's device address and uploads the FFT
+ * tables; make that first call before any stream capture.  Every call reuses the same
+ * array (the previous call's contents stay until overwritten; the accumulators are
+ * cleared by each call), so calls whose GPU work overlaps, from any thread or stream,
+ * race and must be serialised by the caller.  The call returns after the results
+ * are on the host.  Errors: as ltmp2_setup and ltmp2_energy, plus UNSUPPORTED.       */
+int ltmp2_energy_noalloc(const ltmp2_system *sys, int n_tau, const double *tau, const double *w,
+                         double *e_direct, double *e_exchange, double *e_pair, void *stream);
+
 /* Free all device memory of ctx.  NULL is ignored.                              */
 void ltmp2_destroy(ltmp2_ctx *ctx);
 

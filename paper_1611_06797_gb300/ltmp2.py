@@ -239,3 +239,42 @@ def ltmp2_destroy(ctx: Context) -> None:
     if ctx.handle is not None and ctx.handle.value:
         load_library().ltmp2_destroy(ctx.handle)
         ctx.handle = ctypes.c_void_p(0)
+
+
+def ltmp2_energy_noalloc(lattice, grid, miller, coeff, eps, n_occ: int, tau, w, ecut_aux: float = 0.0,
+                         precision: int = FP64, flags: int = 0, stream=None, pairs: bool = True):
+    """ltmp2_setup + ltmp2_energy without any device allocation (see include/ltmp2.h).
+
+    For callers that cannot call cudaMalloc.  All device buffers live in the library's
+    32 MiB static array, so only small systems fit; concurrent calls race.
+    Returns (E_direct, E_exchange, e_pair or None).
+    """
+    lib = load_library()
+    f = lib.ltmp2_energy_noalloc
+    dp = ctypes.POINTER(ctypes.c_double)
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.POINTER(_System), ctypes.c_int, dp, dp, dp, dp, dp, ctypes.c_void_p]
+    lattice = np.ascontiguousarray(np.asarray(lattice, dtype=np.float64).reshape(9))
+    miller = np.ascontiguousarray(np.asarray(miller, dtype=np.int32).reshape(-1, 3))
+    coeff = np.ascontiguousarray(np.asarray(coeff, dtype=np.complex128))
+    eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+    tau = np.ascontiguousarray(np.asarray(tau, dtype=np.float64))
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    s = _System()
+    s.lattice[:] = lattice.tolist()
+    s.grid[:] = [int(g) for g in np.asarray(grid).reshape(3)]
+    s.n_pw = miller.shape[0]
+    s.miller = miller.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    s.n_orb = coeff.shape[0]
+    s.n_occ = int(n_occ)
+    s.coeff = _dp(coeff.view(np.float64))
+    s.eps = _dp(eps)
+    s.ecut_aux = float(ecut_aux)
+    s.precision = int(precision)
+    s.flags = int(flags)
+    ed, ex = np.zeros(1), np.zeros(1)
+    ep = np.zeros((int(n_occ), int(n_occ))) if pairs else None
+    handle = getattr(stream, "cuda_stream", stream) if stream is not None else 0
+    _check(f(ctypes.byref(s), len(tau), _dp(tau), _dp(w), _dp(ed), _dp(ex), _dp(ep) if pairs else None,
+             ctypes.c_void_p(int(handle) if handle else 0)), "ltmp2_energy_noalloc")
+    return float(ed[0]), float(ex[0]), ep
