@@ -38,6 +38,7 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_ALU_TFLOPS = 2 * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12     # 1.259
 FP32_ALU_TFLOPS = 128 * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
+TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense tensor-rate ratio (tf32 / bf16)
 
 WORKLOAD = "cfg2"
 CPU_SAMPLE_ORBITALS = (0, 1)   # oracle sample: pairs (0,0), (0,1), (1,1)
@@ -258,8 +259,8 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def time_form(precision):
-        ctx = L.setup_from_solid(s, precision=precision, real=True)
+    def time_form(precision, simt=False):
+        ctx = L.setup_from_solid(s, precision=precision, real=True, simt_gemm=simt)
         L.ltmp2_set_stream(ctx, stream)
         if args.slab > 0:
             L.ltmp2_set_slab_size(ctx, args.slab)
@@ -294,6 +295,29 @@ def main():
         return {"ms_total": ms, "result": res, "launches": launches, "stages": stages, "sizes": sizes,
                 "n_prim": n_prim, "clocks": clk.summary()}
 
+    def roofline(r, precision, simt):
+        st = r["stages"]
+        costs = stage_costs(r["sizes"], r["n_prim"], True, n_tau * args.steps, s.n_orb - s.n_occ, 0)
+        dom = max(st, key=lambda k: st[k]["ms"])
+        if dom not in costs or st[dom]["launches"] == 0:
+            return {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                    "traffic": traffic_for(dom)}
+        per_launch_ms = st[dom]["ms"] / st[dom]["launches"]
+        work = costs[dom]["flops"] / st[dom]["launches"]
+        if precision == L.FP64:
+            peak, bound, pk = FP64_ALU_TFLOPS, "alu", "derived (2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz)"
+        elif dom == "w_gemm" and not simt:
+            # 3xTF32: three tensor products per real product
+            work *= 3.0
+            peak = peaks["bf16_tflops"] * TF32_OVER_BF16
+            bound, pk = "tensor", f"tf32 = {peak_kind} bf16 {peaks['bf16_tflops']} x nominal 1.1/2.25"
+        else:
+            peak, bound, pk = FP32_ALU_TFLOPS, "alu", "derived (128 FP32 FMA/clk/SM x 152 SMs x 2070 MHz)"
+        achieved = work / (per_launch_ms / 1e3) / 1e12
+        return {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "peak_kind": pk, "traffic": traffic_for(dom),
+                "work_per_launch": work, "avg_launch_ms": per_launch_ms}
+
     primary = L.FP64 if args.form == "fp64" else L.FP32
     r = time_form(primary)
     ms_step = r["ms_total"] / args.steps
@@ -305,26 +329,8 @@ def main():
     ed, ex, ep = r["result"]
     sizes = r["sizes"]
 
-    # roofline of the dominant stage
-    cs = 16 if primary == L.FP64 else 8
-    costs = stage_costs(sizes, r["n_prim"], True, n_tau * args.steps, s.n_orb - s.n_occ, cs)
     st = r["stages"]
-    dom = max(st, key=lambda k: st[k]["ms"])
-    roof = None
-    if dom in costs and st[dom]["launches"] > 0:
-        per_launch_ms = st[dom]["ms"] / st[dom]["launches"]
-        work = costs[dom]["flops"] / st[dom]["launches"]
-        achieved = work / (per_launch_ms / 1e3) / 1e12
-        if primary == L.FP64:
-            peak, bound, pk = FP64_ALU_TFLOPS, "alu", "derived (2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz)"
-        else:
-            peak, bound, pk = FP32_ALU_TFLOPS, "alu", "derived (128 FP32 FMA/clk/SM x 152 SMs x 2070 MHz)"
-        roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "peak_kind": pk, "traffic": traffic_for(dom),
-                "work_per_launch": work, "avg_launch_ms": per_launch_ms}
-    else:
-        roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": traffic_for(dom)}
+    roof = roofline(r, primary, False)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -361,8 +367,23 @@ def main():
             "value": pairs * n_tau / (ms_o / 1e3), "s_per_E_MP2": ms_o / 1e3,
             "speedup_vs_fp64": (ms_step / ms_o) if other == L.FP32 else (ms_o / ms_step),
             "err_vs_fp64_meV_per_atom": err, "within_0.1_meV_per_atom": max(err.values()) <= 0.1,
+            "gemm": "tcgen05 3xTF32" if other == L.FP32 else "SIMT FP64",
+            "roofline": roofline(ro, other, False),
             "stages": {k: {"ms_per_step": v["ms"] / args.steps} for k, v in so.items()},
             "gpu_launches": ro["launches"]}}
+        if other == L.FP32:
+            rs = time_form(L.FP32, simt=True)
+            ms_s = rs["ms_total"] / args.steps
+            es = (abs(rs["result"][0] - d64[0]) + 0.0) * HARTREE_TO_MEV / s.n_atoms
+            out["forms"]["fp32_simt_gemm"] = {
+                "value": pairs * n_tau / (ms_s / 1e3), "s_per_E_MP2": ms_s / 1e3,
+                "speedup_vs_fp64": ms_step / ms_s,
+                "err_vs_fp64_meV_per_atom": {
+                    "E_d": abs(rs["result"][0] - d64[0]) * HARTREE_TO_MEV / s.n_atoms,
+                    "E_x": abs(rs["result"][1] - d64[1]) * HARTREE_TO_MEV / s.n_atoms,
+                    "E": abs(rs["result"][0] + rs["result"][1] - sum(d64)) * HARTREE_TO_MEV / s.n_atoms},
+                "gemm": "SIMT FP32 two-level sum",
+                "stages": {k: {"ms_per_step": v["ms"] / args.steps} for k, v in rs["stages"].items()}}
 
     if rank == 0 and not args.no_e2e:
         # end to end through the public API: host arrays in, host results out, every step

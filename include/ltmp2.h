@@ -55,9 +55,11 @@ extern "C" {
 
 /* ---------------------------------------------------------------- precision */
 /* LTMP2_FP64: complex128 FFTs, FP64 GEMMs, FP64 accumulation (the plain path).   */
-/* LTMP2_FP32: complex64 FFTs; Green's-function and transformed-state GEMMs on   */
-/*             tcgen05 tensor cores in BF16 3-term split precision with FP32     */
-/*             accumulation; per-pair, per-tau and final sums in FP64.           */
+/* LTMP2_FP32: complex64 FFTs; transformed-state GEMM on tcgen05 tensor cores in  */
+/*             3xTF32 split precision (hi*hi + hi*lo + lo*hi), each 32-wide k    */
+/*             block's tensor-memory partial added to FP32 register sums;        */
+/*             Green's function on the CUDA cores in FP32; per-pair, per-tau and */
+/*             final sums in FP64.                                               */
 #define LTMP2_FP64 0
 #define LTMP2_FP32 1
 
@@ -66,6 +68,9 @@ extern "C" {
  * Sec. II D, at k = 0).  Then w_j^{(-G')} = conj(w_j^{(G')}) in real space and only
  * half of the G' set is transformed; the library checks the property in setup.  */
 #define LTMP2_FLAG_REAL_ORBITALS 1
+/* Precision form only: run the transformed-state GEMM on the CUDA cores (FP32, two-level
+ * summation) instead of the tcgen05 3xTF32 tensor-core kernel.  For comparisons.   */
+#define LTMP2_FLAG_SIMT_GEMM 2
 
 typedef struct ltmp2_ctx ltmp2_ctx; /* opaque; owns all device memory of one system */
 
@@ -85,7 +90,7 @@ typedef struct ltmp2_ctx ltmp2_ctx; /* opaque; owns all device memory of one sys
  *   ecut_aux       E_cut^aux in Hartree; <= 0 selects 2/3 of the largest |G_p|^2/2
  *                  ("commonly chosen as 2/3 E_cut", Sec. II A).
  *   precision      LTMP2_FP64 or LTMP2_FP32.
- *   flags          0 or LTMP2_FLAG_REAL_ORBITALS.
+ *   flags          0 or LTMP2_FLAG_REAL_ORBITALS, optionally | LTMP2_FLAG_SIMT_GEMM.
  */
 typedef struct {
   double lattice[9];
@@ -191,6 +196,8 @@ int ltmp2_kernel_launches(const ltmp2_ctx *ctx, long long *count);
  * library image (each GPU that loads the library holds it until the process exits).
  * Systems whose buffers do not fit return LTMP2_ERR_UNSUPPORTED; as a guide, the
  * 12^3 grid with 515 plane waves and 4 occupied orbitals fits in both precisions.
+ * In LTMP2_FP32 the transformed-state GEMM runs on the CUDA cores, as it does in
+ * ltmp2_energy with LTMP2_FLAG_SIMT_GEMM (so that flag is not accepted here).
  * The first call on a device looks up the array's device address and uploads the FFT
  * tables; make that first call before any stream capture.  Every call reuses the same
  * array (the previous call's contents stay until overwritten; the accumulators are

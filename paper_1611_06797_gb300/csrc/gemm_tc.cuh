@@ -1,0 +1,438 @@
+// tcgen05 complex GEMM in 3xTF32 split precision for the transformed states of the
+// precision form (step (iii), Eqs. SCHnewstate / SCHtransmatrix):
+//     W^T[m][n] = sum_q S^T[m][q] P^T[q][n],   complex, FP32 in / FP32 out.
+//
+// The complex product is written as two real K-major GEMMs over K' = 2 n_pw with
+// interleaved real/imaginary parts:
+//     A1[m][2q] = Re S,  A1[m][2q+1] = -Im S        (row m of S^T)
+//     A2[m][2q] = Im S,  A2[m][2q+1] =  Re S
+//     B [n][2q] = Re P,  B [n][2q+1] =  Im P        (P = conj(P^T)^T, P Hermitian)
+//     Re W = A1 B^T,  Im W = A2 B^T.
+// Each operand x is split as x_hi = tf32(x), x_lo = tf32(x - x_hi) (round to nearest),
+// and every product is x_hi y_hi + x_hi y_lo + x_lo y_hi, accumulated in FP32 in tensor
+// memory.  Operands arrive by TMA (128-byte swizzle) into a two-stage shared-memory ring;
+// one thread issues the TMA copies and the MMAs; four warps drain the accumulators.
+// Every wait is bounded: on expiry the kernel raises an error flag instead of hanging.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ltmp2 {
+namespace tc {
+
+constexpr int BM = 128;             // rows of A per tile (complex rows of W^T)
+constexpr int BK = 32;              // fp32 elements per k block = one 128-byte swizzle row
+constexpr int A_TILE_BYTES = BM * 128;
+constexpr int STAGES = 2;
+// Tile of BN columns with NREG accumulator pairs (Re, Im) in tensor memory.  Consecutive
+// 8-wide k steps go round-robin to the NREG pairs, which the epilogue sums in FP32: the
+// tensor core's internal accumulation is not round-to-nearest, and a single chain over
+// K' ~ 6000 drifted by ~1e-4 (relative) on the transformed states.
+template <int BN, int NREG> struct TcCfg {
+  static constexpr int B_TILE_BYTES = BN * 128;
+  static constexpr int STAGE_BYTES = 4 * A_TILE_BYTES + 2 * B_TILE_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;   // + alignment slack
+  static constexpr int TMEM_COLS = 2 * BN * NREG;
+  static_assert(TMEM_COLS == 64 || TMEM_COLS == 128 || TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM columns");
+  // instruction descriptor: D fp32, A and B tf32, both K-major, M = 128, N = BN
+  static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                    ((uint32_t)(BM >> 4) << 24);
+};
+constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;  // 1 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait for the phase with this parity; false when WAIT_LIMIT_NS ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (global_ns() - t0 < WAIT_LIMIT_NS)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// 32 consecutive fp32 accumulator columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row core groups
+// 1024 bytes apart (SBO); the leading offset is unused for this layout.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// ---------------------------------------------------------------- operand packing
+// S^T complex [rows][npw] -> A1/A2 hi/lo, fp32 [rows][kpad]; zero past 2 npw
+__global__ void k_pack_a(const float2 *__restrict__ st, int rows, int npw, int kpad, float *__restrict__ a1h,
+                         float *__restrict__ a1l, float *__restrict__ a2h, float *__restrict__ a2l) {
+  const int m = blockIdx.y;
+  const int half = kpad / 2;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < half; q += gridDim.x * blockDim.x) {
+    float re = 0.f, im = 0.f;
+    if (q < npw && m < rows) {
+      const float2 v = st[(size_t)m * npw + q];
+      re = v.x;
+      im = v.y;
+    }
+    const float h_re = tf32_rn(re), l_re = tf32_rn(re - h_re);
+    const float h_im = tf32_rn(im), l_im = tf32_rn(im - h_im);
+    const size_t o = (size_t)m * kpad + 2 * q;
+    a1h[o] = h_re; a1h[o + 1] = -h_im;
+    a1l[o] = l_re; a1l[o + 1] = -l_im;
+    a2h[o] = h_im; a2h[o + 1] = h_re;
+    a2l[o] = l_im; a2l[o + 1] = l_re;
+  }
+}
+// P^T complex [npw][npw] (Hermitian P) -> B[n][2q] = Re P[n][q] = Re P^T[n][q],
+// B[n][2q+1] = Im P[n][q] = -Im P^T[n][q]; hi/lo split, fp32 [npw][kpad]
+__global__ void k_pack_b(const float2 *__restrict__ pt, int npw, int kpad, float *__restrict__ bh,
+                         float *__restrict__ bl) {
+  const int n = blockIdx.y;
+  const int half = kpad / 2;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < half; q += gridDim.x * blockDim.x) {
+    float re = 0.f, im = 0.f;
+    if (q < npw) {
+      const float2 v = pt[(size_t)n * npw + q];
+      re = v.x;
+      im = -v.y;
+    }
+    const float h_re = tf32_rn(re), l_re = tf32_rn(re - h_re);
+    const float h_im = tf32_rn(im), l_im = tf32_rn(im - h_im);
+    const size_t o = (size_t)n * kpad + 2 * q;
+    bh[o] = h_re; bh[o + 1] = h_im;
+    bl[o] = l_re; bl[o + 1] = l_im;
+  }
+}
+
+// ---------------------------------------------------------------- the GEMM
+struct TcMaps {
+  CUtensorMap a1h, a1l, a2h, a2l, bh, bl;
+};
+
+template <int BN, int NREG>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_cgemm(const __grid_constant__ CUtensorMap ta1h, const __grid_constant__ CUtensorMap ta1l,
+               const __grid_constant__ CUtensorMap ta2h, const __grid_constant__ CUtensorMap ta2l,
+               const __grid_constant__ CUtensorMap tbh, const __grid_constant__ CUtensorMap tbl, int M, int N,
+               int kblocks, float2 *__restrict__ C, int ldc, int *__restrict__ err) {
+  using Cfg = TcCfg<BN, NREG>;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+  __shared__ uint32_t tmem_slot;
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+
+  if (warp == 0) tmem_alloc(&tmem_slot, Cfg::TMEM_COLS);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    auto issue = [&](int kb, int s) {
+      unsigned char *st = smem + s * Cfg::STAGE_BYTES;
+      mbar_expect_tx(&full_bar[s], Cfg::STAGE_BYTES);
+      const int x = kb * BK;
+      tma_load_2d(st + 0 * A_TILE_BYTES, &ta1h, &full_bar[s], x, m0);
+      tma_load_2d(st + 1 * A_TILE_BYTES, &ta1l, &full_bar[s], x, m0);
+      tma_load_2d(st + 2 * A_TILE_BYTES, &ta2h, &full_bar[s], x, m0);
+      tma_load_2d(st + 3 * A_TILE_BYTES, &ta2l, &full_bar[s], x, m0);
+      tma_load_2d(st + 4 * A_TILE_BYTES, &tbh, &full_bar[s], x, n0);
+      tma_load_2d(st + 4 * A_TILE_BYTES + Cfg::B_TILE_BYTES, &tbl, &full_bar[s], x, n0);
+    };
+    // Stage s holds k block kb; the other stage already holds kb + 1.  MMAs of kb are
+    // queued before waiting for those of kb - 1, whose stage then takes kb + 1.
+    for (int s = 0; s < STAGES && s < kblocks; ++s) issue(s, s);
+    for (int kb = 0; kb < kblocks; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
+      if (!mbar_wait(&full_bar[s], ph)) { ok = false; break; }
+      fence_after();
+      const uint32_t base = smem_u32(smem + s * Cfg::STAGE_BYTES);
+#pragma unroll
+      for (int k = 0; k < BK / 8; ++k) {
+        const uint32_t ko = k * 32;  // 8 tf32 elements = 32 bytes along K
+        const uint64_t a1h = sdesc_sw128(base + 0 * A_TILE_BYTES + ko);
+        const uint64_t a1l = sdesc_sw128(base + 1 * A_TILE_BYTES + ko);
+        const uint64_t a2h = sdesc_sw128(base + 2 * A_TILE_BYTES + ko);
+        const uint64_t a2l = sdesc_sw128(base + 3 * A_TILE_BYTES + ko);
+        const uint64_t bh = sdesc_sw128(base + 4 * A_TILE_BYTES + ko);
+        const uint64_t bl = sdesc_sw128(base + 4 * A_TILE_BYTES + Cfg::B_TILE_BYTES + ko);
+        const int step = kb * (BK / 8) + k;
+        const uint32_t reg = (uint32_t)(step % NREG) * (2 * BN);
+        const uint32_t first = (step >= NREG) ? 1u : 0u;
+        mma_tf32(tmem + reg, a1h, bh, Cfg::IDESC, first);
+        mma_tf32(tmem + reg, a1h, bl, Cfg::IDESC, 1u);
+        mma_tf32(tmem + reg, a1l, bh, Cfg::IDESC, 1u);
+        mma_tf32(tmem + reg + BN, a2h, bh, Cfg::IDESC, first);
+        mma_tf32(tmem + reg + BN, a2h, bl, Cfg::IDESC, 1u);
+        mma_tf32(tmem + reg + BN, a2l, bh, Cfg::IDESC, 1u);
+      }
+      mma_commit(&empty_bar[s]);
+      if (kb >= 1 && kb + 1 < kblocks) {
+        const int sp = (kb - 1) % STAGES;
+        if (!mbar_wait(&empty_bar[sp], (uint32_t)(((kb - 1) / STAGES) & 1))) { ok = false; break; }
+        issue(kb + 1, sp);
+      }
+    }
+    mma_commit(&done_bar);
+  }
+  const bool done_ok = mbar_wait(&done_bar, 0);
+  if ((!ok || !done_ok) && lane == 0) atomicExch(err, 1);
+  fence_after();
+  // epilogue: lane r of warp w holds row 32 w + r of every accumulator
+  const int row = warp * 32 + lane;
+  const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
+  const int nsteps = kblocks * (BK / 8);
+#pragma unroll 1
+  for (int c = 0; c < BN / 32; ++c) {
+    float re[32], im[32], tr[32], ti[32];
+    tmem_ld32(t_lane + c * 32, re);
+    tmem_ld32(t_lane + BN + c * 32, im);
+#pragma unroll 1
+    for (int r = 1; r < NREG; ++r) {
+      tmem_ld32(t_lane + r * 2 * BN + c * 32, tr);
+      tmem_ld32(t_lane + r * 2 * BN + BN + c * 32, ti);
+      if (r < nsteps) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) { re[j] += tr[j]; im[j] += ti[j]; }
+      }
+    }
+    const int gm = m0 + row;
+    if (done_ok && gm < M) {
+      float2 *dst = C + (size_t)gm * ldc + n0 + c * 32;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (n0 + c * 32 + j < N) dst[j] = make_float2(re[j], im[j]);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
+}
+
+// ---------------------------------------------------------------- drained variant
+// Warp 4 (one elected thread) issues TMA copies and MMAs; warps 0-3 own tensor-memory
+// lanes 0-127.  Each k block is accumulated into one of two tensor-memory accumulator
+// pairs (Re, Im; BN columns each) starting from zero, and the four epilogue warps add
+// that partial to FP32 register sums (round to nearest) and release the pair for the
+// block after next.  The tensor core's own accumulation thus runs over 12 MMAs only.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(160, 1)
+    k_tc_cgemm_drain(const __grid_constant__ CUtensorMap ta1h, const __grid_constant__ CUtensorMap ta1l,
+                     const __grid_constant__ CUtensorMap ta2h, const __grid_constant__ CUtensorMap ta2l,
+                     const __grid_constant__ CUtensorMap tbh, const __grid_constant__ CUtensorMap tbl, int M, int N,
+                     int kblocks, float2 *__restrict__ C, int ldc, int *__restrict__ err) {
+  using Cfg = TcCfg<BN, 2>;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2], done_bar;
+  __shared__ uint32_t tmem_slot;
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+
+  if (warp == 0) tmem_alloc(&tmem_slot, Cfg::TMEM_COLS);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int r = 0; r < 2; ++r) {
+      mbar_init(&accf_bar[r], 1);
+      mbar_init(&acce_bar[r], 128);
+    }
+    mbar_init(&done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+  bool ok = true;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      auto issue = [&](int kb, int s) {
+        unsigned char *st = smem + s * Cfg::STAGE_BYTES;
+        mbar_expect_tx(&full_bar[s], Cfg::STAGE_BYTES);
+        const int x = kb * BK;
+        tma_load_2d(st + 0 * A_TILE_BYTES, &ta1h, &full_bar[s], x, m0);
+        tma_load_2d(st + 1 * A_TILE_BYTES, &ta1l, &full_bar[s], x, m0);
+        tma_load_2d(st + 2 * A_TILE_BYTES, &ta2h, &full_bar[s], x, m0);
+        tma_load_2d(st + 3 * A_TILE_BYTES, &ta2l, &full_bar[s], x, m0);
+        tma_load_2d(st + 4 * A_TILE_BYTES, &tbh, &full_bar[s], x, n0);
+        tma_load_2d(st + 4 * A_TILE_BYTES + Cfg::B_TILE_BYTES, &tbl, &full_bar[s], x, n0);
+      };
+      for (int s = 0; s < STAGES && s < kblocks; ++s) issue(s, s);
+      for (int kb = 0; kb < kblocks; ++kb) {
+        const int s = kb % STAGES, r = kb & 1;
+        if (!mbar_wait(&full_bar[s], (uint32_t)((kb / STAGES) & 1))) { ok = false; break; }
+        if (kb >= 2 && !mbar_wait(&acce_bar[r], (uint32_t)(((kb - 2) >> 1) & 1))) { ok = false; break; }
+        fence_after();
+        const uint32_t base = smem_u32(smem + s * Cfg::STAGE_BYTES);
+        const uint32_t dre = tmem + (uint32_t)r * (2 * BN), dim = dre + BN;
+#pragma unroll
+        for (int k = 0; k < BK / 8; ++k) {
+          const uint32_t ko = k * 32;
+          const uint64_t a1h = sdesc_sw128(base + 0 * A_TILE_BYTES + ko);
+          const uint64_t a1l = sdesc_sw128(base + 1 * A_TILE_BYTES + ko);
+          const uint64_t a2h = sdesc_sw128(base + 2 * A_TILE_BYTES + ko);
+          const uint64_t a2l = sdesc_sw128(base + 3 * A_TILE_BYTES + ko);
+          const uint64_t bh = sdesc_sw128(base + 4 * A_TILE_BYTES + ko);
+          const uint64_t bl = sdesc_sw128(base + 4 * A_TILE_BYTES + Cfg::B_TILE_BYTES + ko);
+          const uint32_t acc = k > 0 ? 1u : 0u;
+          mma_tf32(dre, a1h, bh, Cfg::IDESC, acc);
+          mma_tf32(dre, a1h, bl, Cfg::IDESC, 1u);
+          mma_tf32(dre, a1l, bh, Cfg::IDESC, 1u);
+          mma_tf32(dim, a2h, bh, Cfg::IDESC, acc);
+          mma_tf32(dim, a2h, bl, Cfg::IDESC, 1u);
+          mma_tf32(dim, a2l, bh, Cfg::IDESC, 1u);
+        }
+        mma_commit(&empty_bar[s]);
+        mma_commit(&accf_bar[r]);
+        if (kb >= 1 && kb + 1 < kblocks) {
+          const int sp = (kb - 1) % STAGES;
+          if (!mbar_wait(&empty_bar[sp], (uint32_t)(((kb - 1) / STAGES) & 1))) { ok = false; break; }
+          issue(kb + 1, sp);
+        }
+      }
+      mma_commit(&done_bar);
+      if (!ok) atomicExch(err, 1);
+    }
+  } else {
+    // epilogue warps: drain every k block's partial into FP32 register sums
+    float sr[BN], si[BN];
+#pragma unroll
+    for (int j = 0; j < BN; ++j) { sr[j] = 0.f; si[j] = 0.f; }
+    const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int kb = 0; kb < kblocks; ++kb) {
+      const int r = kb & 1;
+      if (!mbar_wait(&accf_bar[r], (uint32_t)((kb >> 1) & 1))) { ok = false; break; }
+      fence_after();
+#pragma unroll
+      for (int c = 0; c < BN / 32; ++c) {
+        float v[32];
+        tmem_ld32(t_lane + r * 2 * BN + c * 32, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sr[c * 32 + j] += v[j];
+        tmem_ld32(t_lane + r * 2 * BN + BN + c * 32, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) si[c * 32 + j] += v[j];
+      }
+      fence_before();
+      mbar_arrive(&acce_bar[r]);
+    }
+    if (!ok && lane == 0) atomicExch(err, 1);
+    const int gm = m0 + warp * 32 + lane;
+    if (ok && gm < M) {
+      float2 *dst = C + (size_t)gm * ldc + n0;
+#pragma unroll
+      for (int j = 0; j < BN; ++j)
+        if (n0 + j < N) dst[j] = make_float2(sr[j], si[j]);
+    }
+  }
+  const bool done_ok = mbar_wait(&done_bar, 0);
+  if (!done_ok && lane == 0) atomicExch(err, 1);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
+}
+
+}  // namespace tc
+}  // namespace ltmp2

@@ -6,6 +6,8 @@
 //   (iv)  Fock-like (Eq. SCHfocklike) and Hartree-like (Eq. dLTMP2Compact)
 //         contractions of the co-densities <i|e^{-iGr}|w_j^{(G' tau)}>.
 #pragma once
+#include <type_traits>
+
 #include "fft.cuh"
 #include "plan.h"
 
@@ -41,8 +43,8 @@ __global__ void k_dscale(int n_orb, int n_occ, const double *__restrict__ eps, d
 // ---------------------------------------------------------------- SIMT complex GEMM
 // C[m][n] = sum_k opA(m,k) * B[k][n] * s_k,  opA(m,k) = A[m*lda+k] (A_KM) or A[k*lda+m],
 // conjugated if A_CONJ; s_k = kscale[k] or 1.  64x64 tile, 256 threads, 4x4 per thread.
-// Two-level summation: each 8-wide k tile is summed into a fresh partial that is then
-// added to the accumulator.  A single FP32 chain over K ~ 3000 terms biased the MP2
+// Two-level summation (FP32 only): each 8-wide k tile is summed into a fresh partial that
+// is then added to the accumulator.  A single FP32 chain over K ~ 3000 terms biased the MP2
 // energy by ~2e-5 (relative) on the 24^3 workload; the two-level sum brings it to ~1e-6.
 template <typename T, bool A_KM, bool A_CONJ>
 __global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cpx<T> *__restrict__ A, int lda,
@@ -80,11 +82,13 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cpx<T>
       Bs[kk][nn] = v;
     }
     __syncthreads();
+    // FP32: fresh partial per k tile (two-level sum); FP64 accumulates directly
+    constexpr bool kTwoLevel = std::is_same<T, float>::value;
     cpx<T> part[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) part[i][j] = {T(0), T(0)};
+      for (int j = 0; j < 4; ++j) part[i][j] = kTwoLevel ? cpx<T>{T(0), T(0)} : acc[i][j];
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       cpx<T> a[4], b[4];
@@ -103,7 +107,10 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cpx<T>
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) { acc[i][j].x += part[i][j].x; acc[i][j].y += part[i][j].y; }
+      for (int j = 0; j < 4; ++j) {
+        if (kTwoLevel) { acc[i][j].x += part[i][j].x; acc[i][j].y += part[i][j].y; }
+        else acc[i][j] = part[i][j];
+      }
     __syncthreads();
   }
 #pragma unroll

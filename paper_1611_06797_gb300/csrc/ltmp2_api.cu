@@ -87,7 +87,9 @@ struct ltmp2_ctx {
   double last_imag[2] = {0, 0};
   int slab_capacity = 0;
   long long kernel_launches = 0;
+  TcResources tc;
   ~ltmp2_ctx() {
+    tc_release(tc);
     for (void *q : allocs) cudaFree(q);
   }
 };
@@ -243,6 +245,13 @@ template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys,
   if ((rc = dalloc_bytes(c, &p.mdiag, cs * (size_t)spp * p.max_prim * p.n_aux * p.n_occ))) return rc;
   if ((rc = dalloc(c, &p.sx, (size_t)p.max_prim * p.n_occ * p.n_occ))) return rc;
   if ((rc = dalloc(c, &p.yd, (size_t)p.max_prim * p.n_occ * p.n_occ))) return rc;
+  if (std::is_same<T, float>::value && !(sys->flags & LTMP2_FLAG_SIMT_GEMM)) {
+    void *tcmem = nullptr;
+    if ((rc = dalloc_bytes(c, &tcmem, tc_bytes((int)max_cols, p.n_pw)))) return rc;
+    e = tc_init(c->tc, tcmem, (int)max_cols, p.n_pw, 4);
+    if (e != cudaSuccess) return cuda_status(e);
+    p.tc = &c->tc;
+  }
   e = Path<T>::setup_occupied(p, cocc, c->stream);
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaStreamSynchronize(c->stream);
@@ -261,20 +270,31 @@ int run_energy(ltmp2_ctx *c, int n_tau, const double *tau, const double *w, int 
   for (int k = 0; k < n_tau; ++k) {
     e = Path<T>::green(p, tau[k], c->stream, tm);
     if (e != cudaSuccess) return cuda_status(e);
-    c->kernel_launches += Path<T>::kGreenLaunches;
+    c->kernel_launches += Path<T>::green_launches(p);
     const double coef = w[k] / (p.omega * p.omega * nfft * nfft);
     for (int g0 = gp_begin; g0 < gp_end; g0 += p.max_prim) {
       const int np = std::min(p.max_prim, gp_end - g0);
       e = Path<T>::slab(p, g0, np, coef, c->stream, tm);
       if (e != cudaSuccess) return cuda_status(e);
-      c->kernel_launches += Path<T>::kSlabLaunches;
+      c->kernel_launches += Path<T>::slab_launches(p);
     }
   }
   e = Path<T>::finish(p, c->stream, tm);
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaStreamSynchronize(c->stream);
   if (tm) c->timer.collect();
-  return cuda_status(e);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (p.tc) {
+    // a bounded wait inside the tensor-core GEMM ran out: report, clear the flag
+    int flag = 0;
+    e = cudaMemcpy(&flag, p.tc->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (flag) {
+      cudaMemset(p.tc->err, 0, sizeof(int));
+      return LTMP2_ERR_TIMEOUT;
+    }
+  }
+  return LTMP2_OK;
 }
 
 int check_tau(int n_tau, const double *tau, const double *w) {
@@ -343,7 +363,7 @@ int ltmp2_setup(const ltmp2_system *sys, ltmp2_ctx **out) {
   if (sys->n_pw < 2 || sys->n_orb < 2 || sys->n_occ < 1 || sys->n_occ >= sys->n_orb || sys->n_orb > sys->n_pw)
     return LTMP2_ERR_INVALID_ARG;
   if (sys->precision != LTMP2_FP64 && sys->precision != LTMP2_FP32) return LTMP2_ERR_INVALID_ARG;
-  if (sys->flags & ~LTMP2_FLAG_REAL_ORBITALS) return LTMP2_ERR_INVALID_ARG;
+  if (sys->flags & ~(LTMP2_FLAG_REAL_ORBITALS | LTMP2_FLAG_SIMT_GEMM)) return LTMP2_ERR_INVALID_ARG;
   for (int k = 0; k < 9; ++k)
     if (!std::isfinite(sys->lattice[k])) return LTMP2_ERR_INVALID_ARG;
   const int n = sys->grid[0];

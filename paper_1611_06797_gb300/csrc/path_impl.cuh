@@ -1,6 +1,8 @@
 // Launchers of the hot path for one real type T.  Included once per precision by
 // kernels_f64.cu / kernels_f32.cu, which explicitly instantiate Path<T>.
 #pragma once
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace ltmp2 {
@@ -83,7 +85,12 @@ cudaError_t Path<T>::green(const Plan &p, double tau, cudaStream_t st, StageTime
   k_cgemm<T, false, true><<<grid, 256, 0, st>>>(M, N, K, (const cpx<T> *)p.cv, p.n_pw,
                                                 (const cpx<T> *)p.cv, p.n_pw,
                                                 (const T *)p.dscale + p.n_occ, (cpx<T> *)p.pt, p.n_pw);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if constexpr (std::is_same<T, float>::value) {
+    if (p.tc) return tc_pack_b(*p.tc, p.pt, st);  // split P into TF32 hi/lo operands
+  }
+  return cudaSuccess;
 }
 
 template <typename T>
@@ -99,11 +106,20 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
   }
   {
     ScopedStage s(tm, kStageWGemm);
-    dim3 grid((p.n_pw + 63) / 64, (ncols + 63) / 64);
-    k_cgemm<T, true, false><<<grid, 256, 0, st>>>(ncols, p.n_pw, p.n_pw, (const cpx<T> *)p.st, p.n_pw,
-                                                  (const cpx<T> *)p.pt, p.n_pw, nullptr,
-                                                  (cpx<T> *)p.wt, p.n_pw);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (p.tc) {
+        if ((e = tc_wgemm(*p.tc, p.st, ncols, p.wt, st)) != cudaSuccess) return e;
+        done = true;
+      }
+    }
+    if (!done) {
+      dim3 grid((p.n_pw + 63) / 64, (ncols + 63) / 64);
+      k_cgemm<T, true, false><<<grid, 256, 0, st>>>(ncols, p.n_pw, p.n_pw, (const cpx<T> *)p.st, p.n_pw,
+                                                    (const cpx<T> *)p.pt, p.n_pw, nullptr,
+                                                    (cpx<T> *)p.wt, p.n_pw);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
   }
   const int ib = plane_ib<T>(n, no);
   const size_t smem_plane = (size_t)n * (n + 1) * sizeof(cpx<T>) * (1 + ib);

@@ -6,6 +6,22 @@
 
 namespace ltmp2 {
 
+// Operands, tensor maps and error flag of the tcgen05 3xTF32 GEMM (precision form).
+struct TcResources {
+  int rows_cap = 0, npw = 0, kpad = 0;
+  int variant = 3;         // tile / accumulator layout: 0 (128,1) 1 (128,2) 2 (64,2) 3 (64,4)
+  float *a1h = nullptr, *a1l = nullptr, *a2h = nullptr, *a2l = nullptr, *bh = nullptr, *bl = nullptr;
+  int *err = nullptr;      // device flag: a bounded wait ran out
+  void *maps = nullptr;    // host copy of the six TMA tensor maps
+};
+int tc_kpad(int npw);
+size_t tc_bytes(int rows_cap, int npw);
+cudaError_t tc_init(TcResources &r, void *mem, int rows_cap, int npw, int variant);
+int tc_variant_bn(int variant);
+void tc_release(TcResources &r);
+cudaError_t tc_pack_b(const TcResources &r, const void *pt, cudaStream_t st);
+cudaError_t tc_wgemm(const TcResources &r, const void *st_in, int rows, void *wt, cudaStream_t st);
+
 // One column of a plane-wave sphere at fixed (m1, m2): m3 runs over [zlo, zhi].
 // Columns are stored in order; the sphere's points follow column by column
 // (m3 ascending), starting at col_off[c].
@@ -50,6 +66,7 @@ struct Plan {
   double *ex = nullptr, *ed = nullptr, *exi = nullptr, *edi = nullptr;  // [n_occ][n_occ]
   double *esum = nullptr;    // [4]: E_d, E_x, imag parts
   int max_prim = 0;          // primary G' per slab (capacity)
+  TcResources *tc = nullptr; // precision form: tcgen05 GEMM resources (host pointer), or null
   int slots_per_prim() const { return real_orb ? 1 : 2; }
 };
 
@@ -67,8 +84,10 @@ enum Stage {
 
 // Per-precision entry points (kernels_f64.cu / kernels_f32.cu)
 template <typename T> struct Path {
-  static constexpr int kGreenLaunches = 2;  // scale factors + Green's-function GEMM
-  static constexpr int kSlabLaunches = 7;   // gather, GEMM, z transform, plane, column, direct, accumulate
+  // kernel launches per Green's function build and per slab (the tcgen05 path of the
+  // precision form adds one operand-packing launch to each)
+  static int green_launches(const Plan &p) { return p.tc ? 3 : 2; }
+  static int slab_launches(const Plan &p) { return p.tc ? 8 : 7; }
   static cudaError_t init_device();
   // setup: occupied orbitals -> u (real space) and cgrid
   static cudaError_t setup_occupied(const Plan &p, const void *c_occ_dev, cudaStream_t st);

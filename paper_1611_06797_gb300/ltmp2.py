@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libltmp2.so")
 FP64 = 0
 FP32 = 1
 FLAG_REAL_ORBITALS = 1
+FLAG_SIMT_GEMM = 2
 NUM_STAGES = 7
 STAGE_NAMES = ["green_gemm", "w_gemm", "gather_ztransform", "plane_fft", "column_fft_contract",
                "direct_contract", "accumulate"]
@@ -135,11 +136,11 @@ def ltmp2_setup(lattice, grid, miller, coeff, eps, n_occ: int, ecut_aux: float =
 
 
 def setup_from_solid(solid, precision: int = FP64, real: Optional[bool] = None,
-                     ecut_aux: Optional[float] = None) -> Context:
+                     ecut_aux: Optional[float] = None, simt_gemm: bool = False) -> Context:
     """ltmp2_setup for a synth.ModelSolid (E_aux = 2/3 E_cut unless given)."""
     if ecut_aux is None:
         ecut_aux = 2.0 * solid.ecut / 3.0
-    flags = FLAG_REAL_ORBITALS if real else 0
+    flags = (FLAG_REAL_ORBITALS if real else 0) | (FLAG_SIMT_GEMM if simt_gemm else 0)
     return ltmp2_setup(solid.lattice, solid.grid, solid.miller, solid.coeff, solid.eps, solid.n_occ,
                        ecut_aux, precision, flags)
 

@@ -26,7 +26,8 @@ TOL = 1e-8  # Ha, the plain path's parity tolerance
 def test_noalloc_matches_energy_two_calls(name, precision, real):
     s = solid(name)
     tau, w = sinc_laplace_quadrature(s.spec.n_tau, *denominator_range(OracleSystem.from_solid(s)))
-    ctx = L.setup_from_solid(s, precision=precision, real=real)
+    # the allocation-free path runs the CUDA-core GEMM in the precision form
+    ctx = L.setup_from_solid(s, precision=precision, real=real, simt_gemm=(precision == L.FP32))
     ed, ex, ep = L.ltmp2_energy(ctx, tau, w)
     L.ltmp2_destroy(ctx)
     flags = L.FLAG_REAL_ORBITALS if real else 0
