@@ -25,27 +25,33 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-int make_map(CUtensorMap *m, float *base, int rows, int kpad, int box_rows) {
+int make_map(CUtensorMap *m, float *base, int rows, int kpad, int box_rows, int box_k = tc::BK,
+             CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B) {
   cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)kpad * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)box_k, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1u, 1u};
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return -1;
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
-                                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                            CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -1;
 }
 }  // namespace
 
-int tc_variant_bn(int variant) { return variant <= 1 ? 128 : 64; }  // variant 4: drained, 64
+// Variants: 0-3 single-pass accumulators (tile N 128/64, 1-4 regions, for tests of the
+// accumulation drift), 4 drained (N 64, two-stage ring), 5 stacked Re/Im rows with a
+// six-stage 64-byte-swizzle ring (the default).
+int tc_variant_bn(int variant) { return variant <= 1 ? 128 : (variant == 5 ? tc::S_BN : 64); }
 
 int tc_kpad(int npw) { return ((2 * npw + tc::BK - 1) / tc::BK) * tc::BK; }
 
+static int rows_pad(int rows) { return ((rows + 127) / 128) * 128; }
+
 size_t tc_bytes(int rows_cap, int npw) {
   const size_t kp = (size_t)tc_kpad(npw);
-  return sizeof(float) * kp * (4 * (size_t)rows_cap + 2 * (size_t)npw) + 256;
+  return sizeof(float) * kp * (4 * (size_t)rows_pad(rows_cap) + 2 * (size_t)npw) + 256;
 }
 
 cudaError_t tc_init(TcResources &r, void *mem, int rows_cap, int npw, int variant) {
@@ -53,16 +59,28 @@ cudaError_t tc_init(TcResources &r, void *mem, int rows_cap, int npw, int varian
   r.rows_cap = rows_cap;
   r.npw = npw;
   r.kpad = tc_kpad(npw);
-  const size_t a = (size_t)rows_cap * r.kpad, b = (size_t)npw * r.kpad;
+  const int rp = rows_pad(rows_cap);
+  const size_t a = (size_t)rp * r.kpad, b = (size_t)npw * r.kpad;
   float *f = static_cast<float *>(mem);
   r.a1h = f; r.a1l = f + a; r.a2h = f + 2 * a; r.a2l = f + 3 * a;
   r.bh = f + 4 * a; r.bl = f + 4 * a + b;
   r.err = reinterpret_cast<int *>(f + 4 * a + 2 * b);
   tc::TcMaps *mp = new tc::TcMaps();
-  const int bn = tc_variant_bn(r.variant);
-  if (make_map(&mp->a1h, r.a1h, rows_cap, r.kpad, tc::BM) || make_map(&mp->a1l, r.a1l, rows_cap, r.kpad, tc::BM) ||
-      make_map(&mp->a2h, r.a2h, rows_cap, r.kpad, tc::BM) || make_map(&mp->a2l, r.a2l, rows_cap, r.kpad, tc::BM) ||
-      make_map(&mp->bh, r.bh, npw, r.kpad, bn) || make_map(&mp->bl, r.bl, npw, r.kpad, bn)) {
+  int bad = 0;
+  if (variant == 5) {
+    // stacked operand: hi in a1h and lo in a1l, 2 rp rows each (spanning a1h..a2l)
+    r.a1l = f + 2 * a;
+    bad |= make_map(&mp->a1h, r.a1h, 2 * rp, r.kpad, 128, tc::S_BK, CU_TENSOR_MAP_SWIZZLE_64B);
+    bad |= make_map(&mp->a1l, r.a1l, 2 * rp, r.kpad, 128, tc::S_BK, CU_TENSOR_MAP_SWIZZLE_64B);
+    bad |= make_map(&mp->bh, r.bh, npw, r.kpad, tc::S_BN, tc::S_BK, CU_TENSOR_MAP_SWIZZLE_64B);
+    bad |= make_map(&mp->bl, r.bl, npw, r.kpad, tc::S_BN, tc::S_BK, CU_TENSOR_MAP_SWIZZLE_64B);
+  } else {
+    const int bn = tc_variant_bn(variant);
+    bad |= make_map(&mp->a1h, r.a1h, rows_cap, r.kpad, tc::BM) | make_map(&mp->a1l, r.a1l, rows_cap, r.kpad, tc::BM);
+    bad |= make_map(&mp->a2h, r.a2h, rows_cap, r.kpad, tc::BM) | make_map(&mp->a2l, r.a2l, rows_cap, r.kpad, tc::BM);
+    bad |= make_map(&mp->bh, r.bh, npw, r.kpad, bn) | make_map(&mp->bl, r.bl, npw, r.kpad, bn);
+  }
+  if (bad) {
     delete mp;
     return cudaErrorInvalidValue;
   }
@@ -80,6 +98,8 @@ cudaError_t tc_init(TcResources &r, void *mem, int rows_cap, int npw, int varian
   e = cudaFuncSetAttribute(tc::k_tc_cgemm_drain<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            tc::TcCfg<64, 2>::SMEM_BYTES);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(tc::k_tc_cgemm_stacked, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::S_SMEM);
+  if (e != cudaSuccess) return e;
   return cudaMemset(r.err, 0, sizeof(int));
 }
 
@@ -96,12 +116,22 @@ cudaError_t tc_pack_b(const TcResources &r, const void *pt, cudaStream_t st) {
 
 cudaError_t tc_wgemm(const TcResources &r, const void *st_in, int rows, void *wt, cudaStream_t st) {
   if (rows > r.rows_cap) return cudaErrorInvalidValue;
-  tc::k_pack_a<<<dim3((r.kpad / 2 + 255) / 256, rows), 256, 0, st>>>(static_cast<const float2 *>(st_in), rows,
-                                                                       r.npw, r.kpad, r.a1h, r.a1l, r.a2h, r.a2l);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   const tc::TcMaps &m = *static_cast<const tc::TcMaps *>(r.maps);
   const int variant = r.variant;
+  cudaError_t e;
+  if (variant == 5) {
+    const int r64 = ((rows + 63) / 64) * 64;   // zero-filled up to a whole 64-row block
+    tc::k_pack_a_stacked<<<dim3((r.kpad / 2 + 255) / 256, r64), 256, 0, st>>>(
+        static_cast<const float2 *>(st_in), rows, r.npw, r.kpad, r.a1h, r.a1l);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dim3 grid((r.npw + tc::S_BN - 1) / tc::S_BN, r64 / 64);
+    tc::k_tc_cgemm_stacked<<<grid, 160, tc::S_SMEM, st>>>(m.a1h, m.a1l, m.bh, m.bl, rows, r.npw, r.kpad / tc::S_BK,
+                                                          static_cast<float2 *>(wt), r.npw, r.err);
+    return cudaGetLastError();
+  }
+  tc::k_pack_a<<<dim3((r.kpad / 2 + 255) / 256, rows), 256, 0, st>>>(static_cast<const float2 *>(st_in), rows,
+                                                                       r.npw, r.kpad, r.a1h, r.a1l, r.a2h, r.a2l);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
 #define LTMP2_TC_LAUNCH(BN, NR)                                                                              \
   {                                                                                                          \
     dim3 grid((r.npw + BN - 1) / BN, (rows + tc::BM - 1) / tc::BM);                                          \

@@ -10,9 +10,11 @@
 //     Re W = A1 B^T,  Im W = A2 B^T.
 // Each operand x is split as x_hi = tf32(x), x_lo = tf32(x - x_hi) (round to nearest),
 // and every product is x_hi y_hi + x_hi y_lo + x_lo y_hi, accumulated in FP32 in tensor
-// memory.  Operands arrive by TMA (128-byte swizzle) into a two-stage shared-memory ring;
-// one thread issues the TMA copies and the MMAs; four warps drain the accumulators.
-// Every wait is bounded: on expiry the kernel raises an error flag instead of hanging.
+// memory.  Operands arrive by TMA into a shared-memory ring; one thread issues the TMA
+// copies and the MMAs; four warps read the accumulators.  The production kernel is
+// k_tc_cgemm_stacked (end of file); the earlier variants stay for the accumulation-drift
+// measurements.  Every wait is bounded: on expiry the kernel raises an error flag instead
+// of hanging.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -432,6 +434,180 @@ __global__ void __launch_bounds__(160, 1)
   __syncthreads();
   fence_after();
   if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
+}
+
+// ---------------------------------------------------------------- stacked, deep-ring variant
+// One MMA row tile of 128 = 64 complex rows of A1 (rows 0-63) stacked over the same 64
+// rows of A2 (rows 64-127), so a single accumulator holds Re (lanes 0-63) and Im
+// (lanes 64-127) of a 64 x BN2 block of W^T.  K blocks of 16 fp32 (64-byte swizzle)
+// make a stage 32 KB: A hi, A lo, B hi, B lo.  Six stages are in flight.  Accumulators
+// alternate between two tensor-memory regions and are drained into FP32 register sums
+// every DRAIN stages (12 MMAs per region, as in the drained variant above).
+constexpr int S_BK = 16;                   // fp32 per k block (64 bytes)
+constexpr int S_BN = 128;
+constexpr int S_TILE = 128 * 64;           // 128 rows x 64 bytes
+constexpr int S_STAGE = 4 * S_TILE;
+constexpr int S_STAGES = 6;
+constexpr int S_DRAIN = 2;                 // stages per accumulator region
+constexpr int S_SMEM = S_STAGES * S_STAGE + 1024;
+constexpr int S_TMEM_COLS = 2 * S_BN;
+constexpr uint32_t S_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(S_BN >> 3) << 17) |
+                             ((uint32_t)(128 >> 4) << 24);
+
+// K-major operand, 64-byte swizzle: 8-row core groups 512 bytes apart
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
+// S^T complex [rows][npw] -> stacked A hi/lo fp32 [2 * rows_pad64][kpad]:
+// row 128 b + r = A1 row 64 b + r, row 128 b + 64 + r = A2 row 64 b + r
+__global__ void k_pack_a_stacked(const float2 *__restrict__ st, int rows, int npw, int kpad,
+                                 float *__restrict__ ah, float *__restrict__ al) {
+  const int m = blockIdx.y;
+  const int half = kpad / 2;
+  const size_t r1 = (size_t)128 * (m / 64) + (m % 64), r2 = r1 + 64;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < half; q += gridDim.x * blockDim.x) {
+    float re = 0.f, im = 0.f;
+    if (q < npw && m < rows) {
+      const float2 v = st[(size_t)m * npw + q];
+      re = v.x;
+      im = v.y;
+    }
+    const float h_re = tf32_rn(re), l_re = tf32_rn(re - h_re);
+    const float h_im = tf32_rn(im), l_im = tf32_rn(im - h_im);
+    const size_t o1 = r1 * kpad + 2 * q, o2 = r2 * kpad + 2 * q;
+    ah[o1] = h_re; ah[o1 + 1] = -h_im;
+    al[o1] = l_re; al[o1 + 1] = -l_im;
+    ah[o2] = h_im; ah[o2 + 1] = h_re;
+    al[o2] = l_im; al[o2 + 1] = l_re;
+  }
+}
+
+__global__ void __launch_bounds__(160, 1)
+    k_tc_cgemm_stacked(const __grid_constant__ CUtensorMap tah, const __grid_constant__ CUtensorMap tal,
+                       const __grid_constant__ CUtensorMap tbh, const __grid_constant__ CUtensorMap tbl, int M,
+                       int N, int kblocks, float2 *__restrict__ C, int ldc, int *__restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t full_bar[S_STAGES], empty_bar[S_STAGES], accf_bar[2], acce_bar[2], done_bar;
+  __shared__ uint32_t tmem_slot;
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int arow0 = blockIdx.y * 128;     // stacked operand rows
+  const int m0 = blockIdx.y * 64;         // complex rows of W^T
+  const int n0 = blockIdx.x * S_BN;
+  const int ndrain = (kblocks + S_DRAIN - 1) / S_DRAIN;
+
+  if (warp == 0) tmem_alloc(&tmem_slot, S_TMEM_COLS);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S_STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int r = 0; r < 2; ++r) {
+      mbar_init(&accf_bar[r], 1);
+      mbar_init(&acce_bar[r], 128);
+    }
+    mbar_init(&done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+  bool ok = true;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      auto issue = [&](int kb, int s) {
+        unsigned char *st = smem + s * S_STAGE;
+        mbar_expect_tx(&full_bar[s], S_STAGE);
+        const int x = kb * S_BK;
+        tma_load_2d(st + 0 * S_TILE, &tah, &full_bar[s], x, arow0);
+        tma_load_2d(st + 1 * S_TILE, &tal, &full_bar[s], x, arow0);
+        tma_load_2d(st + 2 * S_TILE, &tbh, &full_bar[s], x, n0);
+        tma_load_2d(st + 3 * S_TILE, &tbl, &full_bar[s], x, n0);
+      };
+      for (int s = 0; s < S_STAGES && s < kblocks; ++s) issue(s, s);
+      for (int kb = 0; kb < kblocks; ++kb) {
+        const int s = kb % S_STAGES;
+        const int db = kb / S_DRAIN, r = db & 1;
+        if (!mbar_wait(&full_bar[s], (uint32_t)((kb / S_STAGES) & 1))) { ok = false; break; }
+        if (kb % S_DRAIN == 0 && db >= 2 && !mbar_wait(&acce_bar[r], (uint32_t)(((db - 2) >> 1) & 1))) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t base = smem_u32(smem + s * S_STAGE);
+        const uint32_t d = tmem + (uint32_t)r * S_BN;
+#pragma unroll
+        for (int k = 0; k < S_BK / 8; ++k) {
+          const uint32_t ko = k * 32;
+          const uint64_t ah = sdesc_sw64(base + 0 * S_TILE + ko), al = sdesc_sw64(base + 1 * S_TILE + ko);
+          const uint64_t bh = sdesc_sw64(base + 2 * S_TILE + ko), bl = sdesc_sw64(base + 3 * S_TILE + ko);
+          const uint32_t acc = (kb % S_DRAIN == 0 && k == 0) ? 0u : 1u;
+          mma_tf32(d, ah, bh, S_IDESC, acc);
+          mma_tf32(d, ah, bl, S_IDESC, 1u);
+          mma_tf32(d, al, bh, S_IDESC, 1u);
+        }
+        mma_commit(&empty_bar[s]);
+        if (kb % S_DRAIN == S_DRAIN - 1 || kb == kblocks - 1) mma_commit(&accf_bar[r]);
+        // refill the stage of k block kb - 1 once its MMAs are done (those of kb are queued)
+        if (kb >= 1 && kb - 1 + S_STAGES < kblocks) {
+          const int sp = (kb - 1) % S_STAGES;
+          if (!mbar_wait(&empty_bar[sp], (uint32_t)(((kb - 1) / S_STAGES) & 1))) { ok = false; break; }
+          issue(kb - 1 + S_STAGES, sp);
+        }
+      }
+      mma_commit(&done_bar);
+      if (!ok) atomicExch(err, 1);
+    }
+  } else {
+    float sum[S_BN];
+#pragma unroll
+    for (int j = 0; j < S_BN; ++j) sum[j] = 0.f;
+    const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int db = 0; db < ndrain; ++db) {
+      const int r = db & 1;
+      if (!mbar_wait(&accf_bar[r], (uint32_t)((db >> 1) & 1))) { ok = false; break; }
+      fence_after();
+#pragma unroll
+      for (int c = 0; c < S_BN / 32; ++c) {
+        float v[32];
+        tmem_ld32(t_lane + r * S_BN + c * 32, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sum[c * 32 + j] += v[j];
+      }
+      fence_before();
+      mbar_arrive(&acce_bar[r]);
+    }
+    if (!ok && lane == 0) atomicExch(err, 1);
+    // pair Re (warps 0, 1) with Im (warps 2, 3) through shared memory: the ring is idle
+    const bool done_ok = mbar_wait(&done_bar, 0);
+    if (!done_ok && lane == 0) atomicExch(err, 1);
+    float *stage = reinterpret_cast<float *>(smem);   // [128][S_BN + 1]
+    const int row = warp * 32 + lane;
+#pragma unroll
+    for (int j = 0; j < S_BN; ++j) stage[row * (S_BN + 1) + j] = sum[j];
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    for (int e = threadIdx.x; e < 64 * S_BN; e += 128) {
+      const int rr = e / S_BN, cc = e % S_BN;
+      const int gm = m0 + rr, gn = n0 + cc;
+      if (ok && done_ok && gm < M && gn < N)
+        C[(size_t)gm * ldc + gn] = make_float2(stage[rr * (S_BN + 1) + cc], stage[(rr + 64) * (S_BN + 1) + cc]);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) tmem_dealloc(tmem, S_TMEM_COLS);
 }
 
 }  // namespace tc

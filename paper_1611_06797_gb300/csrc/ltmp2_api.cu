@@ -248,7 +248,7 @@ template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys,
   if (std::is_same<T, float>::value && !(sys->flags & LTMP2_FLAG_SIMT_GEMM)) {
     void *tcmem = nullptr;
     if ((rc = dalloc_bytes(c, &tcmem, tc_bytes((int)max_cols, p.n_pw)))) return rc;
-    e = tc_init(c->tc, tcmem, (int)max_cols, p.n_pw, 4);
+    e = tc_init(c->tc, tcmem, (int)max_cols, p.n_pw, 5);
     if (e != cudaSuccess) return cuda_status(e);
     p.tc = &c->tc;
   }

@@ -9,7 +9,7 @@ namespace ltmp2 {
 // Operands, tensor maps and error flag of the tcgen05 3xTF32 GEMM (precision form).
 struct TcResources {
   int rows_cap = 0, npw = 0, kpad = 0;
-  int variant = 3;         // tile / accumulator layout: 0 (128,1) 1 (128,2) 2 (64,2) 3 (64,4)
+  int variant = 5;         // 0-3 single-pass (tests), 4 drained N=64, 5 stacked Re/Im deep ring
   float *a1h = nullptr, *a1l = nullptr, *a2h = nullptr, *a2l = nullptr, *bh = nullptr, *bl = nullptr;
   int *err = nullptr;      // device flag: a bounded wait ran out
   void *maps = nullptr;    // host copy of the six TMA tensor maps
