@@ -159,6 +159,44 @@ int ltmp2_energy_partial(ltmp2_ctx *ctx, int n_tau, const double *tau, const dou
  * slab size in effect, or a negative status.                                     */
 int ltmp2_set_slab_size(ltmp2_ctx *ctx, int n);
 
+/* ---------------------------------------------------------------- batching form
+ * Several systems of uneven grids and orbital counts in one launch.  The outer loops
+ * of Sec. III A (tau points, then slabs of the G' loop, Sec. III B) of every system are
+ * captured into one CUDA graph, one branch per system on its own stream, so a run is a
+ * single graph launch in which the systems' kernels overlap on the GPU.               */
+
+/* Autotuner: times one slab of the path for each candidate (slab sizes down from the
+ * setup capacity; in LTMP2_FP32 also the two tensor-core GEMM layouts) and keeps the
+ * fastest per primary G'.  The choice is cached per (grid, n_pw, n_occ, |A|, precision,
+ * real-orbital flag) for the process and applied to ctx.  slab, gemm_variant: NULL or
+ * receive the choice (gemm_variant = -1 in LTMP2_FP64).  Errors: INVALID_ARG, CUDA,
+ * TIMEOUT.                                                                          */
+int ltmp2_autotune(ltmp2_ctx *ctx, int *slab, int *gemm_variant);
+
+typedef struct ltmp2_batch ltmp2_batch; /* opaque; a captured, instantiated graph */
+
+/* Capture the full energy evaluation of n distinct contexts (each with its own
+ * quadrature: n_tau[i], tau[i][*], w[i][*], host arrays copied into the graph) into one
+ * CUDA graph.  The contexts must stay alive, on one device and with unchanged slab /
+ * tuning settings, until ltmp2_batch_destroy.  Nothing runs yet.
+ * Errors: INVALID_ARG (NULL, duplicate ctx, bad tau), OOM, CUDA.                     */
+int ltmp2_batch_create(ltmp2_ctx *const *ctxs, int n, const int *n_tau, const double *const *tau,
+                       const double *const *w, ltmp2_batch **out);
+
+/* One graph launch on the stream of ctxs[0]; waits for it and writes E_direct[i] and
+ * E_exchange[i] (host arrays of n).  Per-pair energies stay readable through each
+ * context's accumulators only via ltmp2_energy.  Errors: INVALID_ARG, CUDA, TIMEOUT. */
+int ltmp2_batch_run(ltmp2_batch *b, double *e_direct, double *e_exchange);
+
+/* Number of kernel nodes in the batch graph (all systems).                          */
+int ltmp2_batch_kernel_nodes(const ltmp2_batch *b, long long *count);
+
+void ltmp2_batch_destroy(ltmp2_batch *b);
+
+/* Autotune every context, then create, run once and destroy a batch.                */
+int ltmp2_energy_batch(ltmp2_ctx *const *ctxs, int n, const int *n_tau, const double *const *tau,
+                       const double *const *w, double *e_direct, double *e_exchange);
+
 /* Number of primary G' vectors (half of |A|); returns < 0 on a NULL ctx.        */
 int ltmp2_num_primary_gprime(const ltmp2_ctx *ctx);
 

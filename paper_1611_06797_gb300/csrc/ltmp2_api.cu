@@ -10,6 +10,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <tuple>
 #include <vector>
@@ -88,6 +89,7 @@ struct ltmp2_ctx {
   int slab_capacity = 0;
   long long kernel_launches = 0;
   TcResources tc;
+  void *tc_mem = nullptr;   // operand buffers of the tensor-core GEMM (owned via allocs)
   ~ltmp2_ctx() {
     tc_release(tc);
     for (void *q : allocs) cudaFree(q);
@@ -248,6 +250,7 @@ template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys,
   if (std::is_same<T, float>::value && !(sys->flags & LTMP2_FLAG_SIMT_GEMM)) {
     void *tcmem = nullptr;
     if ((rc = dalloc_bytes(c, &tcmem, tc_bytes((int)max_cols, p.n_pw)))) return rc;
+    c->tc_mem = tcmem;
     e = tc_init(c->tc, tcmem, (int)max_cols, p.n_pw, 5);
     if (e != cudaSuccess) return cuda_status(e);
     p.tc = &c->tc;
@@ -258,43 +261,56 @@ template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys,
   return cuda_status(e);
 }
 
+// Launch (without waiting) everything one energy evaluation does on `stream`.  Usable
+// inside stream capture: no allocation, copy or synchronisation happens here.
 template <typename T>
-int run_energy(ltmp2_ctx *c, int n_tau, const double *tau, const double *w, int gp_begin, int gp_end) {
+int enqueue_energy(ltmp2_ctx *c, cudaStream_t stream, int n_tau, const double *tau, const double *w, int gp_begin,
+                   int gp_end, StageTimer *tm, long long *launches) {
   Plan &p = c->p;
-  StageTimer *tm = c->timer.on ? &c->timer : nullptr;
-  c->timer.stream = c->stream;
-  cudaError_t e = Path<T>::zero_acc(p, c->stream);
+  cudaError_t e = Path<T>::zero_acc(p, stream);
   if (e != cudaSuccess) return cuda_status(e);
-  c->kernel_launches += 2;  // zero + final reduction
+  *launches += 2;  // zero + final reduction
   const double nfft = (double)p.n * p.n * p.n;
   for (int k = 0; k < n_tau; ++k) {
-    e = Path<T>::green(p, tau[k], c->stream, tm);
+    e = Path<T>::green(p, tau[k], stream, tm);
     if (e != cudaSuccess) return cuda_status(e);
-    c->kernel_launches += Path<T>::green_launches(p);
+    *launches += Path<T>::green_launches(p);
     const double coef = w[k] / (p.omega * p.omega * nfft * nfft);
     for (int g0 = gp_begin; g0 < gp_end; g0 += p.max_prim) {
       const int np = std::min(p.max_prim, gp_end - g0);
-      e = Path<T>::slab(p, g0, np, coef, c->stream, tm);
+      e = Path<T>::slab(p, g0, np, coef, stream, tm);
       if (e != cudaSuccess) return cuda_status(e);
-      c->kernel_launches += Path<T>::slab_launches(p);
+      *launches += Path<T>::slab_launches(p);
     }
   }
-  e = Path<T>::finish(p, c->stream, tm);
+  e = Path<T>::finish(p, stream, tm);
+  return cuda_status(e);
+}
+
+// After the work is complete: a bounded wait inside the tensor-core GEMM that ran out is
+// reported (and the flag cleared).
+int check_tc_flag(ltmp2_ctx *c) {
+  if (!c->p.tc) return LTMP2_OK;
+  int flag = 0;
+  cudaError_t e = cudaMemcpy(&flag, c->p.tc->err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_status(e);
-  e = cudaStreamSynchronize(c->stream);
-  if (tm) c->timer.collect();
-  if (e != cudaSuccess) return cuda_status(e);
-  if (p.tc) {
-    // a bounded wait inside the tensor-core GEMM ran out: report, clear the flag
-    int flag = 0;
-    e = cudaMemcpy(&flag, p.tc->err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (flag) {
-      cudaMemset(p.tc->err, 0, sizeof(int));
-      return LTMP2_ERR_TIMEOUT;
-    }
+  if (flag) {
+    cudaMemset(c->p.tc->err, 0, sizeof(int));
+    return LTMP2_ERR_TIMEOUT;
   }
   return LTMP2_OK;
+}
+
+template <typename T>
+int run_energy(ltmp2_ctx *c, int n_tau, const double *tau, const double *w, int gp_begin, int gp_end) {
+  StageTimer *tm = c->timer.on ? &c->timer : nullptr;
+  c->timer.stream = c->stream;
+  int rc = enqueue_energy<T>(c, c->stream, n_tau, tau, w, gp_begin, gp_end, tm, &c->kernel_launches);
+  if (rc) return rc;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (tm) c->timer.collect();
+  if (e != cudaSuccess) return cuda_status(e);
+  return check_tc_flag(c);
 }
 
 int check_tau(int n_tau, const double *tau, const double *w) {
@@ -335,6 +351,111 @@ int energy_common(ltmp2_ctx *ctx, int n_tau, const double *tau, const double *w,
   return LTMP2_OK;
 }
 
+
+// ---------------------------------------------------------------- autotuner
+// Slab size (primary G' per pass) and tensor-core GEMM variant, chosen by timing one
+// slab per candidate; cached per (grid, N_pw, N_occ, |A|, precision, real) bucket.
+struct TuneKey {
+  int n, n_pw, n_occ, n_aux, precision, real;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(n, n_pw, n_occ, n_aux, precision, real) <
+           std::tie(o.n, o.n_pw, o.n_occ, o.n_aux, o.precision, o.real);
+  }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;  // -> (slab, gemm variant or -1)
+
+int apply_tuning(ltmp2_ctx *c, int slab, int variant) {
+  if (slab < 1 || slab > c->slab_capacity) return LTMP2_ERR_INVALID_ARG;
+  c->p.max_prim = slab;
+  if (c->p.tc && variant >= 0 && variant != c->tc.variant) {
+    tc_release(c->tc);
+    cudaError_t e = tc_init(c->tc, c->tc_mem, c->tc.rows_cap, c->p.n_pw, variant);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return LTMP2_OK;
+}
+
+template <typename T> int tune_ctx(ltmp2_ctx *c, int *slab_out, int *var_out) {
+  Plan &p = c->p;
+  const TuneKey key{p.n, p.n_pw, p.n_occ, p.n_aux, p.precision, p.real_orb ? 1 : 0};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      int rc = apply_tuning(c, std::min(it->second.first, c->slab_capacity), it->second.second);
+      *slab_out = p.max_prim;
+      *var_out = p.tc ? c->tc.variant : -1;
+      return rc;
+    }
+  }
+  std::vector<int> slabs;
+  for (int sl = std::min(c->slab_capacity, p.n_prim); sl >= 1 && slabs.size() < 4; sl /= 2) slabs.push_back(sl);
+  std::vector<int> variants = p.tc ? std::vector<int>{5, 4} : std::vector<int>{-1};
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return LTMP2_ERR_CUDA;
+  double best = 1e300;
+  int best_slab = slabs.front(), best_var = variants.front();
+  int rc = LTMP2_OK;
+  for (int v : variants) {
+    if ((rc = apply_tuning(c, slabs.front(), v))) break;
+    if (Path<T>::green(p, 1.0, c->stream, nullptr) != cudaSuccess) { rc = LTMP2_ERR_CUDA; break; }
+    for (int sl : slabs) {
+      p.max_prim = sl;
+      // one untimed pass, then two timed ones (weight 0: accumulators unchanged)
+      for (int rep = 0; rep < 3 && !rc; ++rep) {
+        if (rep == 1) cudaEventRecord(a, c->stream);
+        if (Path<T>::slab(p, 0, sl, 0.0, c->stream, nullptr) != cudaSuccess) rc = LTMP2_ERR_CUDA;
+      }
+      if (rc) break;
+      cudaEventRecord(b, c->stream);
+      if (cudaEventSynchronize(b) != cudaSuccess) { rc = LTMP2_ERR_CUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      const double per_prim = ms / (2.0 * sl);
+      if (per_prim < best) { best = per_prim; best_slab = sl; best_var = v; }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (!rc) rc = check_tc_flag(c);
+  if (!rc) rc = apply_tuning(c, best_slab, best_var);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = {best_slab, best_var};
+  }
+  *slab_out = best_slab;
+  *var_out = p.tc ? best_var : -1;
+  return LTMP2_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- batching form
+// Every system's whole evaluation (all tau, all slabs) captured into one CUDA graph: one
+// branch per system on its own forked stream, joined at the end.  A run is one graph
+// launch; the graph is replayed by ltmp2_batch_run.
+struct ltmp2_batch {
+  int device = 0;
+  std::vector<ltmp2_ctx *> ctxs;
+  std::vector<long long> launches;
+  cudaStream_t origin = nullptr;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~ltmp2_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto e : events) cudaEventDestroy(e);
+    for (auto st : streams) cudaStreamDestroy(st);
+    if (origin) cudaStreamDestroy(origin);
+  }
+};
+
+namespace {
 }  // namespace
 
 extern "C" {
@@ -645,6 +766,122 @@ void ltmp2_destroy(ltmp2_ctx *ctx) {
   DeviceGuard g(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   delete ctx;
+}
+
+int ltmp2_autotune(ltmp2_ctx *ctx, int *slab, int *gemm_variant) {
+  if (!ctx) return LTMP2_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  int sl = 0, var = -1;
+  const int rc = ctx->p.precision == LTMP2_FP64 ? tune_ctx<double>(ctx, &sl, &var) : tune_ctx<float>(ctx, &sl, &var);
+  if (rc) return rc;
+  if (slab) *slab = sl;
+  if (gemm_variant) *gemm_variant = var;
+  return LTMP2_OK;
+}
+
+int ltmp2_batch_create(ltmp2_ctx *const *ctxs, int n, const int *n_tau, const double *const *tau,
+                       const double *const *w, ltmp2_batch **out) {
+  if (!ctxs || !n_tau || !tau || !w || !out || n < 1) return LTMP2_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return LTMP2_ERR_INVALID_ARG;
+    if (ctxs[i]->device != ctxs[0]->device) return LTMP2_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return LTMP2_ERR_INVALID_ARG;
+    const int rc = check_tau(n_tau[i], tau[i], w[i]);
+    if (rc) return rc;
+  }
+  DeviceGuard g(ctxs[0]->device);
+  ltmp2_batch *b = new (std::nothrow) ltmp2_batch();
+  if (!b) return LTMP2_ERR_OOM;
+  b->device = ctxs[0]->device;
+  b->ctxs.assign(ctxs, ctxs + n);
+  b->launches.assign(n, 0);
+  auto fail = [&](int rc) {
+    cudaGetLastError();
+    delete b;
+    return rc;
+  };
+  if (cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess) return fail(LTMP2_ERR_CUDA);
+  b->streams.resize(n, nullptr);
+  b->events.resize(n + 1, nullptr);
+  for (int i = 0; i < n; ++i)
+    if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess) return fail(LTMP2_ERR_CUDA);
+  for (auto &e : b->events)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(LTMP2_ERR_CUDA);
+  if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(LTMP2_ERR_CUDA);
+  int rc = cuda_status(cudaEventRecord(b->events[n], b->origin));
+  for (int i = 0; i < n && !rc; ++i) {
+    ltmp2_ctx *c = ctxs[i];
+    rc = cuda_status(cudaStreamWaitEvent(b->streams[i], b->events[n], 0));
+    if (!rc)
+      rc = c->p.precision == LTMP2_FP64
+               ? enqueue_energy<double>(c, b->streams[i], n_tau[i], tau[i], w[i], 0, c->p.n_prim, nullptr,
+                                        &b->launches[i])
+               : enqueue_energy<float>(c, b->streams[i], n_tau[i], tau[i], w[i], 0, c->p.n_prim, nullptr,
+                                       &b->launches[i]);
+    if (!rc) rc = cuda_status(cudaEventRecord(b->events[i], b->streams[i]));
+    if (!rc) rc = cuda_status(cudaStreamWaitEvent(b->origin, b->events[i], 0));
+  }
+  const cudaError_t ec = cudaStreamEndCapture(b->origin, &b->graph);
+  if (rc) return fail(rc);
+  if (ec != cudaSuccess) return fail(LTMP2_ERR_CUDA);
+  if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) return fail(LTMP2_ERR_CUDA);
+  *out = b;
+  return LTMP2_OK;
+}
+
+int ltmp2_batch_run(ltmp2_batch *b, double *e_direct, double *e_exchange) {
+  if (!b || !e_direct || !e_exchange) return LTMP2_ERR_INVALID_ARG;
+  DeviceGuard g(b->device);
+  cudaStream_t st = b->ctxs[0]->stream;
+  cudaError_t e = cudaGraphLaunch(b->exec, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    ltmp2_ctx *c = b->ctxs[i];
+    int rc = check_tc_flag(c);
+    if (rc) return rc;
+    double es[4];
+    e = cudaMemcpy(es, c->p.esum, sizeof(es), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    e_direct[i] = es[0];
+    e_exchange[i] = es[1];
+    c->last_imag[0] = es[2];
+    c->last_imag[1] = es[3];
+    c->kernel_launches += b->launches[i];
+  }
+  return LTMP2_OK;
+}
+
+int ltmp2_batch_kernel_nodes(const ltmp2_batch *b, long long *count) {
+  if (!b || !count) return LTMP2_ERR_INVALID_ARG;
+  long long t = 0;
+  for (long long x : b->launches) t += x;
+  *count = t;
+  return LTMP2_OK;
+}
+
+void ltmp2_batch_destroy(ltmp2_batch *b) {
+  if (!b) return;
+  DeviceGuard g(b->device);
+  delete b;
+}
+
+int ltmp2_energy_batch(ltmp2_ctx *const *ctxs, int n, const int *n_tau, const double *const *tau,
+                       const double *const *w, double *e_direct, double *e_exchange) {
+  if (!ctxs || n < 1 || !e_direct || !e_exchange) return LTMP2_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return LTMP2_ERR_INVALID_ARG;
+    const int rc = ltmp2_autotune(ctxs[i], nullptr, nullptr);
+    if (rc) return rc;
+  }
+  ltmp2_batch *b = nullptr;
+  int rc = ltmp2_batch_create(ctxs, n, n_tau, tau, w, &b);
+  if (rc) return rc;
+  rc = ltmp2_batch_run(b, e_direct, e_exchange);
+  ltmp2_batch_destroy(b);
+  return rc;
 }
 
 }  // extern "C"

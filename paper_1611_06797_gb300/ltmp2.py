@@ -279,3 +279,93 @@ def ltmp2_energy_noalloc(lattice, grid, miller, coeff, eps, n_occ: int, tau, w, 
     _check(f(ctypes.byref(s), len(tau), _dp(tau), _dp(w), _dp(ed), _dp(ex), _dp(ep) if pairs else None,
              ctypes.c_void_p(int(handle) if handle else 0)), "ltmp2_energy_noalloc")
     return float(ed[0]), float(ex[0]), ep
+
+
+# ---------------------------------------------------------------- batching form
+def _batch_sig(lib):
+    P = ctypes.POINTER
+    dp = P(ctypes.c_double)
+    vp = ctypes.c_void_p
+    for name, res, args in [
+            ("ltmp2_autotune", ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int)]),
+            ("ltmp2_batch_create", ctypes.c_int, [P(vp), ctypes.c_int, P(ctypes.c_int), P(dp), P(dp), P(vp)]),
+            ("ltmp2_batch_run", ctypes.c_int, [vp, dp, dp]),
+            ("ltmp2_batch_kernel_nodes", ctypes.c_int, [vp, P(ctypes.c_longlong)]),
+            ("ltmp2_batch_destroy", None, [vp]),
+            ("ltmp2_energy_batch", ctypes.c_int, [P(vp), ctypes.c_int, P(ctypes.c_int), P(dp), P(dp), dp, dp])]:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+def ltmp2_autotune(ctx: Context):
+    """Returns (slab, gemm_variant) chosen and applied for ctx."""
+    lib = _batch_sig(load_library())
+    sl, var = ctypes.c_int(), ctypes.c_int()
+    _check(lib.ltmp2_autotune(ctx.handle, ctypes.byref(sl), ctypes.byref(var)), "ltmp2_autotune")
+    return sl.value, var.value
+
+
+def _batch_args(ctxs, taus, ws):
+    n = len(ctxs)
+    handles = (ctypes.c_void_p * n)(*[c.handle.value for c in ctxs])
+    keep = []
+    tps = (ctypes.POINTER(ctypes.c_double) * n)()
+    wps = (ctypes.POINTER(ctypes.c_double) * n)()
+    nt = (ctypes.c_int * n)()
+    for i, (t, w) in enumerate(zip(taus, ws)):
+        t = np.ascontiguousarray(np.asarray(t, dtype=np.float64))
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+        keep += [t, w]
+        tps[i] = _dp(t)
+        wps[i] = _dp(w)
+        nt[i] = len(t)
+    return n, handles, nt, tps, wps, keep
+
+
+class Batch:
+    """A captured CUDA graph evaluating several contexts in one launch."""
+
+    def __init__(self, ctxs, taus, ws):
+        lib = _batch_sig(load_library())
+        self.ctxs = list(ctxs)          # keep the contexts alive
+        n, handles, nt, tps, wps, keep = _batch_args(ctxs, taus, ws)
+        h = ctypes.c_void_p()
+        _check(lib.ltmp2_batch_create(handles, n, nt, tps, wps, ctypes.byref(h)), "ltmp2_batch_create")
+        self.handle = h
+        self.n = n
+
+    def run(self):
+        ed, ex = np.zeros(self.n), np.zeros(self.n)
+        _check(load_library().ltmp2_batch_run(self.handle, _dp(ed), _dp(ex)), "ltmp2_batch_run")
+        return ed, ex
+
+    def kernel_nodes(self) -> int:
+        c = ctypes.c_longlong()
+        _check(load_library().ltmp2_batch_kernel_nodes(self.handle, ctypes.byref(c)), "ltmp2_batch_kernel_nodes")
+        return int(c.value)
+
+    def destroy(self):
+        if self.handle is not None and self.handle.value:
+            load_library().ltmp2_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def ltmp2_batch_create(ctxs, taus, ws) -> Batch:
+    return Batch(ctxs, taus, ws)
+
+
+def ltmp2_energy_batch(ctxs, taus, ws):
+    """Autotune, capture and run once.  Returns (E_direct[n], E_exchange[n])."""
+    lib = _batch_sig(load_library())
+    n, handles, nt, tps, wps, keep = _batch_args(ctxs, taus, ws)
+    ed, ex = np.zeros(n), np.zeros(n)
+    _check(lib.ltmp2_energy_batch(handles, n, nt, tps, wps, _dp(ed), _dp(ex)), "ltmp2_energy_batch")
+    return ed, ex

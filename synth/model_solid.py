@@ -86,6 +86,17 @@ SPECS = {
 }
 
 
+# Batching workload: 8 systems of uneven size (wells 4..48, occupied 8..96, grids 16^3..32^3,
+# sphere radius 0.375 n index units, a = 6 bohr * wells^(1/3), 6..10 Laplace points).
+_BATCH = [(4, 16, 6, (2, 2, 1)), (8, 18, 6, (2, 2, 2)), (12, 20, 7, (3, 2, 2)), (18, 24, 8, (3, 3, 2)),
+          (24, 25, 8, (4, 3, 2)), (32, 27, 9, (4, 4, 2)), (40, 30, 10, (5, 4, 2)), (48, 32, 10, (4, 4, 3))]
+for _k, (_w, _n, _t, _sites) in enumerate(_BATCH):
+    SPECS[f"batch{_k}"] = ModelSolidSpec(f"batch{_k}", a=round(6.0 * _w ** (1.0 / 3.0), 6), grid=_n,
+                                         r2=int((0.375 * _n) ** 2), wells=_w, n_occ=2 * _w, n_tau=_t,
+                                         seed=41 + _k, lattice_sites=_sites)
+BATCH_NAMES = [f"batch{_k}" for _k in range(len(_BATCH))]
+
+
 def spec_by_name(name: str) -> ModelSolidSpec:
     return SPECS[name]
 
@@ -180,59 +191,76 @@ def well_positions(spec: ModelSolidSpec) -> np.ndarray:
     return sites + rng.normal(0.0, spec.jitter, size=sites.shape)
 
 
-def _real_basis(miller: np.ndarray) -> np.ndarray:
-    """Unitary U (PW basis <- cos/sin basis): columns are real functions in real space."""
-    n = miller.shape[0]
-    key = {tuple(m): k for k, m in enumerate(miller.tolist())}
-    U = np.zeros((n, n), dtype=np.complex128)
-    col = 0
-    done = np.zeros(n, dtype=bool)
-    s = 1.0 / math.sqrt(2.0)
-    for k, m in enumerate(miller.tolist()):
-        if done[k]:
-            continue
-        mk = key.get((-m[0], -m[1], -m[2]))
-        if mk is None:
-            raise ValueError("plane-wave set is not inversion symmetric")
-        if mk == k:  # G = 0
-            U[k, col] = 1.0
-            col += 1
-            done[k] = True
-            continue
-        U[k, col] = s
-        U[mk, col] = s
-        U[k, col + 1] = -1j * s
-        U[mk, col + 1] = 1j * s
-        col += 2
-        done[k] = done[mk] = True
-    assert col == n
-    return U
-
-
 def hamiltonian(miller: np.ndarray, lattice: np.ndarray, positions: np.ndarray,
                 depth: float, width: float) -> np.ndarray:
+    """H_pq = |G_p|^2/2 delta_pq + V(G_p - G_q), with V tabulated once on the box of
+    Miller-index differences (structure factor over the wells computed per difference)."""
     B = 2.0 * math.pi * np.linalg.inv(lattice).T
     omega = abs(float(np.linalg.det(lattice)))
-    G = miller.astype(np.float64) @ B
-    dG = G[:, None, :] - G[None, :, :]
-    g2 = (dG ** 2).sum(-1)
+    R = int(np.abs(miller).max())
+    L = 4 * R + 1
+    rng = np.arange(-2 * R, 2 * R + 1)
+    box = np.stack(np.meshgrid(rng, rng, rng, indexing="ij"), -1).reshape(-1, 3)
+    Gb = box.astype(np.float64) @ B
+    g2b = (Gb ** 2).sum(-1)
+    sf = np.zeros(len(box), dtype=np.complex128)
+    for Rw in positions:
+        sf += np.exp(-1j * (Gb @ Rw))
     pref = -(depth / omega) * (2.0 * math.pi * width ** 2) ** 1.5
-    phase = np.zeros(g2.shape, dtype=np.complex128)
-    for R in positions:
-        phase += np.exp(-1j * (dG @ R))
-    H = pref * np.exp(-0.5 * g2 * width ** 2) * phase
+    vbox = pref * np.exp(-0.5 * g2b * width ** 2) * sf
+    idx = ((miller[:, 0] + 2 * R) * L + (miller[:, 1] + 2 * R)) * L + (miller[:, 2] + 2 * R)
+    # difference m_p - m_q  ->  flat box index idx_p - idx_q + offset of the zero vector
+    zero = ((2 * R) * L + 2 * R) * L + 2 * R
+    H = vbox[(idx[:, None] - idx[None, :]) + zero]
+    G = miller.astype(np.float64) @ B
     H[np.diag_indices_from(H)] += 0.5 * (G ** 2).sum(-1)
     return H
 
 
+def _real_hamiltonian(miller: np.ndarray, H: np.ndarray):
+    """H in the basis {1, cos(G.r), sin(G.r)} (one cos and one sin per +-G pair), built by
+    index gathers; returns (Hr real, zero index, primary indices, their negatives)."""
+    key = {tuple(m): k for k, m in enumerate(miller.tolist())}
+    zero = key[(0, 0, 0)]
+    prim, neg = [], []
+    for k, m in enumerate(miller.tolist()):
+        first = m[0] if m[0] != 0 else (m[1] if m[1] != 0 else m[2])
+        if first > 0:
+            prim.append(k)
+            neg.append(key[(-m[0], -m[1], -m[2])])
+    P, Q = np.array(prim), np.array(neg)
+    kk, km = H[np.ix_(P, P)], H[np.ix_(P, Q)]
+    mk, mm = H[np.ix_(Q, P)], H[np.ix_(Q, Q)]
+    cc = 0.5 * (kk + km + mk + mm)
+    cs = -0.5j * (kk - km + mk - mm)
+    sc = 0.5j * (kk + km - mk - mm)
+    ss = 0.5 * (kk - km - mk + mm)
+    r2 = 1.0 / math.sqrt(2.0)
+    h0c = r2 * (H[zero, P] + H[zero, Q])
+    h0s = -1j * r2 * (H[zero, P] - H[zero, Q])
+    n = len(P)
+    Hr = np.empty((2 * n + 1, 2 * n + 1), dtype=np.complex128)
+    Hr[0, 0] = H[zero, zero]
+    Hr[0, 1:n + 1], Hr[0, n + 1:] = h0c, h0s
+    Hr[1:n + 1, 0], Hr[n + 1:, 0] = np.conj(h0c), np.conj(h0s)
+    Hr[1:n + 1, 1:n + 1], Hr[1:n + 1, n + 1:] = cc, cs
+    Hr[n + 1:, 1:n + 1], Hr[n + 1:, n + 1:] = sc, ss
+    return Hr, zero, P, Q
+
+
 def _finish(spec, lattice, grid, miller, positions, H, real_orbitals, random_phases, seed):
     if real_orbitals:
-        U = _real_basis(miller)
-        Hr = (U.conj().T @ H @ U)
+        Hr, zero, P, Q = _real_hamiltonian(miller, H)
         if np.abs(Hr.imag).max() > 1e-10 * max(1.0, np.abs(Hr.real).max()):
             raise RuntimeError("Hamiltonian is not real in the cos/sin basis")
         w, v = np.linalg.eigh(Hr.real)
-        coeff = (U @ v).T.copy()
+        n = len(P)
+        coeff = np.zeros((H.shape[0], H.shape[0]), dtype=np.complex128)
+        r2 = 1.0 / math.sqrt(2.0)
+        vt = v.T
+        coeff[:, zero] = vt[:, 0]
+        coeff[:, P] = r2 * (vt[:, 1:n + 1] - 1j * vt[:, n + 1:])
+        coeff[:, Q] = r2 * (vt[:, 1:n + 1] + 1j * vt[:, n + 1:])
     else:
         w, v = np.linalg.eigh(H)
         coeff = v.T.copy()

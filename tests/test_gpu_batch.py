@@ -1,0 +1,61 @@
+"""Batching form: several systems of uneven grids and orbital counts evaluated by one
+CUDA-graph launch must give, system by system, the energies of ltmp2_energy (same
+kernels, same tuning) and, in FP64, the oracle's within 1e-8 Ha."""
+import numpy as np
+import pytest
+
+import paper_1611_06797_gb300 as L
+from oracle import OracleSystem, denominator_range, laplace_denominator, mp2_energy, sinc_laplace_quadrature
+from tests.conftest import solid
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ["tiny", "tiny2", "cfg1"]
+
+
+def _setup(precision):
+    solids = [solid(n) for n in NAMES]
+    ctxs = [L.setup_from_solid(s, precision=precision, real=True) for s in solids]
+    quads = [sinc_laplace_quadrature(s.spec.n_tau, *denominator_range(OracleSystem.from_solid(s))) for s in solids]
+    return solids, ctxs, quads
+
+
+@pytest.mark.parametrize("precision", [L.FP64, L.FP32])
+def test_batch_graph_matches_individual_calls(precision):
+    solids, ctxs, quads = _setup(precision)
+    for c in ctxs:
+        slab, var = L.ltmp2_autotune(c)
+        assert 1 <= slab <= L.ltmp2_num_primary_gprime(c)
+        assert (var == -1) == (precision == L.FP64)
+    single = [L.ltmp2_energy(c, t, w)[:2] for c, (t, w) in zip(ctxs, quads)]
+    b = L.ltmp2_batch_create(ctxs, [q[0] for q in quads], [q[1] for q in quads])
+    assert b.kernel_nodes() > 0
+    for _ in range(2):          # the captured graph is replayed
+        ed, ex = b.run()
+        for k, (d, x) in enumerate(single):
+            assert abs(ed[k] - d) <= 1e-12 * max(1.0, abs(d)) and abs(ex[k] - x) <= 1e-12 * max(1.0, abs(x))
+    b.destroy()
+
+
+def test_energy_batch_matches_oracle_fp64():
+    solids, ctxs, quads = _setup(L.FP64)
+    ed, ex = L.ltmp2_energy_batch(ctxs, [q[0] for q in quads], [q[1] for q in quads])
+    for k, s in enumerate(solids):
+        ref = mp2_energy(OracleSystem.from_solid(s), laplace_denominator(*quads[k]))
+        assert abs(ed[k] - ref["E_d"]) < 1e-8 and abs(ex[k] - ref["E_x"]) < 1e-8
+
+
+def test_autotune_is_cached_per_bucket():
+    s = solid("cfg1")
+    a = L.setup_from_solid(s, precision=L.FP32, real=True)
+    b = L.setup_from_solid(s, precision=L.FP32, real=True)
+    assert L.ltmp2_autotune(a) == L.ltmp2_autotune(b)
+
+
+def test_batch_rejects_duplicate_contexts():
+    s = solid("tiny")
+    c = L.setup_from_solid(s)
+    t, w = sinc_laplace_quadrature(3, 2 * s.gap, 2 * s.width)
+    with pytest.raises(L.Ltmp2Error) as e:
+        L.ltmp2_batch_create([c, c], [t, t], [w, w])
+    assert e.value.name == "INVALID_ARG"
