@@ -167,11 +167,17 @@ int ltmp2_set_slab_size(ltmp2_ctx *ctx, int n);
 
 /* Autotuner: times one slab of the path for each candidate (slab sizes down from the
  * setup capacity; in LTMP2_FP32 also the two tensor-core GEMM layouts) and keeps the
- * fastest per primary G'.  The choice is cached per (grid, n_pw, n_occ, |A|, precision,
+ * fastest per primary G', then the plane FFT kernel and its block shape.  The choice is cached per (grid, n_pw, n_occ, |A|, precision,
  * real-orbital flag) for the process and applied to ctx.  slab, gemm_variant: NULL or
  * receive the choice (gemm_variant = -1 in LTMP2_FP64).  Errors: INVALID_ARG, CUDA,
  * TIMEOUT.                                                                          */
 int ltmp2_autotune(ltmp2_ctx *ctx, int *slab, int *gemm_variant);
+
+/* Settings in effect for ctx: values[0] slab size, [1] tensor-core GEMM layout (-1 in
+ * FP64 or with LTMP2_FLAG_SIMT_GEMM), [2] plane FFT kernel (0 full-plane passes,
+ * 1 compacted passes), [3] occupied planes per plane-kernel block (0 = default).  The
+ * autotuner also chooses [2] and [3], timing the plane kernel alone.                */
+int ltmp2_get_tuning(const ltmp2_ctx *ctx, int *values);
 
 typedef struct ltmp2_batch ltmp2_batch; /* opaque; a captured, instantiated graph */
 

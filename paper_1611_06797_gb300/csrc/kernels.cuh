@@ -264,6 +264,82 @@ __global__ void k_planes(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> *
   }
 }
 
+// Same result as k_planes, fewer shared-memory passes.  Per block of ib occupied i:
+//  product: conj(phi_i) w_j^{G'} for the block's planes, loaded coalesced into shared
+//           memory (pitch P = N + 1);
+//  x pass : thread (i, y) transforms its row in registers and writes back, in place,
+//           only the m1 of the aux range (columns 0 .. nxa-1 of the row);
+//  y pass : thread (i, m1) transforms its column and writes only the aux-disk entries,
+//           compactly in disk order;
+//  copy   : coalesced copy of the compact plane to tbuf[(col, i)][z][d_aux].
+template <typename T, int N>
+__global__ void k_planes2(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> *__restrict__ tbuf) {
+  constexpr int P = N + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T> *xp = reinterpret_cast<cpx<T> *>(smem_raw);
+  const int nxa = p.mxhi_aux - p.mxlo_aux + 1;
+  const int nd = p.n_daux;
+  cpx<T> *wk = xp + N * P;                    // [ib][N][P]
+  cpx<T> *ob = wk + (size_t)ib * N * P;       // [ib][nd]
+  int *xs = reinterpret_cast<int *>(ob + (size_t)ib * nd);   // per m1: first disk column, m2 lo, m2 hi
+  const int z = blockIdx.x, col = blockIdx.y;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int no = p.n_occ;
+  for (int t = tid; t < nxa; t += nth) { xs[3 * t] = 0; xs[3 * t + 1] = 1; xs[3 * t + 2] = 0; }
+  __syncthreads();
+  for (int d = tid; d < nd; d += nth) {
+    const int4 c = p.daux[d];
+    const int xa = c.x - p.mxlo_aux;
+    if (d == 0 || p.daux[d - 1].x != c.x) { xs[3 * xa] = d; xs[3 * xa + 1] = c.y; }
+    if (d == nd - 1 || p.daux[d + 1].x != c.x) xs[3 * xa + 2] = c.y;
+  }
+  plane_inverse<T, N>(p, z1 + ((size_t)col * N + z) * p.n_dorb, xp);   // ends with a barrier
+  const cpx<T> *u = (const cpx<T> *)p.u;
+  for (int i0 = 0; i0 < no; i0 += ib) {
+    const int nb = min(ib, no - i0);
+    for (int e = tid; e < nb * N * N; e += nth) {
+      const int il = e / (N * N), r = e % (N * N), y = r / N, x = r % N;
+      const cpx<T> uu = u[((size_t)(i0 + il) * N + z) * N * N + r];
+      wk[(il * N + y) * P + x] = cmul(cconj(uu), xp[y * P + x]);
+    }
+    __syncthreads();
+    for (int t = tid; t < nb * N; t += nth) {
+      cpx<T> *row = wk + (size_t)t * P;    // (il * N + y) * P
+      cpx<T> a[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) a[k] = row[k];
+      LineFFT<T, N, -1>::run(a);
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int m = freq_of<N>(k);
+        if (m >= p.mxlo_aux && m <= p.mxhi_aux) row[m - p.mxlo_aux] = a[k];
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < nb * nxa; t += nth) {
+      const int il = t / nxa, xa = t % nxa;
+      const cpx<T> *src = wk + (size_t)il * N * P + xa;
+      cpx<T> b[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) b[k] = src[k * P];
+      LineFFT<T, N, -1>::run(b);
+      const int d0 = xs[3 * xa], lo = xs[3 * xa + 1], hi = xs[3 * xa + 2];
+      cpx<T> *o = ob + (size_t)il * nd + d0 - lo;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int m = freq_of<N>(k);
+        if (m >= lo && m <= hi) o[m] = b[k];
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < nb * nd; e += nth) {
+      const int il = e / nd, d = e % nd;
+      const size_t item = (size_t)col * no + i0 + il;
+      tbuf[(item * N + z) * nd + d] = ob[(size_t)il * nd + d];
+    }
+  }
+}
+
 // setup: real-space occupied orbitals u[j][z][y][x] from z1 (cols = occupied orbitals)
 template <typename T, int N>
 __global__ void k_planes_store(Plan p, const cpx<T> *__restrict__ z1, cpx<T> *__restrict__ out) {

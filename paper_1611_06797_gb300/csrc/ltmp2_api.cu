@@ -363,11 +363,16 @@ struct TuneKey {
   }
 };
 std::mutex g_tune_mutex;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;  // -> (slab, gemm variant or -1)
+struct TuneVal {
+  int slab, variant, plane_kernel, plane_ib;
+};
+std::map<TuneKey, TuneVal> g_tune_cache;
 
-int apply_tuning(ltmp2_ctx *c, int slab, int variant) {
+int apply_tuning(ltmp2_ctx *c, int slab, int variant, int plane_kernel = 0, int plane_ib = 0) {
   if (slab < 1 || slab > c->slab_capacity) return LTMP2_ERR_INVALID_ARG;
   c->p.max_prim = slab;
+  c->p.plane_kernel = plane_kernel;
+  c->p.plane_ib = plane_ib;
   if (c->p.tc && variant >= 0 && variant != c->tc.variant) {
     tc_release(c->tc);
     cudaError_t e = tc_init(c->tc, c->tc_mem, c->tc.rows_cap, c->p.n_pw, variant);
@@ -383,7 +388,8 @@ template <typename T> int tune_ctx(ltmp2_ctx *c, int *slab_out, int *var_out) {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      int rc = apply_tuning(c, std::min(it->second.first, c->slab_capacity), it->second.second);
+      const TuneVal &v = it->second;
+      int rc = apply_tuning(c, std::min(v.slab, c->slab_capacity), v.variant, v.plane_kernel, v.plane_ib);
       *slab_out = p.max_prim;
       *var_out = p.tc ? c->tc.variant : -1;
       return rc;
@@ -417,14 +423,37 @@ template <typename T> int tune_ctx(ltmp2_ctx *c, int *slab_out, int *var_out) {
     }
     if (rc) break;
   }
+  // plane kernel and its block size, timed alone on the columns of one warm slab
+  int best_pk = 0, best_ib = 0;
+  if (!rc) rc = apply_tuning(c, best_slab, best_var);
+  if (!rc && Path<T>::slab(p, 0, best_slab, 0.0, c->stream, nullptr) != cudaSuccess) rc = LTMP2_ERR_CUDA;
+  if (!rc) {
+    const int ncols = best_slab * p.slots_per_prim() * p.n_occ;
+    double best_plane = 1e300;
+    for (int pk = 0; pk < 2 && !rc; ++pk)
+      for (int ib : {2, 4, 8, 16}) {
+        if (ib > p.n_occ) continue;
+        if (Path<T>::plane_pass(p, ncols, pk, ib, c->stream) != cudaSuccess) {  // infeasible shape
+          cudaGetLastError();
+          continue;
+        }
+        cudaEventRecord(a, c->stream);
+        for (int rep = 0; rep < 2; ++rep) Path<T>::plane_pass(p, ncols, pk, ib, c->stream);
+        cudaEventRecord(b, c->stream);
+        if (cudaEventSynchronize(b) != cudaSuccess) { rc = LTMP2_ERR_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best_plane) { best_plane = ms; best_pk = pk; best_ib = ib; }
+      }
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (!rc) rc = check_tc_flag(c);
-  if (!rc) rc = apply_tuning(c, best_slab, best_var);
+  if (!rc) rc = apply_tuning(c, best_slab, best_var, best_pk, best_ib);
   if (rc) return rc;
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[key] = {best_slab, best_var};
+    g_tune_cache[key] = {best_slab, best_var, best_pk, best_ib};
   }
   *slab_out = best_slab;
   *var_out = p.tc ? best_var : -1;
@@ -776,6 +805,15 @@ int ltmp2_autotune(ltmp2_ctx *ctx, int *slab, int *gemm_variant) {
   if (rc) return rc;
   if (slab) *slab = sl;
   if (gemm_variant) *gemm_variant = var;
+  return LTMP2_OK;
+}
+
+int ltmp2_get_tuning(const ltmp2_ctx *ctx, int *values) {
+  if (!ctx || !values) return LTMP2_ERR_INVALID_ARG;
+  values[0] = ctx->p.max_prim;
+  values[1] = ctx->p.tc ? ctx->tc.variant : -1;
+  values[2] = ctx->p.plane_kernel;
+  values[3] = ctx->p.plane_ib;
   return LTMP2_OK;
 }
 

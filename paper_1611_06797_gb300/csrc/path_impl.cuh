@@ -9,14 +9,58 @@ namespace ltmp2 {
 
 #define LTMP2_FOR_EACH_N(X) X(8) X(10) X(12) X(16) X(18) X(20) X(24) X(25) X(27) X(30) X(32) X(36) X(40)
 
-template <typename T> static int plane_ib(int n, int n_occ) {
-  // occupied planes per plane-kernel block: about 96 KB of shared memory
+// Plane kernels: 0 = k_planes (full-plane passes), 1 = k_planes2 (compacted passes).
+// ib = occupied planes per block; 0 picks the default of each kernel.
+template <typename T> static int plane_ib_default(const Plan &p, int kernel) {
+  const int n = p.n;
   const size_t plane = (size_t)n * (n + 1) * sizeof(cpx<T>);
-  int ib = (int)((96 * 1024) / plane) - 1;
+  int ib;
+  if (kernel == 0) {
+    ib = (int)((96 * 1024) / plane) - 1;   // about 96 KB of shared memory
+    if (ib > 8) ib = 8;
+  } else {
+    const size_t per = plane + (size_t)p.n_daux * sizeof(cpx<T>);
+    ib = (int)((100 * 1024 - plane - 3 * sizeof(int) * (n + 1) - 64) / per);
+    if (ib > 384 / n) ib = 384 / n;
+  }
+  if (ib > p.n_occ) ib = p.n_occ;
   if (ib < 1) ib = 1;
-  if (ib > 8) ib = 8;
-  if (ib > n_occ) ib = n_occ;
   return ib;
+}
+
+template <typename T> static size_t plane_smem(const Plan &p, int kernel, int ib) {
+  const int n = p.n;
+  const size_t plane = (size_t)n * (n + 1) * sizeof(cpx<T>);
+  if (kernel == 0) return plane * (1 + ib);
+  return plane * (1 + ib) + (size_t)ib * p.n_daux * sizeof(cpx<T>) + 3 * sizeof(int) * (p.mxhi_aux - p.mxlo_aux + 1);
+}
+
+// launch the plane kernel for the ncols columns of the current slab (z1 -> tbuf)
+template <typename T> static cudaError_t launch_planes(const Plan &p, int ncols, int kernel, int ib, cudaStream_t st) {
+  if (ib <= 0) ib = plane_ib_default<T>(p, kernel);
+  const size_t smem = plane_smem<T>(p, kernel, ib);
+  int threads = ib * p.n;
+  if (threads < 64) threads = 64;
+  if (threads > 1024 || smem > 200 * 1024) return cudaErrorInvalidValue;
+  switch (p.n) {
+#define LTMP2_CASE(NN)                                                                                     \
+  case NN:                                                                                                 \
+    if (kernel == 0)                                                                                       \
+      k_planes<T, NN><<<dim3(NN, ncols), threads, smem, st>>>(p, ib, (const cpx<T> *)p.z1, (cpx<T> *)p.tbuf);  \
+    else                                                                                                   \
+      k_planes2<T, NN><<<dim3(NN, ncols), threads, smem, st>>>(p, ib, (const cpx<T> *)p.z1, (cpx<T> *)p.tbuf); \
+    break;
+    LTMP2_FOR_EACH_N(LTMP2_CASE)
+#undef LTMP2_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Path<T>::plane_pass(const Plan &p, int ncols, int kernel, int ib, cudaStream_t st) {
+  return launch_planes<T>(p, ncols, kernel, ib, st);
 }
 
 struct ScopedStage {
@@ -39,6 +83,8 @@ template <typename T> cudaError_t Path<T>::init_device() {
   e = cudaFuncSetAttribute(k_planes<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
   if (e != cudaSuccess) return e;                                                                   \
   e = cudaFuncSetAttribute(k_zcol<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);   \
+  if (e != cudaSuccess) return e;                                                                   \
+  e = cudaFuncSetAttribute(k_planes2<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
   if (e != cudaSuccess) return e;
   LTMP2_FOR_EACH_N(LTMP2_SET_SMEM)
 #undef LTMP2_SET_SMEM
@@ -121,14 +167,10 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   }
-  const int ib = plane_ib<T>(n, no);
-  const size_t smem_plane = (size_t)n * (n + 1) * sizeof(cpx<T>) * (1 + ib);
   const size_t smem_col = (size_t)p.n_aux * sizeof(cpx<T>);
   const int npairs = p.real_orb ? np * (no * (no + 1) / 2) : np * no * no;
   int col_threads = ((p.n_daux + 31) / 32) * 32;
   if (col_threads > 512) col_threads = 512;
-  int plane_threads = ib * n;
-  if (plane_threads < 64) plane_threads = 64;
   switch (n) {
 #define LTMP2_CASE(NN)                                                                                  \
   case NN: {                                                                                            \
@@ -141,9 +183,7 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
     }                                                                                                   \
     {                                                                                                   \
       ScopedStage s(tm, kStagePlane);                                                                   \
-      k_planes<T, NN><<<dim3(NN, ncols), plane_threads, smem_plane, st>>>(p, ib, (const cpx<T> *)p.z1,  \
-                                                                          (cpx<T> *)p.tbuf);            \
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;                                            \
+      if ((e = launch_planes<T>(p, ncols, p.plane_kernel, p.plane_ib, st)) != cudaSuccess) return e;    \
     }                                                                                                   \
     {                                                                                                   \
       ScopedStage s(tm, kStageColumn);                                                                  \

@@ -67,6 +67,8 @@ struct Plan {
   double *esum = nullptr;    // [4]: E_d, E_x, imag parts
   int max_prim = 0;          // primary G' per slab (capacity)
   TcResources *tc = nullptr; // precision form: tcgen05 GEMM resources (host pointer), or null
+  int plane_kernel = 0;      // 0: k_planes, 1: k_planes2 (set by the autotuner)
+  int plane_ib = 0;          // occupied planes per plane-kernel block, 0 = kernel default
   int slots_per_prim() const { return real_orb ? 1 : 2; }
 };
 
@@ -96,6 +98,8 @@ template <typename T> struct Path {
   // one slab of primary G' [gp0, gp0 + np): everything up to the pair sums, then accumulate
   static cudaError_t slab(const Plan &p, int gp0, int np, double coef, cudaStream_t st,
                           StageTimer *tm);
+  // the plane kernel alone (for the autotuner): kernel 0/1, ib (0 = default)
+  static cudaError_t plane_pass(const Plan &p, int ncols, int kernel, int ib, cudaStream_t st);
   // zero accumulators / final reduction
   static cudaError_t zero_acc(const Plan &p, cudaStream_t st);
   static cudaError_t finish(const Plan &p, cudaStream_t st, StageTimer *tm);

@@ -288,6 +288,7 @@ def _batch_sig(lib):
     vp = ctypes.c_void_p
     for name, res, args in [
             ("ltmp2_autotune", ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int)]),
+            ("ltmp2_get_tuning", ctypes.c_int, [vp, P(ctypes.c_int)]),
             ("ltmp2_batch_create", ctypes.c_int, [P(vp), ctypes.c_int, P(ctypes.c_int), P(dp), P(dp), P(vp)]),
             ("ltmp2_batch_run", ctypes.c_int, [vp, dp, dp]),
             ("ltmp2_batch_kernel_nodes", ctypes.c_int, [vp, P(ctypes.c_longlong)]),
@@ -305,6 +306,13 @@ def ltmp2_autotune(ctx: Context):
     sl, var = ctypes.c_int(), ctypes.c_int()
     _check(lib.ltmp2_autotune(ctx.handle, ctypes.byref(sl), ctypes.byref(var)), "ltmp2_autotune")
     return sl.value, var.value
+
+
+def ltmp2_get_tuning(ctx: Context) -> dict:
+    lib = _batch_sig(load_library())
+    v = (ctypes.c_int * 4)()
+    _check(lib.ltmp2_get_tuning(ctx.handle, v), "ltmp2_get_tuning")
+    return {"slab": v[0], "gemm_variant": v[1], "plane_kernel": v[2], "plane_ib": v[3]}
 
 
 def _batch_args(ctxs, taus, ws):
