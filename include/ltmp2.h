@@ -203,6 +203,39 @@ void ltmp2_batch_destroy(ltmp2_batch *b);
 int ltmp2_energy_batch(ltmp2_ctx *const *ctxs, int n, const int *n_tau, const double *const *tau,
                        const double *const *w, double *e_direct, double *e_exchange);
 
+/* ---------------------------------------------------------------- learned form
+ * Weak occupied pairs are screened: their exchange co-densities (the N_o^2 part of
+ * step (iv.b), Sec. III C) are not formed and their exchange energy is estimated by a
+ * small pair-energy model instead; the direct term (step (iv.a)) stays exact for all
+ * pairs.  The paper has no counterpart.                                              */
+
+/* keep: NULL (every pair contracted) or [n_occ][n_occ] bytes, symmetric, keep[i][i] != 0;
+ * keep[i][j] == 0 leaves pair (i, j) out of the exchange contraction in later
+ * ltmp2_energy* calls (their e^x_ij, and so E_exchange, omit it).  Errors: INVALID_ARG,
+ * OOM, CUDA.                                                                           */
+int ltmp2_set_pair_mask(ltmp2_ctx *ctx, const unsigned char *keep);
+
+/* Cheap descriptors of every unordered occupied pair i <= j (row order i, then j),
+ * LTMP2_NUM_DESC doubles each: e_i - mu, e_j - mu (Ha), log10 of the density overlap
+ * (1/N) sum_r |u_i|^2 |u_j|^2, centroid distance (bohr, periodic centroids, minimum
+ * image), spreads of i and j (bohr), i == j, distance / (spread_i + spread_j).
+ * desc: host array of n_occ (n_occ + 1) / 2 * LTMP2_NUM_DESC doubles.             */
+#define LTMP2_NUM_DESC 8
+int ltmp2_pair_descriptors(ltmp2_ctx *ctx, double *desc);
+
+/* Pair-energy surrogate: a perceptron n_in -> width -> width -> 1 (tanh, FP32;
+ * n_in <= 16, width <= 64), trained with Adam on standardised inputs and targets by
+ * hand-written kernels on the current device.                                         */
+typedef struct ltmp2_mlp ltmp2_mlp;
+int ltmp2_mlp_create(int n_in, int width, unsigned long long seed, ltmp2_mlp **out);
+/* X [n][n_in], y [n] host arrays; full-batch Adam for `epochs` steps at rate lr;
+ * final_loss (may be NULL): mean squared error of the standardised targets.         */
+int ltmp2_mlp_train(ltmp2_mlp *net, const float *X, const float *y, int n, int epochs, float lr,
+                    float *final_loss);
+/* y[n] = model(X[n][n_in]) in the units of the training targets.                    */
+int ltmp2_mlp_predict(const ltmp2_mlp *net, const float *X, int n, float *y);
+void ltmp2_mlp_destroy(ltmp2_mlp *net);
+
 /* Number of primary G' vectors (half of |A|); returns < 0 on a NULL ctx.        */
 int ltmp2_num_primary_gprime(const ltmp2_ctx *ctx);
 

@@ -225,11 +225,16 @@ __global__ void k_planes(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> *
   plane_inverse<T, N>(p, z1 + ((size_t)col * N + z) * p.n_dorb, xp);
   const cpx<T> *u = (const cpx<T> *)p.u;
   const int nxa = p.mxhi_aux - p.mxlo_aux + 1;
-  for (int i0 = 0; i0 < no; i0 += ib) {
-    const int nb = min(ib, no - i0);
+  // occupied i of this column: all, or the kept list when exchange pairs are screened
+  const int jcol = col % no;
+  const int ni = p.keep_count ? p.keep_count[jcol] : no;
+  const int *ilist = p.keep_count ? p.keep_list + (size_t)jcol * no : nullptr;
+  for (int i0 = 0; i0 < ni; i0 += ib) {
+    const int nb = min(ib, ni - i0);
     for (int e = tid; e < nb * N * N; e += nth) {
       const int il = e / (N * N), r = e % (N * N), y = r / N, x = r % N;
-      const cpx<T> uu = u[((size_t)(i0 + il) * N + z) * N * N + r];
+      const int iocc = ilist ? ilist[i0 + il] : i0 + il;
+      const cpx<T> uu = u[((size_t)iocc * N + z) * N * N + r];
       wk[(il * N + y) * P + x] = cmul(cconj(uu), xp[y * P + x]);
     }
     __syncthreads();
@@ -257,7 +262,7 @@ __global__ void k_planes(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> *
     for (int e = tid; e < nb * p.n_daux; e += nth) {
       const int il = e / p.n_daux, d = e % p.n_daux;
       const int4 c = p.daux[d];
-      const size_t item = (size_t)col * no + i0 + il;
+      const size_t item = (size_t)col * no + (ilist ? ilist[i0 + il] : i0 + il);
       tbuf[(item * N + z) * p.n_daux + d] = wk[(il * N + wrapn(c.y, N)) * P + wrapn(c.x, N)];
     }
     __syncthreads();
@@ -295,11 +300,16 @@ __global__ void k_planes2(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> 
   }
   plane_inverse<T, N>(p, z1 + ((size_t)col * N + z) * p.n_dorb, xp);   // ends with a barrier
   const cpx<T> *u = (const cpx<T> *)p.u;
-  for (int i0 = 0; i0 < no; i0 += ib) {
-    const int nb = min(ib, no - i0);
+  // occupied i of this column: all, or the kept list when exchange pairs are screened
+  const int jcol = col % no;
+  const int ni = p.keep_count ? p.keep_count[jcol] : no;
+  const int *ilist = p.keep_count ? p.keep_list + (size_t)jcol * no : nullptr;
+  for (int i0 = 0; i0 < ni; i0 += ib) {
+    const int nb = min(ib, ni - i0);
     for (int e = tid; e < nb * N * N; e += nth) {
       const int il = e / (N * N), r = e % (N * N), y = r / N, x = r % N;
-      const cpx<T> uu = u[((size_t)(i0 + il) * N + z) * N * N + r];
+      const int iocc = ilist ? ilist[i0 + il] : i0 + il;
+      const cpx<T> uu = u[((size_t)iocc * N + z) * N * N + r];
       wk[(il * N + y) * P + x] = cmul(cconj(uu), xp[y * P + x]);
     }
     __syncthreads();
@@ -334,7 +344,7 @@ __global__ void k_planes2(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> 
     __syncthreads();
     for (int e = tid; e < nb * nd; e += nth) {
       const int il = e / nd, d = e % nd;
-      const size_t item = (size_t)col * no + i0 + il;
+      const size_t item = (size_t)col * no + (ilist ? ilist[i0 + il] : i0 + il);
       tbuf[(item * N + z) * nd + d] = ob[(size_t)il * nd + d];
     }
   }
@@ -404,6 +414,13 @@ __global__ void k_zcol(Plan p, int gp0, int np, const cpx<T> *__restrict__ tbuf,
     self = (i == j);
   }
   const bool diag = (i == j);
+  if (p.pair_keep && !diag && !p.pair_keep[i * no + j]) {   // screened: exchange estimated elsewhere
+    if (threadIdx.x == 0) {
+      sx[((size_t)gpl * no + i) * no + j] = make_double2(0.0, 0.0);
+      if (p.real_orb) sx[((size_t)gpl * no + j) * no + i] = make_double2(0.0, 0.0);
+    }
+    return;
+  }
   const size_t itemA = ((size_t)slotA * no + j) * no + i;   // (i, j, slotA)
   const size_t itemB = ((size_t)slotB * no + i) * no + j;   // (j, i, slotB)
   const T *v = vtab<T>(p);
@@ -485,6 +502,61 @@ __global__ void k_direct(Plan p, int np, const cpx<T> *__restrict__ mdiag, doubl
     }
     ax += (double)cx; ay += (double)cy;
     yd[((size_t)gpl * no + i) * no + j] = make_double2(ax, ay);
+  }
+}
+
+// ---------------------------------------------------------------- pair descriptors
+// Per occupied orbital: z_k = (1/N) sum_t |u(t)|^2 exp(2 pi i t_k / n), k = x, y, z
+// (periodic centroid from arg z_k, spread from |z_k|).  out[i][6] = (Re, Im) x 3.
+template <typename T> __global__ void k_orb_moments(Plan p, double *__restrict__ out) {
+  const int i = blockIdx.x, n = p.n;
+  const size_t n3 = (size_t)n * n * n;
+  const cpx<T> *u = (const cpx<T> *)p.u + (size_t)i * n3;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (size_t t = threadIdx.x; t < n3; t += blockDim.x) {
+    const int x = (int)(t % n), y = (int)((t / n) % n), z = (int)(t / ((size_t)n * n));
+    const double w = (double)u[t].x * u[t].x + (double)u[t].y * u[t].y;
+    double sx, cx, sy, cy, sz, cz;
+    sincospi(2.0 * x / n, &sx, &cx);
+    sincospi(2.0 * y / n, &sy, &cy);
+    sincospi(2.0 * z / n, &sz, &cz);
+    acc[0] += w * cx; acc[1] += w * sx; acc[2] += w * cy; acc[3] += w * sy; acc[4] += w * cz; acc[5] += w * sz;
+  }
+  __shared__ double red[6][256];
+  for (int q = 0; q < 6; ++q) red[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int q = 0; q < 6; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 6; ++q) out[(size_t)i * 6 + q] = red[q][0] / (double)n3;
+}
+
+// Per ordered pair (block (i, j), j >= i): S_ij = (1/N) sum_t |u_i(t)|^2 |u_j(t)|^2, the
+// overlap of the two orbital densities; S[i][j] = S[j][i].
+template <typename T> __global__ void k_pair_overlap(Plan p, double *__restrict__ S) {
+  const int i = blockIdx.y, j = blockIdx.x;
+  if (j < i) return;
+  const size_t n3 = (size_t)p.n * p.n * p.n;
+  const cpx<T> *ui = (const cpx<T> *)p.u + (size_t)i * n3, *uj = (const cpx<T> *)p.u + (size_t)j * n3;
+  double acc = 0;
+  for (size_t t = threadIdx.x; t < n3; t += blockDim.x) {
+    const double a = (double)ui[t].x * ui[t].x + (double)ui[t].y * ui[t].y;
+    const double b = (double)uj[t].x * uj[t].x + (double)uj[t].y * uj[t].y;
+    acc += a * b;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    S[(size_t)i * p.n_occ + j] = red[0] / (double)n3;
+    S[(size_t)j * p.n_occ + i] = red[0] / (double)n3;
   }
 }
 

@@ -87,7 +87,10 @@ struct ltmp2_ctx {
   EventTimer timer;
   double last_imag[2] = {0, 0};
   int slab_capacity = 0;
+  double lattice[9] = {0};
   long long kernel_launches = 0;
+  unsigned char *d_keep = nullptr;   // screened-pair mask and kept lists (learned form)
+  int *d_keep_list = nullptr, *d_keep_count = nullptr;
   TcResources tc;
   void *tc_mem = nullptr;   // operand buffers of the tensor-core GEMM (owned via allocs)
   ~ltmp2_ctx() {
@@ -636,6 +639,7 @@ int ltmp2_setup(const ltmp2_system *sys, ltmp2_ctx **out) {
     return LTMP2_ERR_CUDA;
   }
   Plan &p = c->p;
+  std::memcpy(c->lattice, sys->lattice, sizeof(c->lattice));
   p.n = n;
   p.n_occ = no;
   p.n_orb = norb;
@@ -805,6 +809,107 @@ int ltmp2_autotune(ltmp2_ctx *ctx, int *slab, int *gemm_variant) {
   if (rc) return rc;
   if (slab) *slab = sl;
   if (gemm_variant) *gemm_variant = var;
+  return LTMP2_OK;
+}
+
+int ltmp2_set_pair_mask(ltmp2_ctx *ctx, const unsigned char *keep) {
+  if (!ctx) return LTMP2_ERR_INVALID_ARG;
+  Plan &p = ctx->p;
+  if (!keep) {
+    p.pair_keep = nullptr;
+    p.keep_list = nullptr;
+    p.keep_count = nullptr;
+    return LTMP2_OK;
+  }
+  const int no = p.n_occ;
+  for (int i = 0; i < no; ++i) {
+    if (!keep[i * no + i]) return LTMP2_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if ((keep[i * no + j] != 0) != (keep[j * no + i] != 0)) return LTMP2_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(ctx->device);
+  int rc = LTMP2_OK;
+  if (!ctx->d_keep) {
+    if ((rc = dalloc(ctx, &ctx->d_keep, (size_t)no * no))) return rc;
+    if ((rc = dalloc(ctx, &ctx->d_keep_list, (size_t)no * no))) return rc;
+    if ((rc = dalloc(ctx, &ctx->d_keep_count, (size_t)no))) return rc;
+  }
+  std::vector<unsigned char> k01((size_t)no * no);
+  std::vector<int> list((size_t)no * no, 0), count(no, 0);
+  for (int j = 0; j < no; ++j)
+    for (int i = 0; i < no; ++i) {
+      k01[(size_t)i * no + j] = keep[(size_t)i * no + j] ? 1 : 0;
+      if (keep[(size_t)i * no + j]) list[(size_t)j * no + count[j]++] = i;
+    }
+  if (cudaMemcpy(ctx->d_keep, k01.data(), k01.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ctx->d_keep_list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ctx->d_keep_count, count.data(), count.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    return LTMP2_ERR_CUDA;
+  p.pair_keep = ctx->d_keep;
+  p.keep_list = ctx->d_keep_list;
+  p.keep_count = ctx->d_keep_count;
+  return LTMP2_OK;
+}
+
+int ltmp2_pair_descriptors(ltmp2_ctx *ctx, double *desc) {
+  if (!ctx || !desc) return LTMP2_ERR_INVALID_ARG;
+  Plan &p = ctx->p;
+  const int no = p.n_occ;
+  DeviceGuard g(ctx->device);
+  double *dmom = nullptr, *dov = nullptr;
+  if (cudaMalloc(&dmom, sizeof(double) * 6 * no) != cudaSuccess ||
+      cudaMalloc(&dov, sizeof(double) * (size_t)no * no) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(dmom);
+    return LTMP2_ERR_OOM;
+  }
+  cudaError_t e = p.precision == LTMP2_FP64 ? Path<double>::descriptors(p, dmom, dov, ctx->stream)
+                                            : Path<float>::descriptors(p, dmom, dov, ctx->stream);
+  std::vector<double> mom(6 * (size_t)no), ov((size_t)no * no), eps(p.n_orb);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(mom.data(), dmom, sizeof(double) * mom.size(), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(ov.data(), dov, sizeof(double) * ov.size(), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(eps.data(), p.eps, sizeof(double) * eps.size(), cudaMemcpyDeviceToHost);
+  cudaFree(dmom);
+  cudaFree(dov);
+  if (e != cudaSuccess) return cuda_status(e);
+  // periodic centroid (fractional) and spread (bohr) of each occupied density
+  const double tp = 6.283185307179586476925286766559;
+  std::vector<double> frac(3 * (size_t)no), spread(no);
+  for (int i = 0; i < no; ++i) {
+    double s2 = 0;
+    for (int k = 0; k < 3; ++k) {
+      const double re = mom[6 * i + 2 * k], im = mom[6 * i + 2 * k + 1];
+      double f = std::atan2(im, re) / tp;
+      frac[3 * i + k] = f - std::floor(f);
+      const double mag = std::max(std::sqrt(re * re + im * im), 1e-12);
+      const double sig = std::sqrt(-2.0 * std::log(std::min(mag, 1.0))) / tp;   // fractional units
+      const double alen = std::sqrt(ctx->lattice[3 * k] * ctx->lattice[3 * k] + ctx->lattice[3 * k + 1] * ctx->lattice[3 * k + 1] +
+                                    ctx->lattice[3 * k + 2] * ctx->lattice[3 * k + 2]);
+      s2 += (sig * alen) * (sig * alen);
+    }
+    spread[i] = std::sqrt(s2);
+  }
+  size_t row = 0;
+  for (int i = 0; i < no; ++i)
+    for (int j = i; j < no; ++j, ++row) {
+      double r[3] = {0, 0, 0};
+      for (int k = 0; k < 3; ++k) {
+        double df = frac[3 * i + k] - frac[3 * j + k];
+        df -= std::floor(df + 0.5);
+        for (int c = 0; c < 3; ++c) r[c] += df * ctx->lattice[3 * k + c];
+      }
+      const double dist = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+      double *f = desc + row * LTMP2_NUM_DESC;
+      f[0] = eps[i] - p.mu;
+      f[1] = eps[j] - p.mu;
+      f[2] = std::log10(std::max(ov[(size_t)i * no + j], 1e-300));
+      f[3] = dist;
+      f[4] = spread[i];
+      f[5] = spread[j];
+      f[6] = (i == j) ? 1.0 : 0.0;
+      f[7] = dist / (spread[i] + spread[j] + 1e-3);
+    }
   return LTMP2_OK;
 }
 

@@ -211,6 +211,15 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
   return cudaSuccess;
 }
 
+template <typename T>
+cudaError_t Path<T>::descriptors(const Plan &p, double *moments, double *overlap, cudaStream_t st) {
+  k_orb_moments<T><<<p.n_occ, 256, 0, st>>>(p, moments);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_pair_overlap<T><<<dim3(p.n_occ, p.n_occ), 256, 0, st>>>(p, overlap);
+  return cudaGetLastError();
+}
+
 template <typename T> cudaError_t Path<T>::zero_acc(const Plan &p, cudaStream_t st) {
   k_zero_acc<<<(p.n_occ * p.n_occ + 255) / 256, 256, 0, st>>>(p);
   return cudaGetLastError();

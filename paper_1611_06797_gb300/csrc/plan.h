@@ -68,6 +68,10 @@ struct Plan {
   int max_prim = 0;          // primary G' per slab (capacity)
   TcResources *tc = nullptr; // precision form: tcgen05 GEMM resources (host pointer), or null
   int plane_kernel = 0;      // 0: k_planes, 1: k_planes2 (set by the autotuner)
+  // screened exchange pairs (learned form); all null = every pair contracted
+  const unsigned char *pair_keep = nullptr;  // [n_occ][n_occ] 1 = contract, symmetric, diagonal kept
+  const int *keep_list = nullptr;            // [n_occ][n_occ] kept i for each j (first keep_count[j])
+  const int *keep_count = nullptr;           // [n_occ]
   int plane_ib = 0;          // occupied planes per plane-kernel block, 0 = kernel default
   int slots_per_prim() const { return real_orb ? 1 : 2; }
 };
@@ -100,6 +104,8 @@ template <typename T> struct Path {
                           StageTimer *tm);
   // the plane kernel alone (for the autotuner): kernel 0/1, ib (0 = default)
   static cudaError_t plane_pass(const Plan &p, int ncols, int kernel, int ib, cudaStream_t st);
+  // per-orbital density moments [n_occ][6] and pair density overlaps [n_occ][n_occ] (device)
+  static cudaError_t descriptors(const Plan &p, double *moments, double *overlap, cudaStream_t st);
   // zero accumulators / final reduction
   static cudaError_t zero_acc(const Plan &p, cudaStream_t st);
   static cudaError_t finish(const Plan &p, cudaStream_t st, StageTimer *tm);

@@ -377,3 +377,85 @@ def ltmp2_energy_batch(ctxs, taus, ws):
     ed, ex = np.zeros(n), np.zeros(n)
     _check(lib.ltmp2_energy_batch(handles, n, nt, tps, wps, _dp(ed), _dp(ex)), "ltmp2_energy_batch")
     return ed, ex
+
+
+# ---------------------------------------------------------------- learned form
+NUM_DESC = 8
+
+
+def _learned_sig(lib):
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    fp = P(ctypes.c_float)
+    for name, res, args in [
+            ("ltmp2_set_pair_mask", ctypes.c_int, [vp, P(ctypes.c_ubyte)]),
+            ("ltmp2_pair_descriptors", ctypes.c_int, [vp, P(ctypes.c_double)]),
+            ("ltmp2_mlp_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, P(vp)]),
+            ("ltmp2_mlp_train", ctypes.c_int, [vp, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.c_float, fp]),
+            ("ltmp2_mlp_predict", ctypes.c_int, [vp, fp, ctypes.c_int, fp]),
+            ("ltmp2_mlp_destroy", None, [vp])]:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+def ltmp2_set_pair_mask(ctx: Context, keep) -> None:
+    """keep: None or [n_occ][n_occ] booleans (symmetric, diagonal True)."""
+    lib = _learned_sig(load_library())
+    if keep is None:
+        _check(lib.ltmp2_set_pair_mask(ctx.handle, None), "ltmp2_set_pair_mask")
+        return
+    k = np.ascontiguousarray(np.asarray(keep, dtype=np.uint8))
+    ctx._keep = k
+    _check(lib.ltmp2_set_pair_mask(ctx.handle, k.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))),
+           "ltmp2_set_pair_mask")
+
+
+def ltmp2_pair_descriptors(ctx: Context) -> np.ndarray:
+    """[n_pairs][NUM_DESC] for unordered pairs i <= j (row order i, then j)."""
+    lib = _learned_sig(load_library())
+    n = ctx.n_occ * (ctx.n_occ + 1) // 2
+    d = np.zeros((n, NUM_DESC))
+    _check(lib.ltmp2_pair_descriptors(ctx.handle, _dp(d)), "ltmp2_pair_descriptors")
+    return d
+
+
+class Mlp:
+    """Pair-energy perceptron trained and evaluated by the library's kernels."""
+
+    def __init__(self, n_in: int = NUM_DESC, width: int = 64, seed: int = 1):
+        lib = _learned_sig(load_library())
+        h = ctypes.c_void_p()
+        _check(lib.ltmp2_mlp_create(int(n_in), int(width), ctypes.c_ulonglong(seed), ctypes.byref(h)),
+               "ltmp2_mlp_create")
+        self.handle = h
+        self.n_in = n_in
+
+    def train(self, X, y, epochs: int = 2000, lr: float = 3e-3) -> float:
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float32))
+        y = np.ascontiguousarray(np.asarray(y, dtype=np.float32))
+        loss = ctypes.c_float()
+        fp = ctypes.POINTER(ctypes.c_float)
+        _check(load_library().ltmp2_mlp_train(self.handle, X.ctypes.data_as(fp), y.ctypes.data_as(fp), len(y),
+                                              int(epochs), ctypes.c_float(lr), ctypes.byref(loss)), "ltmp2_mlp_train")
+        return float(loss.value)
+
+    def predict(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float32))
+        y = np.zeros(X.shape[0], dtype=np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        _check(load_library().ltmp2_mlp_predict(self.handle, X.ctypes.data_as(fp), X.shape[0], y.ctypes.data_as(fp)),
+               "ltmp2_mlp_predict")
+        return y
+
+    def destroy(self):
+        if self.handle is not None and self.handle.value:
+            load_library().ltmp2_mlp_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
