@@ -216,8 +216,8 @@ int ltmp2_energy_batch(ltmp2_ctx *const *ctxs, int n, const int *n_tau, const do
 int ltmp2_set_pair_mask(ltmp2_ctx *ctx, const unsigned char *keep);
 
 /* Cheap descriptors of every unordered occupied pair i <= j (row order i, then j),
- * LTMP2_NUM_DESC doubles each: e_i - mu, e_j - mu (Ha), log10 of the density overlap
- * (1/N) sum_r |u_i|^2 |u_j|^2, centroid distance (bohr, periodic centroids, minimum
+ * LTMP2_NUM_DESC doubles each: e_i - mu, e_j - mu (Ha), log10 S_ij / sqrt(S_ii S_jj)
+ * with S_ij = (1/N) sum_r |u_i|^2 |u_j|^2, centroid distance (bohr, periodic centroids, minimum
  * image), spreads of i and j (bohr), i == j, distance / (spread_i + spread_j).
  * desc: host array of n_occ (n_occ + 1) / 2 * LTMP2_NUM_DESC doubles.             */
 #define LTMP2_NUM_DESC 8

@@ -903,7 +903,8 @@ int ltmp2_pair_descriptors(ltmp2_ctx *ctx, double *desc) {
       double *f = desc + row * LTMP2_NUM_DESC;
       f[0] = eps[i] - p.mu;
       f[1] = eps[j] - p.mu;
-      f[2] = std::log10(std::max(ov[(size_t)i * no + j], 1e-300));
+      f[2] = std::log10(std::max(ov[(size_t)i * no + j], 1e-300) /
+                        std::sqrt(std::max(ov[(size_t)i * no + i] * ov[(size_t)j * no + j], 1e-300)));
       f[3] = dist;
       f[4] = spread[i];
       f[5] = spread[j];

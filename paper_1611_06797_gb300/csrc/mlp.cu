@@ -3,8 +3,9 @@
 // produces, used to estimate the exchange energy of weak pairs that are then not
 // contracted.  The paper has no counterpart; it belongs to the batching / screening forms
 // of this library.  Training and inference are hand-written kernels: one thread per
-// sample, weights in shared memory, gradients gathered in shared memory per block and
-// summed over blocks in a fixed order, Adam updates on the device.
+// sample, weights in shared memory, per-block gradients as outer-product sums in shared
+// memory, block partials summed in a fixed order, Adam updates on the device.  Training
+// is deterministic: no atomics anywhere.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -69,54 +70,80 @@ __global__ void k_mlp_predict(Dims d, const float *__restrict__ params, const fl
   y[s] = ymean + ystd * forward(d, w, x, h1, h2);
 }
 
-// mean-squared-error gradient of the block's samples -> partial[block][total]; loss -> lpart[block]
+// Mean-squared-error gradient of the block's samples -> partial[block][total]; loss ->
+// lpart[block].  Phase 1: one thread per sample runs forward and backward and leaves its
+// activations and error signals in shared memory; phase 2: threads over parameters sum
+// the block's outer products in a fixed order (no atomics).
 __global__ void k_mlp_grad(Dims d, const float *__restrict__ params, const float *__restrict__ Xs,
                            const float *__restrict__ ys, int n, float *__restrict__ partial,
                            float *__restrict__ lpart) {
   extern __shared__ float sm[];
-  float *w = sm;
-  float *g = sm + d.total;
-  for (int k = threadIdx.x; k < d.total; k += blockDim.x) {
-    w[k] = params[k];
-    g[k] = 0.f;
-  }
+  const int B = blockDim.x, H = d.h;
+  float *w = sm;                                  // [total]
+  float *H1 = w + d.total;                        // [B][H] layer-1 activations
+  float *D2 = H1 + (size_t)B * H;                 // [B][H] error at layer-2 pre-activations
+  float *DZ = D2 + (size_t)B * H;                 // [B][H] error at layer-1 pre-activations
+  float *O2 = DZ + (size_t)B * H;                 // [B][H] dout * h2
+  float *XS = O2 + (size_t)B * H;                 // [B][n_in]
+  float *DO = XS + (size_t)B * d.n_in;            // [B] dout
+  for (int k = threadIdx.x; k < d.total; k += B) w[k] = params[k];
   __shared__ float lred[kThreads];
   __syncthreads();
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = threadIdx.x, s = blockIdx.x * B + t;
   float loss = 0.f;
-  if (s < n) {
+  {
     float x[kMaxIn], h1[kMaxH], h2[kMaxH];
-    for (int q = 0; q < d.n_in; ++q) x[q] = Xs[(size_t)s * d.n_in + q];
-    const float o = forward(d, w, x, h1, h2);
-    const float r = o - ys[s];
-    loss = r * r;
-    const float dout = 2.f * r / (float)n;
-    atomicAdd(&g[d.b3], dout);
-    // h2 <- dL/d(pre-activation of layer 2)
-    for (int k = 0; k < d.h; ++k) {
-      atomicAdd(&g[d.w3 + k], dout * h2[k]);
-      h2[k] = dout * w[d.w3 + k] * (1.f - h2[k] * h2[k]);
+    float dout = 0.f;
+    if (s < n) {
+      for (int q = 0; q < d.n_in; ++q) x[q] = Xs[(size_t)s * d.n_in + q];
+      const float o = forward(d, w, x, h1, h2);
+      const float r = o - ys[s];
+      loss = r * r;
+      dout = 2.f * r / (float)n;
+    } else {
+      for (int q = 0; q < d.n_in; ++q) x[q] = 0.f;
+      for (int k = 0; k < H; ++k) { h1[k] = 0.f; h2[k] = 0.f; }
     }
-    for (int k = 0; k < d.h; ++k) {
-      atomicAdd(&g[d.b2 + k], h2[k]);
-      for (int q = 0; q < d.h; ++q) atomicAdd(&g[d.w2 + k * d.h + q], h2[k] * h1[q]);
+    DO[t] = dout;
+    for (int q = 0; q < d.n_in; ++q) XS[t * d.n_in + q] = x[q];
+    for (int k = 0; k < H; ++k) {
+      H1[t * H + k] = h1[k];
+      O2[t * H + k] = dout * h2[k];
+      D2[t * H + k] = dout * w[d.w3 + k] * (1.f - h2[k] * h2[k]);
     }
-    for (int q = 0; q < d.h; ++q) {
+    for (int q = 0; q < H; ++q) {
       float a = 0.f;
-      for (int k = 0; k < d.h; ++k) a += w[d.w2 + k * d.h + q] * h2[k];
-      const float dz = a * (1.f - h1[q] * h1[q]);
-      atomicAdd(&g[d.b1 + q], dz);
-      for (int p = 0; p < d.n_in; ++p) atomicAdd(&g[d.w1 + q * d.n_in + p], dz * x[p]);
+      for (int k = 0; k < H; ++k) a += w[d.w2 + k * H + q] * D2[t * H + k];
+      DZ[t * H + q] = a * (1.f - h1[q] * h1[q]);
     }
   }
-  lred[threadIdx.x] = loss;
+  lred[t] = loss;
   __syncthreads();
-  for (int k = threadIdx.x; k < d.total; k += blockDim.x) partial[(size_t)blockIdx.x * d.total + k] = g[k];
-  for (int wdt = blockDim.x / 2; wdt > 0; wdt >>= 1) {
-    if (threadIdx.x < wdt) lred[threadIdx.x] += lred[threadIdx.x + wdt];
+  float *out = partial + (size_t)blockIdx.x * d.total;
+  for (int k = t; k < d.total; k += B) {
+    float g = 0.f;
+    if (k >= d.w2 && k < d.b2) {            // W2[r][c]: sum_s D2[s][r] H1[s][c]
+      const int r = (k - d.w2) / H, c = (k - d.w2) % H;
+      for (int q = 0; q < B; ++q) g += D2[q * H + r] * H1[q * H + c];
+    } else if (k >= d.w1 && k < d.b1) {     // W1[r][c]: sum_s DZ[s][r] X[s][c]
+      const int r = (k - d.w1) / d.n_in, c = (k - d.w1) % d.n_in;
+      for (int q = 0; q < B; ++q) g += DZ[q * H + r] * XS[q * d.n_in + c];
+    } else if (k >= d.b1 && k < d.w2) {
+      for (int q = 0; q < B; ++q) g += DZ[q * H + (k - d.b1)];
+    } else if (k >= d.b2 && k < d.w3) {
+      for (int q = 0; q < B; ++q) g += D2[q * H + (k - d.b2)];
+    } else if (k >= d.w3 && k < d.b3) {
+      for (int q = 0; q < B; ++q) g += O2[q * H + (k - d.w3)];
+    } else {
+      for (int q = 0; q < B; ++q) g += DO[q];
+    }
+    out[k] = g;
+  }
+  for (int wdt = B / 2; wdt > 0; wdt >>= 1) {
+    if (t < wdt) lred[t] += lred[t + wdt];
     __syncthreads();
   }
-  if (threadIdx.x == 0) lpart[blockIdx.x] = lred[0];
+  if (t == 0) lpart[blockIdx.x] = lred[0];
 }
 
 // sum the block partials in a fixed order and take one Adam step
@@ -242,7 +269,7 @@ int ltmp2_mlp_train(ltmp2_mlp *net, const float *X, const float *y, int n, int e
   }
   cudaMemcpy(dX, xs.data(), sizeof(float) * xs.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(dy, ys.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
-  const size_t smem = sizeof(float) * 2 * d.total;
+  const size_t smem = sizeof(float) * (d.total + (size_t)kThreads * (4 * d.h + d.n_in + 1));
   if (cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     cleanup();

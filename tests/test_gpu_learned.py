@@ -60,7 +60,8 @@ def test_pair_descriptors_follow_their_definitions():
     g[:, m[:, 0], m[:, 1], m[:, 2]] = s.coeff[:s.n_occ]
     rho = np.abs(np.fft.ifftn(g, axes=(1, 2, 3)) * n ** 3) ** 2
     S = np.einsum("axyz,bxyz->ab", rho, rho) / n ** 3
-    assert np.abs(d[:, 2] - np.log10(S[i, j])).max() < 1e-9
+    assert np.abs(d[:, 2] - np.log10(S[i, j] / np.sqrt(S[i, i] * S[j, j]))).max() < 1e-9
+    assert np.all(d[:, 2] <= 1e-12)                       # Cauchy-Schwarz
     diag = i == j
     assert np.all(d[diag, 3] < 1e-9) and np.all(d[diag, 6] == 1.0) and np.all(d[~diag, 6] == 0.0)
     assert np.all(d[:, 0] <= d[:, 1] + 1e-15)
@@ -82,9 +83,9 @@ def test_learned_screening_within_budget_on_unseen_system():
     Xs, ys = [], []
     for s in train:
         c = L.setup_from_solid(s, precision=L.FP32, real=True)
-        X, ex = LF.training_data(c, *_quad(s))
+        X, r = LF.training_data(c, *_quad(s))
         Xs.append(X)
-        ys.append(LF.encode(ex))
+        ys.append(r)
         L.ltmp2_destroy(c)
     net = L.Mlp(seed=11)
     net.train(np.concatenate(Xs), np.concatenate(ys), epochs=3000, lr=3e-3)
@@ -96,4 +97,5 @@ def test_learned_screening_within_budget_on_unseen_system():
     r = LF.screened_energy(c, tau, w, net, budget_ha=budget, share=1.0)
     assert abs(r["E_d"] - ed) < 1e-9 * abs(ed)
     assert abs(r["E_d"] + r["E_x"] - ed - ex) < budget
+    assert r["error_bound_Ha"] <= budget
     assert r["screened_pairs"] >= 0

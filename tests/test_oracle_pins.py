@@ -297,3 +297,13 @@ def test_working_form_is_additive_over_gprime_subsets():
     parts = [_working_form(o, tau, w, range(k, n, 3)) for k in range(3)]
     assert abs(sum(p[0] for p in parts) - full[0]) < 1e-13 * abs(full[0])
     assert abs(sum(p[1] for p in parts) - full[1]) < 1e-13 * abs(full[1])
+
+
+def test_exchange_pair_energy_bounded_by_half_direct():
+    """|e^x_ij| <= |e^d_ij| / 2 for every ordered pair (Cauchy-Schwarz: D_ab = D_ba < 0,
+    so |sum K_ab conj(K_ba) D_ab| <= sum |K_ab|^2 |D_ab|), canonical and Laplace."""
+    s = solid("tiny2", random_phases=True)
+    o = OracleSystem.from_solid(s)
+    for D in (canonical_denominator, laplace_denominator(*sinc_laplace_quadrature(6, *denominator_range(o)))):
+        r = mp2_energy(o, D)
+        assert np.all(np.abs(r["e_x"]) <= 0.5 * np.abs(r["e_d"]) * (1 + 1e-12))
