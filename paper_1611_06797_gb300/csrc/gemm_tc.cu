@@ -54,11 +54,14 @@ size_t tc_bytes(int rows_cap, int npw) {
   return sizeof(float) * kp * (4 * (size_t)rows_pad(rows_cap) + 2 * (size_t)npw) + 256;
 }
 
-cudaError_t tc_init(TcResources &r, void *mem, int rows_cap, int npw, int variant) {
+cudaError_t tc_init(TcResources &r, void *mem, int rows_cap, int npw, int variant, bool real) {
+  if (real && variant != 5) return cudaErrorInvalidValue;  // only the stacked kernel has a real form
   r.variant = variant;
+  r.real = real;
   r.rows_cap = rows_cap;
   r.npw = npw;
-  r.kpad = tc_kpad(npw);
+  // real basis: K = n_pw (a multiple of the 32-element k block), at most the complex size
+  r.kpad = real ? ((npw + tc::BK - 1) / tc::BK) * tc::BK : tc_kpad(npw);
   const int rp = rows_pad(rows_cap);
   const size_t a = (size_t)rp * r.kpad, b = (size_t)npw * r.kpad;
   float *f = static_cast<float *>(mem);
@@ -109,6 +112,11 @@ void tc_release(TcResources &r) {
 }
 
 cudaError_t tc_pack_b(const TcResources &r, const void *pt, cudaStream_t st) {
+  if (r.real) {
+    tc::k_pack_b_real<<<dim3((r.kpad + 255) / 256, r.npw), 256, 0, st>>>(static_cast<const float *>(pt), r.npw,
+                                                                           r.kpad, r.bh, r.bl);
+    return cudaGetLastError();
+  }
   tc::k_pack_b<<<dim3((r.kpad / 2 + 255) / 256, r.npw), 256, 0, st>>>(static_cast<const float2 *>(pt), r.npw,
                                                                         r.kpad, r.bh, r.bl);
   return cudaGetLastError();
@@ -121,7 +129,11 @@ cudaError_t tc_wgemm(const TcResources &r, const void *st_in, int rows, void *wt
   cudaError_t e;
   if (variant == 5) {
     const int r64 = ((rows + 63) / 64) * 64;   // zero-filled up to a whole 64-row block
-    tc::k_pack_a_stacked<<<dim3((r.kpad / 2 + 255) / 256, r64), 256, 0, st>>>(
+    if (r.real)
+      tc::k_pack_a_stacked_real<<<dim3((r.kpad + 255) / 256, r64), 256, 0, st>>>(
+          static_cast<const float2 *>(st_in), rows, r.npw, r.kpad, r.a1h, r.a1l);
+    else
+      tc::k_pack_a_stacked<<<dim3((r.kpad / 2 + 255) / 256, r64), 256, 0, st>>>(
         static_cast<const float2 *>(st_in), rows, r.npw, r.kpad, r.a1h, r.a1l);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     dim3 grid((r.npw + tc::S_BN - 1) / tc::S_BN, r64 / 64);

@@ -489,6 +489,40 @@ __global__ void k_pack_a_stacked(const float2 *__restrict__ st, int rows, int np
   }
 }
 
+// Real-basis Green's function (real orbitals): W^T = S_r^T P_r with S_r^T complex and P_r
+// real symmetric, so Re W^T = (Re S_r^T) P_r and Im W^T = (Im S_r^T) P_r over K = n_pw.
+// Stacked rows: row 128 b + r = Re of row 64 b + r, row 128 b + 64 + r = its Im;
+// B[n][q] = P_r[n][q].  The same stacked kernel then yields Re (lanes 0-63) and Im
+// (lanes 64-127) with half the k blocks of the complex form.
+__global__ void k_pack_a_stacked_real(const float2 *__restrict__ st, int rows, int npw, int kpad,
+                                      float *__restrict__ ah, float *__restrict__ al) {
+  const int m = blockIdx.y;
+  const size_t r1 = (size_t)128 * (m / 64) + (m % 64), r2 = r1 + 64;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < kpad; q += gridDim.x * blockDim.x) {
+    float re = 0.f, im = 0.f;
+    if (q < npw && m < rows) {
+      const float2 v = st[(size_t)m * npw + q];
+      re = v.x;
+      im = v.y;
+    }
+    const float h_re = tf32_rn(re), h_im = tf32_rn(im);
+    ah[r1 * kpad + q] = h_re;
+    al[r1 * kpad + q] = tf32_rn(re - h_re);
+    ah[r2 * kpad + q] = h_im;
+    al[r2 * kpad + q] = tf32_rn(im - h_im);
+  }
+}
+__global__ void k_pack_b_real(const float *__restrict__ pr, int npw, int kpad, float *__restrict__ bh,
+                              float *__restrict__ bl) {
+  const int n = blockIdx.y;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < kpad; q += gridDim.x * blockDim.x) {
+    const float v = q < npw ? pr[(size_t)n * npw + q] : 0.f;
+    const float h = tf32_rn(v);
+    bh[(size_t)n * kpad + q] = h;
+    bl[(size_t)n * kpad + q] = tf32_rn(v - h);
+  }
+}
+
 __global__ void __launch_bounds__(160, 1)
     k_tc_cgemm_stacked(const __grid_constant__ CUtensorMap tah, const __grid_constant__ CUtensorMap tal,
                        const __grid_constant__ CUtensorMap tbh, const __grid_constant__ CUtensorMap tbl, int M,

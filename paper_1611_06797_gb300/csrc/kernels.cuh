@@ -122,6 +122,142 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cpx<T>
     }
 }
 
+// ---------------------------------------------------------------- real-basis GEMM
+// C[m][n] = sum_k opA(m,k) * B[k][n] * s_k with B real and A (hence C) either real
+// (TA = T) or complex (TA = cpx<T>): the Green's function in the real basis (real x real)
+// and the transformed states (complex x real, two multiply-adds per term).  Same tiling
+// and two-level FP32 summation as k_cgemm.
+template <typename T> __device__ __forceinline__ void rmac(T &c, T a, T b) { c = fma(a, b, c); }
+template <typename T> __device__ __forceinline__ void rmac(cpx<T> &c, cpx<T> a, T b) {
+  c.x = fma(a.x, b, c.x);
+  c.y = fma(a.y, b, c.y);
+}
+template <typename T> __device__ __forceinline__ void radd(T &c, T a) { c += a; }
+template <typename T> __device__ __forceinline__ void radd(cpx<T> &c, cpx<T> a) { c.x += a.x; c.y += a.y; }
+template <typename X> __device__ __forceinline__ X rzero() { return X{}; }
+
+template <typename T, typename TA, bool A_KM>
+__global__ void __launch_bounds__(256) k_rgemm(int M, int N, int K, const TA *__restrict__ A, int lda,
+                                               const T *__restrict__ B, int ldb, const T *__restrict__ kscale,
+                                               TA *__restrict__ C, int ldc) {
+  constexpr int BM = 64, BN = 64, BK = 8;
+  __shared__ TA As[BK][BM];
+  __shared__ T Bs[BK][BN];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  TA acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = rzero<TA>();
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int e = threadIdx.x; e < BM * BK; e += 256) {
+      int mm, kk;
+      if (A_KM) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      TA v = rzero<TA>();
+      if (gm < M && gk < K) v = A_KM ? A[(size_t)gm * lda + gk] : A[(size_t)gk * lda + gm];
+      As[kk][mm] = v;
+    }
+    for (int e = threadIdx.x; e < BN * BK; e += 256) {
+      const int nn = e % BN, kk = e / BN;
+      const int gn = n0 + nn, gk = k0 + kk;
+      T v = T(0);
+      if (gn < N && gk < K) {
+        v = B[(size_t)gk * ldb + gn];
+        if (kscale) v *= kscale[gk];
+      }
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+    constexpr bool kTwoLevel = std::is_same<T, float>::value;
+    TA part[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[i][j] = kTwoLevel ? rzero<TA>() : acc[i][j];
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      TA a[4];
+      T b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) rmac(part[i][j], a[i], b[j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (kTwoLevel) radd(acc[i][j], part[i][j]);
+        else acc[i][j] = part[i][j];
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+      if (gm < M && gn < N) C[(size_t)gm * ldc + gn] = acc[i][j];
+    }
+}
+
+// Real cos/sin basis of the orbital sphere (real orbitals).  For G_q in the primary half
+// (first non-zero Miller index > 0) slot q holds the cos coordinate and slot qbar (-G_q)
+// the sin coordinate of the pair; slot G = 0 is its own.  The map U (plane-wave
+// coefficients -> real-basis coordinates) is unitary:
+//     (U x)[q]    = (x(q) + x(qbar)) / sqrt2,   (U x)[qbar] = i (x(q) - x(qbar)) / sqrt2,
+// and real functions have real coordinates, so P_v(tau) = U^+ P_r U with P_r real
+// symmetric and W = P_v S = U^+ (P_r (U S)).
+__device__ __forceinline__ bool pw_primary(const int *m) {
+  return m[0] != 0 ? m[0] > 0 : (m[1] != 0 ? m[1] > 0 : m[2] > 0);
+}
+template <typename T> __device__ __forceinline__ cpx<T> to_real_basis(const int *m, cpx<T> xq, cpx<T> xb) {
+  constexpr T r2 = T(0.70710678118654752440084436210485);
+  if (m[0] == 0 && m[1] == 0 && m[2] == 0) return xq;
+  if (pw_primary(m)) return {(xq.x + xb.x) * r2, (xq.y + xb.y) * r2};
+  // slot q carries the sin coordinate of the pair (qbar, q): i (x(qbar) - x(q)) / sqrt2
+  return {-(xb.y - xq.y) * r2, (xb.x - xq.x) * r2};
+}
+template <typename T> __device__ __forceinline__ cpx<T> from_real_basis(const int *m, cpx<T> wq, cpx<T> wb) {
+  constexpr T r2 = T(0.70710678118654752440084436210485);
+  if (m[0] == 0 && m[1] == 0 && m[2] == 0) return wq;
+  // primary q: x(q) = (w[q] - i w[qbar]) / sqrt2;  otherwise x(q) = (w[qbar] + i w[q]) / sqrt2
+  if (pw_primary(m)) return {(wq.x + wb.y) * r2, (wq.y - wb.x) * r2};
+  return {(wb.x - wq.y) * r2, (wb.y + wq.x) * r2};
+}
+
+// S^T in the real basis: row (slot, j) = U (e^{(e_j-mu)tau} e^{-iG'r} phi_j)
+template <typename T>
+__global__ void k_gather_s_real(Plan p, int gp0, int np, cpx<T> *__restrict__ st) {
+  const int col = blockIdx.y;
+  const int slot = col / p.n_occ, j = col % p.n_occ;
+  const int g = slot_aux(p, gp0, np, slot);
+  const int gx = p.aux_m[3 * g], gy = p.aux_m[3 * g + 1], gz = p.aux_m[3 * g + 2];
+  const T dj = ((const T *)p.dscale)[j];
+  const int n = p.n;
+  const cpx<T> *cg = (const cpx<T> *)p.cgrid + (size_t)j * n * n * n;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < p.n_pw; q += gridDim.x * blockDim.x) {
+    const int *m = p.pw_m + 3 * q;
+    const cpx<T> xq = cg[((size_t)wrapn(m[2] + gz, n) * n + wrapn(m[1] + gy, n)) * n + wrapn(m[0] + gx, n)];
+    const cpx<T> xb = cg[((size_t)wrapn(gz - m[2], n) * n + wrapn(gy - m[1], n)) * n + wrapn(gx - m[0], n)];
+    st[(size_t)col * p.n_pw + q] = cscale(to_real_basis<T>(m, xq, xb), dj);
+  }
+}
+
+// W^T rows back from real-basis coordinates to plane-wave coefficients
+template <typename T>
+__global__ void k_from_real_basis(Plan p, const cpx<T> *__restrict__ w, cpx<T> *__restrict__ out) {
+  const size_t row = (size_t)blockIdx.y * p.n_pw;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < p.n_pw; q += gridDim.x * blockDim.x)
+    out[row + q] = from_real_basis<T>(p.pw_m + 3 * q, w[row + q], w[row + p.pw_pair[q]]);
+}
+
 // ---------------------------------------------------------------- gather S^T
 // S^T[(slot, j)][q] = e^{(e_j - mu) tau} c_j((G_q + G'_slot) mod grid): the plane-wave
 // coefficients of e^{-iG'r} phi_j restricted to the orbital sphere, scaled.

@@ -212,6 +212,31 @@ int upload_coeff(ltmp2_ctx *c, const double *coeff, int n_pw, int row0, int rows
   return cuda_status(cudaMemcpy(*dst, h.data(), h.size() * sizeof(CT<T>), cudaMemcpyHostToDevice));
 }
 
+// Real-basis coordinates of real orbitals (x(-G) = conj x(G)) in internal order: slot q
+// of a primary G_q holds sqrt2 Re x(q), the slot of -G_q holds sqrt2 Im x(-G_q), and
+// G = 0 holds Re x(0) (the unitary map U of the real-basis kernels).
+template <typename T>
+int upload_real_coeff(ltmp2_ctx *c, const ltmp2_system *sys, int row0, int rows, const std::vector<int> &order,
+                      void **dst) {
+  const int n_pw = sys->n_pw;
+  const double r2 = 1.4142135623730950488016887242097;
+  std::vector<T> h((size_t)rows * n_pw);
+  for (int q = 0; q < n_pw; ++q) {
+    const int o = order[q];
+    const int *m = sys->miller + 3 * o;
+    const int kind = (m[0] == 0 && m[1] == 0 && m[2] == 0)
+                         ? 0
+                         : ((m[0] != 0 ? m[0] > 0 : (m[1] != 0 ? m[1] > 0 : m[2] > 0)) ? 1 : 2);
+    for (int r = 0; r < rows; ++r) {
+      const double *src = sys->coeff + ((size_t)(row0 + r) * n_pw + o) * 2;
+      h[(size_t)r * n_pw + q] = (T)(kind == 0 ? src[0] : (kind == 1 ? r2 * src[0] : r2 * src[1]));
+    }
+  }
+  int rc = dalloc_bytes(c, dst, h.size() * sizeof(T));
+  if (rc) return rc;
+  return cuda_status(cudaMemcpy(*dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
 template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys, const std::vector<int> &order) {
   Plan &p = c->p;
   cudaError_t e = Path<T>::init_device();
@@ -219,13 +244,17 @@ template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys,
   const size_t cs = sizeof(CT<T>);
   const size_t n3 = (size_t)p.n * p.n * p.n;
   int rc;
-  if ((rc = upload_coeff<T>(c, sys->coeff, p.n_pw, p.n_occ, p.n_v, order, &p.cv))) return rc;
+  if (p.real_basis) {
+    if ((rc = upload_real_coeff<T>(c, sys, p.n_occ, p.n_v, order, &p.cv))) return rc;
+  } else {
+    if ((rc = upload_coeff<T>(c, sys->coeff, p.n_pw, p.n_occ, p.n_v, order, &p.cv))) return rc;
+  }
   void *cocc = nullptr;
   if ((rc = upload_coeff<T>(c, sys->coeff, p.n_pw, 0, p.n_occ, order, &cocc))) return rc;
   if ((rc = dalloc_bytes(c, &p.cgrid, cs * n3 * p.n_occ))) return rc;
   if ((rc = dalloc_bytes(c, &p.u, cs * n3 * p.n_occ))) return rc;
   if ((rc = dalloc_bytes(c, &p.dscale, sizeof(T) * p.n_orb))) return rc;
-  if ((rc = dalloc_bytes(c, &p.pt, cs * (size_t)p.n_pw * p.n_pw))) return rc;
+  if ((rc = dalloc_bytes(c, &p.pt, (p.real_basis ? sizeof(T) : cs) * (size_t)p.n_pw * p.n_pw))) return rc;
   // slab capacity from the free memory
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
@@ -254,7 +283,7 @@ template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys,
     void *tcmem = nullptr;
     if ((rc = dalloc_bytes(c, &tcmem, tc_bytes((int)max_cols, p.n_pw)))) return rc;
     c->tc_mem = tcmem;
-    e = tc_init(c->tc, tcmem, (int)max_cols, p.n_pw, 5);
+    e = tc_init(c->tc, tcmem, (int)max_cols, p.n_pw, 5, p.real_basis);
     if (e != cudaSuccess) return cuda_status(e);
     p.tc = &c->tc;
   }
@@ -378,7 +407,7 @@ int apply_tuning(ltmp2_ctx *c, int slab, int variant, int plane_kernel = 0, int 
   c->p.plane_ib = plane_ib;
   if (c->p.tc && variant >= 0 && variant != c->tc.variant) {
     tc_release(c->tc);
-    cudaError_t e = tc_init(c->tc, c->tc_mem, c->tc.rows_cap, c->p.n_pw, variant);
+    cudaError_t e = tc_init(c->tc, c->tc_mem, c->tc.rows_cap, c->p.n_pw, variant, c->tc.real);
     if (e != cudaSuccess) return cuda_status(e);
   }
   return LTMP2_OK;
@@ -400,7 +429,8 @@ template <typename T> int tune_ctx(ltmp2_ctx *c, int *slab_out, int *var_out) {
   }
   std::vector<int> slabs;
   for (int sl = std::min(c->slab_capacity, p.n_prim); sl >= 1 && slabs.size() < 4; sl /= 2) slabs.push_back(sl);
-  std::vector<int> variants = p.tc ? std::vector<int>{5, 4} : std::vector<int>{-1};
+  std::vector<int> variants =
+      p.tc ? (c->tc.real ? std::vector<int>{5} : std::vector<int>{5, 4}) : std::vector<int>{-1};
   cudaEvent_t a = nullptr, b = nullptr;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return LTMP2_ERR_CUDA;
   double best = 1e300;
@@ -650,6 +680,7 @@ int ltmp2_setup(const ltmp2_system *sys, ltmp2_ctx **out) {
   p.n_aux = naux;
   p.n_prim = (int)prim.size();
   p.real_orb = real_orb;
+  p.real_basis = real_orb;
   p.precision = sys->precision;
   p.omega = omega;
   p.mu = 0.5 * (sys->eps[no - 1] + sys->eps[no]);
@@ -684,6 +715,13 @@ int ltmp2_setup(const ltmp2_system *sys, ltmp2_ctx **out) {
   if (!rc) rc = up(&p.daux, hdaux);
   if (!rc) rc = up(&p.daux_off, hdaux_off);
   if (!rc) rc = up(&p.pw_m, hpw);
+  if (!rc && p.real_basis) {
+    // internal position of -G_q for every internal q
+    std::vector<int> pos(npw), hpair(npw);
+    for (int q = 0; q < npw; ++q) pos[order[q]] = q;
+    for (int q = 0; q < npw; ++q) hpair[q] = pos[negpw[order[q]]];
+    rc = up(&p.pw_pair, hpair);
+  }
   if (!rc) rc = up(&p.aux_m, haux);
   if (!rc) rc = up(&p.aux_neg, aneg);
   if (!rc) rc = up(&p.prim, prim);

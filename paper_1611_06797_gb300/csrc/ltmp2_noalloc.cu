@@ -133,12 +133,26 @@ int run_noalloc(const ltmp2_system *sys, Plan &p, Arena &ar, const std::vector<i
       if (r < p.n_occ) ho[(size_t)r * p.n_pw + q] = v;
       else hv[(size_t)(r - p.n_occ) * p.n_pw + q] = v;
     }
+  // real orbitals: the virtuals' real-basis coordinates (see the real-basis kernels)
+  std::vector<T> hr;
+  if (p.real_basis) {
+    hr.resize((size_t)p.n_v * p.n_pw);
+    const T r2 = (T)1.4142135623730950488016887242097;
+    for (int r = 0; r < p.n_v; ++r)
+      for (int q = 0; q < p.n_pw; ++q) {
+        const int *mq = sys->miller + 3 * order[q];
+        const C2 v = hv[(size_t)r * p.n_pw + q];
+        const bool zero = mq[0] == 0 && mq[1] == 0 && mq[2] == 0;
+        const bool prim = mq[0] != 0 ? mq[0] > 0 : (mq[1] != 0 ? mq[1] > 0 : mq[2] > 0);
+        hr[(size_t)r * p.n_pw + q] = zero ? v.x : (prim ? r2 * v.x : r2 * v.y);
+      }
+  }
   void *cocc = ar.take(ho.size() * cs);
-  p.cv = ar.take(hv.size() * cs);
+  p.cv = p.real_basis ? ar.take(hr.size() * sizeof(T)) : ar.take(hv.size() * cs);
   p.cgrid = ar.take(cs * n3 * p.n_occ);
   p.u = ar.take(cs * n3 * p.n_occ);
   p.dscale = ar.take(sizeof(T) * p.n_orb);
-  p.pt = ar.take(cs * (size_t)p.n_pw * p.n_pw);
+  p.pt = ar.take((p.real_basis ? sizeof(T) : cs) * (size_t)p.n_pw * p.n_pw);
   const size_t no2 = (size_t)p.n_occ * p.n_occ;
   p.ex = (double *)ar.take(no2 * sizeof(double));
   p.ed = (double *)ar.take(no2 * sizeof(double));
@@ -171,7 +185,11 @@ int run_noalloc(const ltmp2_system *sys, Plan &p, Arena &ar, const std::vector<i
 
   int rc;
   if ((rc = copy_in(cocc, ho.data(), ho.size() * cs, st))) return rc;
-  if ((rc = copy_in(p.cv, hv.data(), hv.size() * cs, st))) return rc;
+  if (p.real_basis) {
+    if ((rc = copy_in(p.cv, hr.data(), hr.size() * sizeof(T), st))) return rc;
+  } else {
+    if ((rc = copy_in(p.cv, hv.data(), hv.size() * cs, st))) return rc;
+  }
   if (Path<T>::init_device() != cudaSuccess) return LTMP2_ERR_CUDA;
   if (Path<T>::setup_occupied(p, cocc, st) != cudaSuccess) return LTMP2_ERR_CUDA;
   // the energy loop of ltmp2_energy, in the same order
@@ -322,6 +340,7 @@ extern "C" int ltmp2_energy_noalloc(const ltmp2_system *sys, int n_tau, const do
   p.n_aux = naux;
   p.n_prim = (int)prim.size();
   p.real_orb = real_orb;
+  p.real_basis = real_orb;
   p.precision = sys->precision;
   p.omega = std::fabs(det);
   p.mu = 0.5 * (sys->eps[no - 1] + sys->eps[no]);
@@ -356,6 +375,12 @@ extern "C" int ltmp2_energy_noalloc(const ltmp2_system *sys, int n_tau, const do
   if ((rc = put(&p.daux, hdaux))) return rc;
   if ((rc = put(&p.daux_off, hdaux_off))) return rc;
   if ((rc = put(&p.pw_m, hpw))) return rc;
+  if (real_orb) {
+    std::vector<int> pos(npw), hpair(npw);
+    for (int q = 0; q < npw; ++q) pos[order[q]] = q;
+    for (int q = 0; q < npw; ++q) hpair[q] = pos[negpw[order[q]]];
+    if ((rc = put(&p.pw_pair, hpair))) return rc;
+  }
   if ((rc = put(&p.aux_m, haux))) return rc;
   if ((rc = put(&p.aux_neg, aneg))) return rc;
   if ((rc = put(&p.prim, prim))) return rc;

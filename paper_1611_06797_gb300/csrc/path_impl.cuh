@@ -125,12 +125,18 @@ cudaError_t Path<T>::green(const Plan &p, double tau, cudaStream_t st, StageTime
   k_dscale<T><<<(p.n_orb + 255) / 256, 256, 0, st>>>(p.n_orb, p.n_occ, p.eps, p.mu, tau, (T *)p.dscale);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // P^T[q][p] = sum_a conj(c_a(q)) e^{-(e_a-mu)tau} c_a(p)
   const int M = p.n_pw, N = p.n_pw, K = p.n_v;
   dim3 grid((N + 63) / 64, (M + 63) / 64);
-  k_cgemm<T, false, true><<<grid, 256, 0, st>>>(M, N, K, (const cpx<T> *)p.cv, p.n_pw,
-                                                (const cpx<T> *)p.cv, p.n_pw,
-                                                (const T *)p.dscale + p.n_occ, (cpx<T> *)p.pt, p.n_pw);
+  if (p.real_basis) {
+    // P_r[q][p] = sum_a r_a(q) e^{-(e_a-mu)tau} r_a(p), r_a the real coordinates of a
+    k_rgemm<T, T, false><<<grid, 256, 0, st>>>(M, N, K, (const T *)p.cv, p.n_pw, (const T *)p.cv, p.n_pw,
+                                               (const T *)p.dscale + p.n_occ, (T *)p.pt, p.n_pw);
+  } else {
+    // P^T[q][p] = sum_a conj(c_a(q)) e^{-(e_a-mu)tau} c_a(p)
+    k_cgemm<T, false, true><<<grid, 256, 0, st>>>(M, N, K, (const cpx<T> *)p.cv, p.n_pw,
+                                                  (const cpx<T> *)p.cv, p.n_pw,
+                                                  (const T *)p.dscale + p.n_occ, (cpx<T> *)p.pt, p.n_pw);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if constexpr (std::is_same<T, float>::value) {
@@ -147,7 +153,10 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
   cudaError_t e;
   {
     ScopedStage s(tm, kStageGatherZ);
-    k_gather_s<T><<<dim3((p.n_pw + 255) / 256, ncols), 256, 0, st>>>(p, gp0, np, (cpx<T> *)p.st);
+    if (p.real_basis)
+      k_gather_s_real<T><<<dim3((p.n_pw + 255) / 256, ncols), 256, 0, st>>>(p, gp0, np, (cpx<T> *)p.st);
+    else
+      k_gather_s<T><<<dim3((p.n_pw + 255) / 256, ncols), 256, 0, st>>>(p, gp0, np, (cpx<T> *)p.st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
@@ -161,11 +170,25 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
     }
     if (!done) {
       dim3 grid((p.n_pw + 63) / 64, (ncols + 63) / 64);
-      k_cgemm<T, true, false><<<grid, 256, 0, st>>>(ncols, p.n_pw, p.n_pw, (const cpx<T> *)p.st, p.n_pw,
-                                                    (const cpx<T> *)p.pt, p.n_pw, nullptr,
-                                                    (cpx<T> *)p.wt, p.n_pw);
+      if (p.real_basis)
+        k_rgemm<T, cpx<T>, true><<<grid, 256, 0, st>>>(ncols, p.n_pw, p.n_pw, (const cpx<T> *)p.st, p.n_pw,
+                                                        (const T *)p.pt, p.n_pw, nullptr, (cpx<T> *)p.wt,
+                                                        p.n_pw);
+      else
+        k_cgemm<T, true, false><<<grid, 256, 0, st>>>(ncols, p.n_pw, p.n_pw, (const cpx<T> *)p.st, p.n_pw,
+                                                      (const cpx<T> *)p.pt, p.n_pw, nullptr,
+                                                      (cpx<T> *)p.wt, p.n_pw);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+  }
+  // real basis: W^T back to plane-wave coefficients, into the (now free) S^T buffer
+  const cpx<T> *w_pw = (const cpx<T> *)p.wt;
+  if (p.real_basis) {
+    ScopedStage s(tm, kStageGatherZ);
+    k_from_real_basis<T><<<dim3((p.n_pw + 255) / 256, ncols), 256, 0, st>>>(p, (const cpx<T> *)p.wt,
+                                                                            (cpx<T> *)p.st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    w_pw = (const cpx<T> *)p.st;
   }
   const size_t smem_col = (size_t)p.n_aux * sizeof(cpx<T>);
   const int npairs = p.real_orb ? np * (no * (no + 1) / 2) : np * no * no;
@@ -176,8 +199,7 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
   case NN: {                                                                                            \
     {                                                                                                   \
       ScopedStage s(tm, kStageGatherZ);                                                                 \
-      k_w_zinv<T, NN><<<dim3((p.n_dorb + 127) / 128, ncols), 128, 0, st>>>(p, p.n_pw,                    \
-                                                                          (const cpx<T> *)p.wt,          \
+      k_w_zinv<T, NN><<<dim3((p.n_dorb + 127) / 128, ncols), 128, 0, st>>>(p, p.n_pw, w_pw,              \
                                                                           (cpx<T> *)p.z1);               \
       if ((e = cudaGetLastError()) != cudaSuccess) return e;                                            \
     }                                                                                                   \

@@ -10,13 +10,14 @@ namespace ltmp2 {
 struct TcResources {
   int rows_cap = 0, npw = 0, kpad = 0;
   int variant = 5;         // 0-3 single-pass (tests), 4 drained N=64, 5 stacked Re/Im deep ring
+  bool real = false;       // real-basis Green's function: K = n_pw (variant 5 only)
   float *a1h = nullptr, *a1l = nullptr, *a2h = nullptr, *a2l = nullptr, *bh = nullptr, *bl = nullptr;
   int *err = nullptr;      // device flag: a bounded wait ran out
   void *maps = nullptr;    // host copy of the six TMA tensor maps
 };
 int tc_kpad(int npw);
 size_t tc_bytes(int rows_cap, int npw);
-cudaError_t tc_init(TcResources &r, void *mem, int rows_cap, int npw, int variant);
+cudaError_t tc_init(TcResources &r, void *mem, int rows_cap, int npw, int variant, bool real = false);
 int tc_variant_bn(int variant);
 void tc_release(TcResources &r);
 cudaError_t tc_pack_b(const TcResources &r, const void *pt, cudaStream_t st);
@@ -34,6 +35,10 @@ struct Plan {
   int n_prim = 0;            // primary G' (first non-zero Miller index > 0)
   int mxlo_orb = 0, mxhi_orb = 0, mxlo_aux = 0, mxhi_aux = 0;
   bool real_orb = false;
+  // real_orb and the Green's function is built in the real cos/sin basis: cv holds the
+  // real coordinates of the virtuals, pt the real symmetric P_v, and the W product is
+  // complex x real (half the multiply-adds of the complex product)
+  bool real_basis = false;
   int precision = 0;         // 0 = FP64, 1 = FP32
   double omega = 0.0, mu = 0.0;
 
@@ -43,6 +48,7 @@ struct Plan {
   int4 *daux = nullptr;      // [n_daux]
   int *daux_off = nullptr;   // [n_daux]
   int *pw_m = nullptr;       // [n_pw * 3] Miller indices of the orbital sphere, internal order
+  int *pw_pair = nullptr;    // [n_pw] internal position of -G_q (real basis only)
   int *aux_m = nullptr;      // [n_aux * 3]
   int *aux_neg = nullptr;    // [n_aux] position of -G in A
   int *prim = nullptr;       // [n_prim] position in A of each primary G'
@@ -51,11 +57,11 @@ struct Plan {
   double *eps = nullptr;     // [n_orb] (device)
 
   // precision-dependent device data (cpx<T>)
-  void *cv = nullptr;        // [n_v][n_pw] virtual coefficients, internal order
+  void *cv = nullptr;        // [n_v][n_pw] virtual coefficients, internal order (T if real_basis)
   void *cgrid = nullptr;     // [n_occ][n^3] occupied coefficients scattered on the grid
   void *u = nullptr;         // [n_occ][n^3] occupied orbitals in real space, [z][y][x]
   void *dscale = nullptr;    // [n_orb] T: virtual e^{-(e_a-mu)tau}, occupied e^{(e_j-mu)tau}
-  void *pt = nullptr;        // [n_pw][n_pw] transposed Green's function P^T
+  void *pt = nullptr;        // [n_pw][n_pw] transposed Green's function P^T (real P if real_basis)
   void *st = nullptr;        // [max_cols][n_pw] gathered, scaled e^{-iG'r}|j> (S^T)
   void *wt = nullptr;        // [max_cols][n_pw] transformed states W^T
   void *z1 = nullptr;        // [max_cols][n][n_dorb] W after the inverse z transform
@@ -93,7 +99,7 @@ template <typename T> struct Path {
   // kernel launches per Green's function build and per slab (the tcgen05 path of the
   // precision form adds one operand-packing launch to each)
   static int green_launches(const Plan &p) { return p.tc ? 3 : 2; }
-  static int slab_launches(const Plan &p) { return p.tc ? 8 : 7; }
+  static int slab_launches(const Plan &p) { return (p.tc ? 8 : 7) + (p.real_basis ? 1 : 0); }
   static cudaError_t init_device();
   // setup: occupied orbitals -> u (real space) and cgrid
   static cudaError_t setup_occupied(const Plan &p, const void *c_occ_dev, cudaStream_t st);
