@@ -8,9 +8,11 @@ from .ltmp2_oracle import (OracleSystem, aux_set, overlap_densities_conv,
                            overlap_densities_fft, overlap_densities_dft, pair_integrals,
                            mp2_pair_energy, mp2_energy, sinc_laplace_quadrature,
                            quadrature_max_error, canonical_denominator, laplace_denominator,
-                           denominator_range)
+                           denominator_range, cutoff_levels, level_energies,
+                           cutoff_extrapolation)
 
 __all__ = ["OracleSystem", "aux_set", "overlap_densities_conv", "overlap_densities_fft",
            "overlap_densities_dft", "pair_integrals", "mp2_pair_energy", "mp2_energy",
            "sinc_laplace_quadrature", "quadrature_max_error", "canonical_denominator",
-           "laplace_denominator", "denominator_range"]
+           "laplace_denominator", "denominator_range", "cutoff_levels", "level_energies",
+           "cutoff_extrapolation"]

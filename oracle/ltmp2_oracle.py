@@ -310,3 +310,57 @@ def quadrature_max_error(tau: np.ndarray, w: np.ndarray, xmin: float, xmax: floa
     x = np.geomspace(xmin, xmax, samples)
     s = np.exp(-np.outer(x, tau)) @ w
     return float(np.max(np.abs(1.0 - x * s)))
+
+
+# ---------------------------------------------------------------------------
+# Internal auxiliary-cutoff extrapolation (Sec. III D, Eq. CutDecay)
+# ---------------------------------------------------------------------------
+def cutoff_levels(ecut_aux: float, n_c: int = 8, alpha: float = 1.05) -> np.ndarray:
+    """The nested auxiliary cutoffs E_aux[n] = E_aux / alpha^(n-1), n = 1..n_c."""
+    if n_c < 1 or not alpha > 1.0:
+        raise ValueError("need n_c >= 1 and alpha > 1")
+    return ecut_aux / alpha ** np.arange(n_c, dtype=float)
+
+
+def level_energies(sys: OracleSystem, D: Callable[[np.ndarray], np.ndarray], n_c: int = 8,
+                   alpha: float = 1.05):
+    """MP2 energies with every auxiliary G-sum (both the inner G and the outer G' of
+    Eq. SCHfocklike / dLTMP2Compact) truncated at each nested cutoff E_aux[n].
+
+    Written as its definition: the whole calculation repeated with A replaced by
+    A_n = {G != 0 : |G|^2/2 <= E_aux[n]}.  Returns (ecut[n], |A_n|, E_d[n], E_x[n]).
+    """
+    ecut = cutoff_levels(sys.ecut_aux, n_c, alpha)
+    counts, ed, ex = [], [], []
+    for e in ecut:
+        s = dataclasses.replace(sys, ecut_aux=float(e))
+        counts.append(len(aux_set(s)[0]))
+        r = mp2_energy(s, D)
+        ed.append(r["E_d"])
+        ex.append(r["E_x"])
+    return ecut, np.array(counts), np.array(ed), np.array(ex)
+
+
+def cutoff_extrapolation(ecut: Sequence[float], energy: Sequence[float]) -> Tuple[float, float, float]:
+    """Least-squares line y = a + b x through y = E[n], x = E_aux[n]^(-3/2) (Eq. CutDecay).
+
+    Returns (a, b, sigma_a); a is the energy extrapolated to an infinite auxiliary
+    cutoff and sigma_a its standard error from the fit residuals (the paper quotes
+    such a fitting error with its extrapolated energies, Sec. IV C; 0 for two points).
+    The normal equations of the straight-line fit, written out.
+    """
+    x = np.asarray(ecut, float) ** -1.5
+    y = np.asarray(energy, float)
+    if len(x) < 2:
+        raise ValueError("need at least two cutoffs")
+    n = float(len(x))
+    sx, sy = float(np.sum(x)), float(np.sum(y))
+    sxx, sxy = float(np.sum(x * x)), float(np.sum(x * y))
+    det = n * sxx - sx * sx
+    b = (n * sxy - sx * sy) / det
+    a = (sy - b * sx) / n
+    sa = 0.0
+    if len(x) > 2:
+        s2 = float(np.sum((y - a - b * x) ** 2)) / (n - 2.0)
+        sa = math.sqrt(s2 * sxx / det)
+    return a, b, sa
