@@ -236,6 +236,37 @@ int ltmp2_mlp_train(ltmp2_mlp *net, const float *X, const float *y, int n, int e
 int ltmp2_mlp_predict(const ltmp2_mlp *net, const float *X, int n, float *y);
 void ltmp2_mlp_destroy(ltmp2_mlp *net);
 
+/* ---------------------------------------------------------------- internal cutoff extrapolation
+ * Sec. III D, Eq. CutDecay: the MP2 energy converges with the auxiliary cutoff as
+ * E(E_aux) - E(inf) ~ E_aux^(-3/2).  With n_c levels, every later ltmp2_energy* call
+ * also evaluates the energy on the nested spheres A_n = {G : |G|^2/2 <= E_aux[n]},
+ * E_aux[n] = E_aux / alpha^(n-1), n = 1..n_c (A_1 = A; both the inner G-sum and the
+ * outer G'-sum are truncated), in the same pass: only the column and direct-term
+ * contractions group their G-sums by level, plus one accumulation launch per slab.   */
+
+/* n_c <= 1 switches the levels off; 2 <= n_c <= LTMP2_MAX_LEVELS, alpha > 1 (the paper
+ * uses n_c = 8, alpha = 1.05).  The first call allocates the level accumulators
+ * (2 x 16 x slab capacity x n_occ^2 x 16 bytes).  Errors: INVALID_ARG; UNSUPPORTED when
+ * the column kernel's shared memory (2 |A| complex values) exceeds 200 KB (FP64 with
+ * |A| > 6400); OOM; CUDA.                                                            */
+#define LTMP2_MAX_LEVELS 16
+int ltmp2_set_extrapolation(ltmp2_ctx *ctx, int n_c, double alpha);
+
+/* Per level n (arrays of n_c entries on the host, any may be NULL): the cutoff E_aux[n]
+ * (Ha), |A_n| (G = 0 excluded), and E_direct[n], E_exchange[n] (Ha per cell) of the
+ * last ltmp2_energy* call made with these levels (level 1 equals that call's result).
+ * INVALID_ARG when the levels are off, or energies are asked for before such a call. */
+int ltmp2_level_energies(const ltmp2_ctx *ctx, double *ecut_aux, int *n_aux, double *e_direct,
+                         double *e_exchange);
+
+/* Least-squares line y = a + b x through the n >= 2 points y = energy[k],
+ * x = ecut_aux[k]^(-3/2) (Eq. CutDecay): *e_inf = a (the extrapolated energy),
+ * *slope = b, *sigma = standard error of a from the residuals (0 for n = 2); slope
+ * and sigma may be NULL.  Host arithmetic only.  INVALID_ARG on non-positive or equal
+ * cutoffs.                                                                           */
+int ltmp2_extrapolate(int n, const double *ecut_aux, const double *energy, double *e_inf, double *slope,
+                      double *sigma);
+
 /* Number of primary G' vectors (half of |A|); returns < 0 on a NULL ctx.        */
 int ltmp2_num_primary_gprime(const ltmp2_ctx *ctx);
 

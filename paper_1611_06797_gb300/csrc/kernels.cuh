@@ -525,11 +525,49 @@ __device__ __forceinline__ void block_reduce_store(double ax, double ay, double2
   }
 }
 
-template <typename T, int N>
-__global__ void k_zcol(Plan p, int gp0, int np, const cpx<T> *__restrict__ tbuf, cpx<T> *__restrict__ mdiag,
+// Level-resolved sums (internal cutoff extrapolation): terms staged per G in PR[]; warp w
+// sums the groups n = w, w + nw, ... of lev_order (G with L(G) = n + 1), so each level
+// costs one warp reduction.  Thread 0 then runs from the innermost level outwards: the
+// running sum is the sum over A_n, stored for n = 1 in dst1 and for n >= 2 in lev.
+template <typename T>
+__device__ __forceinline__ void level_reduce_store(const Plan &p, const cpx<T> *PR, size_t elem, size_t elem_t,
+                                                   bool transpose, double2 *dst1, double2 *lev) {
+  __shared__ double lred[kMaxLevels][2];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int w = tid / 32, l = tid % 32, nw = nth / 32;   // blockDim.x is a multiple of 32
+  for (int n = w; n < p.n_lev; n += nw) {
+    T bx = T(0), by = T(0);
+    for (int k = p.lev_start[n] + l; k < p.lev_start[n + 1]; k += 32) {
+      const cpx<T> t = PR[p.lev_order[k]];
+      bx += t.x;
+      by += t.y;
+    }
+    double dx = (double)bx, dy = (double)by;
+    for (int o = 16; o > 0; o >>= 1) {
+      dx += __shfl_xor_sync(0xffffffffu, dx, o);
+      dy += __shfl_xor_sync(0xffffffffu, dy, o);
+    }
+    if (l == 0) { lred[n][0] = dx; lred[n][1] = dy; }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double rx = 0.0, ry = 0.0;
+    for (int n = p.n_lev - 1; n >= 0; --n) {
+      rx += lred[n][0];
+      ry += lred[n][1];
+      double2 *base = n == 0 ? dst1 : lev + (size_t)n * p.lev_stride;
+      base[elem] = make_double2(rx, ry);
+      if (transpose) base[elem_t] = make_double2(rx, -ry);
+    }
+  }
+}
+
+template <typename T, int N, bool LEV>
+__global__ void __launch_bounds__(256) k_zcol(Plan p, int gp0, int np, const cpx<T> *__restrict__ tbuf, cpx<T> *__restrict__ mdiag,
                        double2 *__restrict__ sx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T> *MA = reinterpret_cast<cpx<T> *>(smem_raw);
+  cpx<T> *PR = MA + p.n_aux;   // LEV only: v(G) times the product, per G
   const int no = p.n_occ;
   const int tid = threadIdx.x, nth = blockDim.x;
   int i, j, gpl, slotA, slotB;
@@ -552,8 +590,11 @@ __global__ void k_zcol(Plan p, int gp0, int np, const cpx<T> *__restrict__ tbuf,
   const bool diag = (i == j);
   if (p.pair_keep && !diag && !p.pair_keep[i * no + j]) {   // screened: exchange estimated elsewhere
     if (threadIdx.x == 0) {
-      sx[((size_t)gpl * no + i) * no + j] = make_double2(0.0, 0.0);
-      if (p.real_orb) sx[((size_t)gpl * no + j) * no + i] = make_double2(0.0, 0.0);
+      for (int n = 0; n < (LEV ? p.n_lev : 1); ++n) {
+        double2 *base = n == 0 ? sx : p.sxl + (size_t)n * p.lev_stride;
+        base[((size_t)gpl * no + i) * no + j] = make_double2(0.0, 0.0);
+        if (p.real_orb) base[((size_t)gpl * no + j) * no + i] = make_double2(0.0, 0.0);
+      }
     }
     return;
   }
@@ -577,7 +618,11 @@ __global__ void k_zcol(Plan p, int gp0, int np, const cpx<T> *__restrict__ tbuf,
         const int g = off + m - c.z;
         MA[g] = a[k];
         if (diag) mdiag[((size_t)slotA * p.n_aux + g) * no + i] = a[k];
-        if (self) accx += v[g] * (a[k].x * a[k].x + a[k].y * a[k].y);
+        if (self) {
+          const T t = v[g] * (a[k].x * a[k].x + a[k].y * a[k].y);
+          if (LEV) PR[g] = {t, T(0)};
+          else accx += t;
+        }
       }
     }
   }
@@ -603,20 +648,29 @@ __global__ void k_zcol(Plan p, int gp0, int np, const cpx<T> *__restrict__ tbuf,
           } else {
             prod = cmulconj(MA[g], a[k]);
           }
-          accx += v[g] * prod.x;
-          accy += v[g] * prod.y;
+          if (LEV) {
+            PR[g] = {v[g] * prod.x, v[g] * prod.y};
+          } else {
+            accx += v[g] * prod.x;
+            accy += v[g] * prod.y;
+          }
         }
       }
     }
   }
-  double2 *dst = sx + ((size_t)gpl * no + i) * no + j;
-  double2 *dst_t = (p.real_orb && i != j) ? sx + ((size_t)gpl * no + j) * no + i : nullptr;
-  block_reduce_store<T>((double)accx, (double)accy, dst, dst_t);
+  const size_t elem = ((size_t)gpl * no + i) * no + j, elem_t = ((size_t)gpl * no + j) * no + i;
+  const bool transpose = p.real_orb && i != j;
+  if constexpr (LEV) {
+    __syncthreads();
+    level_reduce_store<T>(p, PR, elem, elem_t, transpose, sx, p.sxl);
+  } else {
+    block_reduce_store<T>((double)accx, (double)accy, sx + elem, transpose ? sx + elem_t : nullptr);
+  }
 }
 
 // ---------------------------------------------------------------- direct term
 // Y_ij(G') = sum_G v(G) M_ii(G;G') M_jj(-G;-G')  (general)  or  M_ii(G;G') conj(M_jj(G;G')) (real)
-template <typename T>
+template <typename T, bool LEV>
 __global__ void k_direct(Plan p, int np, const cpx<T> *__restrict__ mdiag, double2 *__restrict__ yd) {
   const int gpl = blockIdx.x, i = blockIdx.y;
   const int no = p.n_occ;
@@ -625,6 +679,28 @@ __global__ void k_direct(Plan p, int np, const cpx<T> *__restrict__ mdiag, doubl
   const cpx<T> *MA = mdiag + (size_t)slotA * p.n_aux * no;
   const cpx<T> *MB = mdiag + (size_t)slotB * p.n_aux * no;
   for (int j = threadIdx.x; j < no; j += blockDim.x) {
+    if constexpr (LEV) {
+      // groups from the innermost level outwards; the running sum is the sum over A_n
+      double ax = 0, ay = 0;
+      for (int n = p.n_lev - 1; n >= 0; --n) {
+        T cx = T(0), cy = T(0);
+        int cnt = 0;
+        for (int k = p.lev_start[n]; k < p.lev_start[n + 1]; ++k) {
+          const int g = p.lev_order[k];
+          const cpx<T> x = MA[(size_t)g * no + i];
+          cpx<T> prod;
+          if (!p.real_orb) prod = cmul(x, MB[(size_t)p.aux_neg[g] * no + j]);
+          else prod = cmulconj(x, MB[(size_t)g * no + j]);
+          cx += v[g] * prod.x;
+          cy += v[g] * prod.y;
+          if ((++cnt & 31) == 0) { ax += (double)cx; ay += (double)cy; cx = cy = T(0); }
+        }
+        ax += (double)cx; ay += (double)cy;
+        double2 *base = n == 0 ? yd : p.ydl + (size_t)n * p.lev_stride;
+        base[((size_t)gpl * no + i) * no + j] = make_double2(ax, ay);
+      }
+      continue;
+    }
     double ax = 0, ay = 0;
     T cx = T(0), cy = T(0);
     for (int g = 0; g < p.n_aux; ++g) {
@@ -721,10 +797,62 @@ static __global__ void k_accum(Plan p, int gp0, int np, double coef, const doubl
   p.edi[ij] += edi;
 }
 
+// level n >= 2 of the extrapolation (blockIdx.y = n - 2): only G' in A_n contribute
+static __global__ void k_accum_lev(Plan p, int gp0, int np, double coef) {
+  const int no = p.n_occ;
+  const int ij = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ij >= no * no) return;
+  const int i = ij / no, j = ij % no;
+  {
+    const int n = blockIdx.y + 1;
+    const double2 *sx = p.sxl + (size_t)n * p.lev_stride, *yd = p.ydl + (size_t)n * p.lev_stride;
+    double ex = 0, ed = 0;
+    for (int gpl = 0; gpl < np; ++gpl) {
+      const int g = p.prim[gp0 + gpl];
+      if (p.aux_lev[g] < n + 1) continue;
+      const double vv = coef * p.v_aux64[g];
+      const double2 a = sx[((size_t)gpl * no + i) * no + j], b = sx[((size_t)gpl * no + j) * no + i];
+      const double2 c = yd[((size_t)gpl * no + i) * no + j], d = yd[((size_t)gpl * no + j) * no + i];
+      ex += vv * (a.x + b.x);
+      ed += -2.0 * vv * (c.x + d.x);
+    }
+    p.exl[(size_t)n * no * no + ij] += ex;
+    p.edl[(size_t)n * no * no + ij] += ed;
+  }
+}
+
 static __global__ void k_zero_acc(Plan p) {
   const int no2 = p.n_occ * p.n_occ;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < no2; k += gridDim.x * blockDim.x) {
     p.ex[k] = 0; p.exi[k] = 0; p.ed[k] = 0; p.edi[k] = 0;
+  }
+  if (p.n_lev > 1)
+    for (size_t k = blockIdx.x * blockDim.x + threadIdx.x; k < (size_t)p.n_lev * no2; k += gridDim.x * blockDim.x) {
+      p.exl[k] = 0; p.edl[k] = 0;
+    }
+}
+
+// fixed-order level sums: esum_lev[2n] = E_d over A_{n+1}, esum_lev[2n+1] = E_x; one block of 256
+static __global__ void k_finish_lev(Plan p) {
+  __shared__ double red[2][256];
+  const int no2 = p.n_occ * p.n_occ;
+  for (int n = 0; n < p.n_lev; ++n) {
+    const double *ed = n == 0 ? p.ed : p.edl + (size_t)n * no2;
+    const double *ex = n == 0 ? p.ex : p.exl + (size_t)n * no2;
+    double sd = 0, sx = 0;
+    for (int k = threadIdx.x; k < no2; k += blockDim.x) { sd += ed[k]; sx += ex[k]; }
+    red[0][threadIdx.x] = sd;
+    red[1][threadIdx.x] = sx;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) {
+        red[0][threadIdx.x] += red[0][threadIdx.x + w];
+        red[1][threadIdx.x] += red[1][threadIdx.x + w];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) { p.esum_lev[2 * n] = red[0][0]; p.esum_lev[2 * n + 1] = red[1][0]; }
+    __syncthreads();
   }
 }
 

@@ -93,6 +93,12 @@ struct ltmp2_ctx {
   int *d_keep_list = nullptr, *d_keep_count = nullptr;
   TcResources tc;
   void *tc_mem = nullptr;   // operand buffers of the tensor-core GEMM (owned via allocs)
+  double ecut_aux = 0.0;               // E_aux of A (Hartree)
+  std::vector<double> aux_g2;          // |G|^2 of A in internal order
+  // internal cutoff extrapolation: level cutoffs, |A_n| (G != 0), device buffers
+  std::vector<double> lev_ecut;
+  std::vector<int> lev_count;
+  bool lev_alloc = false, lev_done = false;
   ~ltmp2_ctx() {
     tc_release(tc);
     for (void *q : allocs) cudaFree(q);
@@ -301,7 +307,7 @@ int enqueue_energy(ltmp2_ctx *c, cudaStream_t stream, int n_tau, const double *t
   Plan &p = c->p;
   cudaError_t e = Path<T>::zero_acc(p, stream);
   if (e != cudaSuccess) return cuda_status(e);
-  *launches += 2;  // zero + final reduction
+  *launches += Path<T>::frame_launches(p);  // zero + final reduction(s)
   const double nfft = (double)p.n * p.n * p.n;
   for (int k = 0; k < n_tau; ++k) {
     e = Path<T>::green(p, tau[k], stream, tm);
@@ -339,6 +345,7 @@ int run_energy(ltmp2_ctx *c, int n_tau, const double *tau, const double *w, int 
   c->timer.stream = c->stream;
   int rc = enqueue_energy<T>(c, c->stream, n_tau, tau, w, gp_begin, gp_end, tm, &c->kernel_launches);
   if (rc) return rc;
+  c->lev_done = c->p.n_lev > 1;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (tm) c->timer.collect();
   if (e != cudaSuccess) return cuda_status(e);
@@ -648,13 +655,14 @@ int ltmp2_setup(const ltmp2_system *sys, ltmp2_ctx **out) {
   std::map<std::array<int, 3>, int> awhere;
   for (int k = 0; k < naux; ++k) awhere[amo[k]] = k;
   std::vector<int> aneg(naux), prim;
-  std::vector<double> v64(naux);
+  std::vector<double> v64(naux), ag2(naux);
   std::vector<float> v32(naux);
   for (int k = 0; k < naux; ++k) {
     auto it = awhere.find({-amo[k][0], -amo[k][1], -amo[k][2]});
     if (it == awhere.end()) return LTMP2_ERR_GRID;
     aneg[k] = it->second;
     const double g2 = g2_of(B, amo[k][0], amo[k][1], amo[k][2]);
+    ag2[k] = g2;
     v64[k] = (g2 > 0.0) ? 12.566370614359172953850573533118 / g2 : 0.0;
     v32[k] = (float)v64[k];
     const int first = amo[k][0] != 0 ? amo[k][0] : (amo[k][1] != 0 ? amo[k][1] : amo[k][2]);
@@ -670,6 +678,8 @@ int ltmp2_setup(const ltmp2_system *sys, ltmp2_ctx **out) {
   }
   Plan &p = c->p;
   std::memcpy(c->lattice, sys->lattice, sizeof(c->lattice));
+  c->ecut_aux = ecut_aux;
+  c->aux_g2 = ag2;
   p.n = n;
   p.n_occ = no;
   p.n_orb = norb;
@@ -1064,6 +1074,121 @@ int ltmp2_energy_batch(ltmp2_ctx *const *ctxs, int n, const int *n_tau, const do
   rc = ltmp2_batch_run(b, e_direct, e_exchange);
   ltmp2_batch_destroy(b);
   return rc;
+}
+
+// ---------------------------------------------------------------- internal cutoff extrapolation
+static_assert(kMaxLevels == LTMP2_MAX_LEVELS, "level capacity");
+int ltmp2_set_extrapolation(ltmp2_ctx *ctx, int n_c, double alpha) {
+  if (!ctx) return LTMP2_ERR_INVALID_ARG;
+  Plan &p = ctx->p;
+  ctx->lev_done = false;
+  if (n_c <= 1) {
+    p.n_lev = 0;
+    ctx->lev_ecut.clear();
+    ctx->lev_count.clear();
+    return LTMP2_OK;
+  }
+  if (n_c > kMaxLevels || !(alpha > 1.0) || !std::isfinite(alpha)) return LTMP2_ERR_INVALID_ARG;
+  const size_t cs = p.precision == LTMP2_FP64 ? 16 : 8;
+  if (2 * (size_t)p.n_aux * cs > 200 * 1024) return LTMP2_ERR_UNSUPPORTED;  // column kernel's shared memory
+  DeviceGuard g(ctx->device);
+  const int naux = p.n_aux, no = p.n_occ;
+  std::vector<double> ecut(n_c);
+  for (int n = 0; n < n_c; ++n) ecut[n] = ctx->ecut_aux / std::pow(alpha, (double)n);
+  // L(G) = number of nested spheres that contain G (G = 0, which never contributes, gets n_c)
+  std::vector<unsigned char> lev(naux);
+  std::vector<int> count(n_c, 0);
+  for (int k = 0; k < naux; ++k) {
+    int L = 1;
+    const double e = 0.5 * ctx->aux_g2[k];
+    if (ctx->aux_g2[k] == 0.0) L = n_c;
+    else
+      while (L < n_c && e <= ecut[L]) ++L;
+    lev[k] = (unsigned char)L;
+    if (ctx->aux_g2[k] != 0.0)
+      for (int n = 0; n < L; ++n) ++count[n];
+  }
+  std::vector<int> order(naux), start(n_c + 1, 0);
+  for (int k = 0; k < naux; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lev[a] < lev[b]; });
+  for (int n = 0; n <= n_c; ++n) {
+    int k = 0;
+    while (k < naux && lev[order[k]] <= n) ++k;
+    start[n] = k;
+  }
+  int rc;
+  if (!ctx->lev_alloc) {
+    p.lev_stride = (size_t)ctx->slab_capacity * no * no;
+    unsigned char *al = nullptr;
+    int *lo = nullptr, *ls = nullptr;
+    if ((rc = dalloc(ctx, &p.sxl, (size_t)kMaxLevels * p.lev_stride))) return rc;
+    if ((rc = dalloc(ctx, &p.ydl, (size_t)kMaxLevels * p.lev_stride))) return rc;
+    if ((rc = dalloc(ctx, &p.exl, (size_t)kMaxLevels * no * no))) return rc;
+    if ((rc = dalloc(ctx, &p.edl, (size_t)kMaxLevels * no * no))) return rc;
+    if ((rc = dalloc(ctx, &p.esum_lev, (size_t)2 * kMaxLevels))) return rc;
+    if ((rc = dalloc(ctx, &al, (size_t)naux))) return rc;
+    if ((rc = dalloc(ctx, &lo, (size_t)naux))) return rc;
+    if ((rc = dalloc(ctx, &ls, (size_t)kMaxLevels + 1))) return rc;
+    p.aux_lev = al;
+    p.lev_order = lo;
+    p.lev_start = ls;
+    ctx->lev_alloc = true;
+  }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpy((void *)p.aux_lev, lev.data(), naux, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy((void *)p.lev_order, order.data(), naux * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy((void *)p.lev_start, start.data(), (n_c + 1) * sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_status(e);
+  p.n_lev = n_c;
+  ctx->lev_ecut = ecut;
+  ctx->lev_count = count;
+  return LTMP2_OK;
+}
+
+int ltmp2_level_energies(const ltmp2_ctx *ctx, double *ecut_aux, int *n_aux, double *e_direct,
+                         double *e_exchange) {
+  if (!ctx || ctx->p.n_lev < 2) return LTMP2_ERR_INVALID_ARG;
+  const int nl = ctx->p.n_lev;
+  for (int n = 0; n < nl; ++n) {
+    if (ecut_aux) ecut_aux[n] = ctx->lev_ecut[n];
+    if (n_aux) n_aux[n] = ctx->lev_count[n];
+  }
+  if (!e_direct && !e_exchange) return LTMP2_OK;
+  if (!ctx->lev_done) return LTMP2_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  double es[2 * kMaxLevels];
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(es, ctx->p.esum_lev, 2 * nl * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int n = 0; n < nl; ++n) {
+    if (e_direct) e_direct[n] = es[2 * n];
+    if (e_exchange) e_exchange[n] = es[2 * n + 1];
+  }
+  return LTMP2_OK;
+}
+
+int ltmp2_extrapolate(int n, const double *ecut_aux, const double *energy, double *e_inf, double *slope,
+                      double *sigma) {
+  if (n < 2 || !ecut_aux || !energy || !e_inf) return LTMP2_ERR_INVALID_ARG;
+  double sx = 0, sy = 0, sxx = 0, sxy = 0;
+  std::vector<double> x(n);
+  for (int k = 0; k < n; ++k) {
+    if (!(ecut_aux[k] > 0.0) || !std::isfinite(ecut_aux[k]) || !std::isfinite(energy[k])) return LTMP2_ERR_INVALID_ARG;
+    x[k] = std::pow(ecut_aux[k], -1.5);
+    sx += x[k]; sy += energy[k]; sxx += x[k] * x[k]; sxy += x[k] * energy[k];
+  }
+  const double det = n * sxx - sx * sx;
+  if (!(std::fabs(det) > 0.0)) return LTMP2_ERR_INVALID_ARG;   // all cutoffs equal
+  const double b = (n * sxy - sx * sy) / det, a = (sy - b * sx) / n;
+  *e_inf = a;
+  if (slope) *slope = b;
+  if (sigma) {
+    double r2 = 0;
+    for (int k = 0; k < n; ++k) r2 += (energy[k] - a - b * x[k]) * (energy[k] - a - b * x[k]);
+    *sigma = n > 2 ? std::sqrt(r2 / (n - 2) * sxx / det) : 0.0;
+  }
+  return LTMP2_OK;
 }
 
 }  // extern "C"

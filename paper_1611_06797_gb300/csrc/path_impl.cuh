@@ -82,7 +82,9 @@ template <typename T> cudaError_t Path<T>::init_device() {
 #define LTMP2_SET_SMEM(NN)                                                                          \
   e = cudaFuncSetAttribute(k_planes<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
   if (e != cudaSuccess) return e;                                                                   \
-  e = cudaFuncSetAttribute(k_zcol<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);   \
+  e = cudaFuncSetAttribute(k_zcol<T, NN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
+  if (e != cudaSuccess) return e;                                                                   \
+  e = cudaFuncSetAttribute(k_zcol<T, NN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
   if (e != cudaSuccess) return e;                                                                   \
   e = cudaFuncSetAttribute(k_planes2<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
   if (e != cudaSuccess) return e;
@@ -190,10 +192,11 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     w_pw = (const cpx<T> *)p.st;
   }
-  const size_t smem_col = (size_t)p.n_aux * sizeof(cpx<T>);
+  const bool lev = p.n_lev > 1;
+  const size_t smem_col = (lev ? 2 : 1) * (size_t)p.n_aux * sizeof(cpx<T>);
   const int npairs = p.real_orb ? np * (no * (no + 1) / 2) : np * no * no;
   int col_threads = ((p.n_daux + 31) / 32) * 32;
-  if (col_threads > 512) col_threads = 512;
+  if (col_threads > 256) col_threads = 256;   // the column kernel's launch bound (FP64 N >= 36 uses ~255 registers)
   switch (n) {
 #define LTMP2_CASE(NN)                                                                                  \
   case NN: {                                                                                            \
@@ -209,8 +212,12 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
     }                                                                                                   \
     {                                                                                                   \
       ScopedStage s(tm, kStageColumn);                                                                  \
-      k_zcol<T, NN><<<npairs, col_threads, smem_col, st>>>(p, gp0, np, (const cpx<T> *)p.tbuf,          \
-                                                           (cpx<T> *)p.mdiag, p.sx);                    \
+      if (lev)                                                                                          \
+        k_zcol<T, NN, true><<<npairs, col_threads, smem_col, st>>>(p, gp0, np, (const cpx<T> *)p.tbuf,  \
+                                                                   (cpx<T> *)p.mdiag, p.sx);            \
+      else                                                                                              \
+        k_zcol<T, NN, false><<<npairs, col_threads, smem_col, st>>>(p, gp0, np, (const cpx<T> *)p.tbuf, \
+                                                                    (cpx<T> *)p.mdiag, p.sx);           \
       if ((e = cudaGetLastError()) != cudaSuccess) return e;                                            \
     }                                                                                                   \
   } break;
@@ -222,13 +229,18 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
   {
     ScopedStage s(tm, kStageDirect);
     int th = no < 128 ? ((no + 31) / 32) * 32 : 128;
-    k_direct<T><<<dim3(np, no), th, 0, st>>>(p, np, (const cpx<T> *)p.mdiag, p.yd);
+    if (lev) k_direct<T, true><<<dim3(np, no), th, 0, st>>>(p, np, (const cpx<T> *)p.mdiag, p.yd);
+    else k_direct<T, false><<<dim3(np, no), th, 0, st>>>(p, np, (const cpx<T> *)p.mdiag, p.yd);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
     ScopedStage s(tm, kStageAccum);
     k_accum<<<(no * no + 127) / 128, 128, 0, st>>>(p, gp0, np, coef, p.sx, p.yd);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (lev) {
+      k_accum_lev<<<dim3((no * no + 31) / 32, p.n_lev - 1), 32, 0, st>>>(p, gp0, np, coef);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }
@@ -250,6 +262,9 @@ template <typename T> cudaError_t Path<T>::zero_acc(const Plan &p, cudaStream_t 
 template <typename T> cudaError_t Path<T>::finish(const Plan &p, cudaStream_t st, StageTimer *tm) {
   ScopedStage s(tm, kStageAccum);
   k_finish<<<1, 256, 0, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || p.n_lev < 2) return e;
+  k_finish_lev<<<1, 256, 0, st>>>(p);
   return cudaGetLastError();
 }
 

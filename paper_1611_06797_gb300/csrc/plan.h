@@ -79,6 +79,17 @@ struct Plan {
   const int *keep_list = nullptr;            // [n_occ][n_occ] kept i for each j (first keep_count[j])
   const int *keep_count = nullptr;           // [n_occ]
   int plane_ib = 0;          // occupied planes per plane-kernel block, 0 = kernel default
+  // internal auxiliary-cutoff extrapolation (Sec. III D): nested spheres A_1 = A, ...,
+  // A_n = {G : |G|^2/2 <= E_aux / alpha^(n-1)}; every G- and G'-sum is also kept per level.
+  // n_lev < 2: off.
+  int n_lev = 0;
+  const unsigned char *aux_lev = nullptr;  // [n_aux] L(G): G belongs to A_1 .. A_L(G)
+  const int *lev_order = nullptr;          // [n_aux] aux positions grouped by L (L = 1 first)
+  const int *lev_start = nullptr;          // [n_lev + 1] group boundaries in lev_order
+  size_t lev_stride = 0;                   // elements per level of sxl / ydl
+  double2 *sxl = nullptr, *ydl = nullptr;  // [n_lev][slab cap][n_occ][n_occ] pair sums over A_n
+  double *exl = nullptr, *edl = nullptr;   // [n_lev][n_occ][n_occ] level pair energies (n >= 2)
+  double *esum_lev = nullptr;              // [2 n_lev]: E_d[n], E_x[n]
   int slots_per_prim() const { return real_orb ? 1 : 2; }
 };
 
@@ -88,6 +99,8 @@ struct StageTimer {
   virtual void end(int stage) = 0;
   virtual ~StageTimer() {}
 };
+
+constexpr int kMaxLevels = 16;   // nested cutoffs of the internal extrapolation
 
 enum Stage {
   kStageGreen = 0, kStageWGemm = 1, kStageGatherZ = 2, kStagePlane = 3,
@@ -99,7 +112,11 @@ template <typename T> struct Path {
   // kernel launches per Green's function build and per slab (the tcgen05 path of the
   // precision form adds one operand-packing launch to each)
   static int green_launches(const Plan &p) { return p.tc ? 3 : 2; }
-  static int slab_launches(const Plan &p) { return (p.tc ? 8 : 7) + (p.real_basis ? 1 : 0); }
+  static int slab_launches(const Plan &p) {
+    return (p.tc ? 8 : 7) + (p.real_basis ? 1 : 0) + (p.n_lev > 1 ? 1 : 0);
+  }
+  // launches of zero_acc + finish
+  static int frame_launches(const Plan &p) { return p.n_lev > 1 ? 3 : 2; }
   static cudaError_t init_device();
   // setup: occupied orbitals -> u (real space) and cgrid
   static cudaError_t setup_occupied(const Plan &p, const void *c_occ_dev, cudaStream_t st);

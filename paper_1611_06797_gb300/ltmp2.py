@@ -71,6 +71,9 @@ def load_library():
         "ltmp2_reset_stage_times": (ctypes.c_int, [vp]),
         "ltmp2_destroy": (None, [vp]),
         "ltmp2_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "ltmp2_set_extrapolation": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double]),
+        "ltmp2_level_energies": (ctypes.c_int, [vp, dp, P(ctypes.c_int), dp, dp]),
+        "ltmp2_extrapolate": (ctypes.c_int, [ctypes.c_int, dp, dp, dp, dp, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -99,6 +102,7 @@ class Context:
     def __init__(self, handle: int, n_occ: int):
         self.handle = ctypes.c_void_p(handle)
         self.n_occ = n_occ
+        self.n_levels = 0
         self._stream = None
 
     def __del__(self):
@@ -279,6 +283,37 @@ def ltmp2_energy_noalloc(lattice, grid, miller, coeff, eps, n_occ: int, tau, w, 
     _check(f(ctypes.byref(s), len(tau), _dp(tau), _dp(w), _dp(ed), _dp(ex), _dp(ep) if pairs else None,
              ctypes.c_void_p(int(handle) if handle else 0)), "ltmp2_energy_noalloc")
     return float(ed[0]), float(ex[0]), ep
+
+
+# ---------------------------------------------------------------- internal cutoff extrapolation
+def ltmp2_set_extrapolation(ctx: Context, n_c: int = 8, alpha: float = 1.05) -> None:
+    """Evaluate later energies also on n_c nested auxiliary spheres (n_c <= 1: off)."""
+    _check(load_library().ltmp2_set_extrapolation(ctx.handle, int(n_c), float(alpha)),
+           "ltmp2_set_extrapolation")
+    ctx.n_levels = int(n_c) if n_c > 1 else 0
+
+
+def ltmp2_level_energies(ctx: Context) -> dict:
+    """Cutoffs, |A_n| and E_direct / E_exchange per level of the last energy call."""
+    nl = getattr(ctx, "n_levels", 0)
+    if nl < 2:
+        raise Ltmp2Error(-1, "ltmp2_level_energies: levels are off")
+    ecut, ed, ex = np.zeros(nl), np.zeros(nl), np.zeros(nl)
+    cnt = (ctypes.c_int * nl)()
+    _check(load_library().ltmp2_level_energies(ctx.handle, _dp(ecut), cnt, _dp(ed), _dp(ex)),
+           "ltmp2_level_energies")
+    return {"ecut_aux": ecut, "n_aux": np.array(cnt[:]), "E_d": ed, "E_x": ex}
+
+
+def ltmp2_extrapolate(ecut_aux, energy) -> Tuple[float, float, float]:
+    """(E_inf, slope, sigma) of the fit E = E_inf + slope * E_aux^(-3/2) (Eq. CutDecay)."""
+    e = np.ascontiguousarray(np.asarray(ecut_aux, dtype=np.float64))
+    y = np.ascontiguousarray(np.asarray(energy, dtype=np.float64))
+    if e.shape != y.shape:
+        raise ValueError("ecut_aux and energy differ in length")
+    a, b, sg = np.zeros(1), np.zeros(1), np.zeros(1)
+    _check(load_library().ltmp2_extrapolate(len(e), _dp(e), _dp(y), _dp(a), _dp(b), _dp(sg)), "ltmp2_extrapolate")
+    return float(a[0]), float(b[0]), float(sg[0])
 
 
 # ---------------------------------------------------------------- batching form

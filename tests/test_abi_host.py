@@ -117,3 +117,17 @@ def test_setup_without_device_reports_cuda():
     with pytest.raises(L.Ltmp2Error) as e:
         _setup(solid("tiny"))
     assert e.value.name == "CUDA"
+
+
+def test_extrapolation_fit_is_the_oracle_fit():
+    """ltmp2_extrapolate is host arithmetic: the same straight-line fit in
+    E_aux^(-3/2) (Eq. CutDecay) as the oracle's, on the same points."""
+    from oracle import cutoff_extrapolation, cutoff_levels
+    rng = np.random.default_rng(7)
+    ecut = cutoff_levels(8.0, 8, 1.05)
+    y = -0.9 + 3.0 * ecut ** -1.5 + 1e-5 * rng.standard_normal(8)
+    a, b, sg = L.ltmp2_extrapolate(ecut, y)
+    ra, rb, rs = cutoff_extrapolation(ecut, y)
+    assert abs(a - ra) < 1e-12 and abs(b - rb) < 1e-9 * abs(rb) and abs(sg - rs) < 1e-9 * rs
+    with pytest.raises(L.Ltmp2Error):
+        L.ltmp2_extrapolate([1.0, 1.0], [0.0, 1.0])
