@@ -175,9 +175,17 @@ int ltmp2_autotune(ltmp2_ctx *ctx, int *slab, int *gemm_variant);
 
 /* Settings in effect for ctx: values[0] slab size, [1] tensor-core GEMM layout (-1 in
  * FP64 or with LTMP2_FLAG_SIMT_GEMM), [2] plane FFT kernel (0 full-plane passes,
- * 1 compacted passes), [3] occupied planes per plane-kernel block (0 = default).  The
- * autotuner also chooses [2] and [3], timing the plane kernel alone.                */
+ * 1 compacted passes, 2 product in registers with a compact intermediate), [3] occupied
+ * planes per plane-kernel block (0 = default).  The autotuner also chooses [2] and [3],
+ * timing the plane kernel alone.                                                      */
 int ltmp2_get_tuning(const ltmp2_ctx *ctx, int *values);
+
+/* Apply settings by hand, same layout as ltmp2_get_tuning; a negative entry keeps the
+ * current value.  Every choice gives the same energies up to rounding.  INVALID_ARG for
+ * a slab outside 1..capacity, a GEMM layout without the tensor-core path (or other than
+ * 5 for real orbitals), or a plane-kernel shape over 1024 threads or 200 KB of shared
+ * memory.                                                                             */
+int ltmp2_set_tuning(ltmp2_ctx *ctx, const int *values);
 
 typedef struct ltmp2_batch ltmp2_batch; /* opaque; a captured, instantiated graph */
 

@@ -486,6 +486,111 @@ __global__ void k_planes2(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> 
   }
 }
 
+// Same result as k_planes, with the product formed in registers.  Per block of ib
+// occupied i:
+//  x pass : thread (i, y) loads row y of phi_i (vector loads from global memory, L2
+//           resident) and of w_j^{G'} (shared), multiplies conj(phi_i) w in registers,
+//           transforms, and keeps only the m1 of the aux range: a compact
+//           [ib][N][nxa] intermediate (nxa is odd, so the row pitch spreads the banks);
+//  y pass : thread (i, m1) transforms its column and writes the aux-disk entries,
+//           compactly in disk order;
+//  copy   : coalesced copy of the compact plane to tbuf[(col, i)][z][d_aux].
+template <typename T, int N> __device__ __forceinline__ void load_row(const cpx<T> *__restrict__ src, cpx<T> (&a)[N]) {
+  if constexpr (sizeof(cpx<T>) == 8 && N % 2 == 0) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      const float4 v = __ldg(s4 + k);
+      a[2 * k] = {(T)v.x, (T)v.y};
+      a[2 * k + 1] = {(T)v.z, (T)v.w};
+    }
+  } else if constexpr (sizeof(cpx<T>) == 16) {
+    const double2 *s2 = reinterpret_cast<const double2 *>(src);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const double2 v = __ldg(s2 + k);
+      a[k] = {(T)v.x, (T)v.y};
+    }
+  } else {
+    const float2 *s2 = reinterpret_cast<const float2 *>(src);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const float2 v = __ldg(s2 + k);
+      a[k] = {(T)v.x, (T)v.y};
+    }
+  }
+}
+
+template <typename T, int N>
+__global__ void k_planes3(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> *__restrict__ tbuf) {
+  constexpr int P = N + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T> *xp = reinterpret_cast<cpx<T> *>(smem_raw);
+  const int nxa = p.mxhi_aux - p.mxlo_aux + 1;   // odd: the aux sphere is symmetric
+  const int nd = p.n_daux;
+  cpx<T> *wk = xp + N * P;                    // [ib][N][nxa]
+  cpx<T> *ob = wk + (size_t)ib * N * nxa;     // [ib][nd]
+  int *xs = reinterpret_cast<int *>(ob + (size_t)ib * nd);   // per m1: first disk column, m2 lo, m2 hi
+  const int z = blockIdx.x, col = blockIdx.y;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int no = p.n_occ;
+  for (int t = tid; t < nxa; t += nth) { xs[3 * t] = 0; xs[3 * t + 1] = 1; xs[3 * t + 2] = 0; }
+  __syncthreads();
+  for (int d = tid; d < nd; d += nth) {
+    const int4 c = p.daux[d];
+    const int xa = c.x - p.mxlo_aux;
+    if (d == 0 || p.daux[d - 1].x != c.x) { xs[3 * xa] = d; xs[3 * xa + 1] = c.y; }
+    if (d == nd - 1 || p.daux[d + 1].x != c.x) xs[3 * xa + 2] = c.y;
+  }
+  plane_inverse<T, N>(p, z1 + ((size_t)col * N + z) * p.n_dorb, xp);   // ends with a barrier
+  const cpx<T> *u = (const cpx<T> *)p.u;
+  const int mlo = p.mxlo_aux, mhi = p.mxhi_aux;
+  const int jcol = col % no;
+  const int ni = p.keep_count ? p.keep_count[jcol] : no;
+  const int *ilist = p.keep_count ? p.keep_list + (size_t)jcol * no : nullptr;
+  for (int i0 = 0; i0 < ni; i0 += ib) {
+    const int nb = min(ib, ni - i0);
+    for (int t = tid; t < nb * N; t += nth) {
+      const int il = t / N, y = t - il * N;
+      const int iocc = ilist ? ilist[i0 + il] : i0 + il;
+      cpx<T> a[N];
+      load_row<T, N>(u + (((size_t)iocc * N + z) * N + y) * N, a);
+      const cpx<T> *wr = xp + y * P;
+#pragma unroll
+      for (int k = 0; k < N; ++k) a[k] = cmul(cconj(a[k]), wr[k]);
+      LineFFT<T, N, -1>::run(a);
+      cpx<T> *row = wk + (size_t)t * nxa - mlo;   // row[m] for m in [mlo, mhi]
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int m = freq_of<N>(k);
+        if (m >= mlo && m <= mhi) row[m] = a[k];
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < nb * nxa; t += nth) {
+      const int il = t / nxa, xa = t - il * nxa;
+      const cpx<T> *src = wk + (size_t)il * N * nxa + xa;
+      cpx<T> b[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) b[k] = src[k * nxa];
+      LineFFT<T, N, -1>::run(b);
+      const int d0 = xs[3 * xa], lo = xs[3 * xa + 1], hi = xs[3 * xa + 2];
+      cpx<T> *o = ob + (size_t)il * nd + d0 - lo;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int m = freq_of<N>(k);
+        if (m >= lo && m <= hi) o[m] = b[k];
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < nb * nd; e += nth) {
+      const int il = e / nd, d = e - il * nd;
+      const size_t item = (size_t)col * no + (ilist ? ilist[i0 + il] : i0 + il);
+      tbuf[(item * N + z) * nd + d] = ob[(size_t)il * nd + d];
+    }
+  }
+}
+
 // setup: real-space occupied orbitals u[j][z][y][x] from z1 (cols = occupied orbitals)
 template <typename T, int N>
 __global__ void k_planes_store(Plan p, const cpx<T> *__restrict__ z1, cpx<T> *__restrict__ out) {

@@ -407,7 +407,7 @@ struct TuneVal {
 };
 std::map<TuneKey, TuneVal> g_tune_cache;
 
-int apply_tuning(ltmp2_ctx *c, int slab, int variant, int plane_kernel = 0, int plane_ib = 0) {
+int apply_tuning(ltmp2_ctx *c, int slab, int variant, int plane_kernel = 2, int plane_ib = 0) {
   if (slab < 1 || slab > c->slab_capacity) return LTMP2_ERR_INVALID_ARG;
   c->p.max_prim = slab;
   c->p.plane_kernel = plane_kernel;
@@ -470,7 +470,7 @@ template <typename T> int tune_ctx(ltmp2_ctx *c, int *slab_out, int *var_out) {
   if (!rc) {
     const int ncols = best_slab * p.slots_per_prim() * p.n_occ;
     double best_plane = 1e300;
-    for (int pk = 0; pk < 2 && !rc; ++pk)
+    for (int pk = 0; pk < 3 && !rc; ++pk)
       for (int ib : {2, 4, 8, 16}) {
         if (ib > p.n_occ) continue;
         if (Path<T>::plane_pass(p, ncols, pk, ib, c->stream) != cudaSuccess) {  // infeasible shape
@@ -969,6 +969,24 @@ int ltmp2_get_tuning(const ltmp2_ctx *ctx, int *values) {
   values[2] = ctx->p.plane_kernel;
   values[3] = ctx->p.plane_ib;
   return LTMP2_OK;
+}
+
+int ltmp2_set_tuning(ltmp2_ctx *ctx, const int *values) {
+  if (!ctx || !values) return LTMP2_ERR_INVALID_ARG;
+  Plan &p = ctx->p;
+  const int slab = values[0] < 0 ? p.max_prim : values[0];
+  int variant = values[1];
+  const int pk = values[2] < 0 ? p.plane_kernel : values[2];
+  const int ib = values[3] < 0 ? p.plane_ib : values[3];
+  if (slab < 1 || slab > ctx->slab_capacity) return LTMP2_ERR_INVALID_ARG;
+  if (variant >= 0) {
+    if (!p.tc || variant > 5 || (ctx->tc.real && variant != 5)) return LTMP2_ERR_INVALID_ARG;
+  }
+  const bool ok = p.precision == LTMP2_FP64 ? Path<double>::plane_feasible(p, pk, ib)
+                                             : Path<float>::plane_feasible(p, pk, ib);
+  if (!ok) return LTMP2_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  return apply_tuning(ctx, slab, variant, pk, ib);
 }
 
 int ltmp2_batch_create(ltmp2_ctx *const *ctxs, int n, const int *n_tau, const double *const *tau,

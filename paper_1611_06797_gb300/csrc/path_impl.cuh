@@ -9,15 +9,23 @@ namespace ltmp2 {
 
 #define LTMP2_FOR_EACH_N(X) X(8) X(10) X(12) X(16) X(18) X(20) X(24) X(25) X(27) X(30) X(32) X(36) X(40)
 
-// Plane kernels: 0 = k_planes (full-plane passes), 1 = k_planes2 (compacted passes).
+// Plane kernels: 0 = k_planes (full-plane passes), 1 = k_planes2 (compacted passes),
+// 2 = k_planes3 (product in registers, compact intermediate).
 // ib = occupied planes per block; 0 picks the default of each kernel.
 template <typename T> static int plane_ib_default(const Plan &p, int kernel) {
   const int n = p.n;
   const size_t plane = (size_t)n * (n + 1) * sizeof(cpx<T>);
+  const int nxa = p.mxhi_aux - p.mxlo_aux + 1;
   int ib;
   if (kernel == 0) {
     ib = (int)((96 * 1024) / plane) - 1;   // about 96 KB of shared memory
     if (ib > 8) ib = 8;
+  } else if (kernel == 2) {
+    // four planes per block: small blocks, many resident per SM (best on the 24^3 workload
+    // in both precisions among 2..16)
+    const size_t per = ((size_t)n * nxa + p.n_daux) * sizeof(cpx<T>);
+    ib = (int)((100 * 1024 - plane - 3 * sizeof(int) * nxa - 64) / per);
+    if (ib > 4) ib = 4;
   } else {
     const size_t per = plane + (size_t)p.n_daux * sizeof(cpx<T>);
     ib = (int)((100 * 1024 - plane - 3 * sizeof(int) * (n + 1) - 64) / per);
@@ -31,8 +39,11 @@ template <typename T> static int plane_ib_default(const Plan &p, int kernel) {
 template <typename T> static size_t plane_smem(const Plan &p, int kernel, int ib) {
   const int n = p.n;
   const size_t plane = (size_t)n * (n + 1) * sizeof(cpx<T>);
+  const int nxa = p.mxhi_aux - p.mxlo_aux + 1;
   if (kernel == 0) return plane * (1 + ib);
-  return plane * (1 + ib) + (size_t)ib * p.n_daux * sizeof(cpx<T>) + 3 * sizeof(int) * (p.mxhi_aux - p.mxlo_aux + 1);
+  if (kernel == 2)
+    return plane + (size_t)ib * ((size_t)n * nxa + p.n_daux) * sizeof(cpx<T>) + 3 * sizeof(int) * nxa;
+  return plane * (1 + ib) + (size_t)ib * p.n_daux * sizeof(cpx<T>) + 3 * sizeof(int) * nxa;
 }
 
 // launch the plane kernel for the ncols columns of the current slab (z1 -> tbuf)
@@ -47,8 +58,10 @@ template <typename T> static cudaError_t launch_planes(const Plan &p, int ncols,
   case NN:                                                                                                 \
     if (kernel == 0)                                                                                       \
       k_planes<T, NN><<<dim3(NN, ncols), threads, smem, st>>>(p, ib, (const cpx<T> *)p.z1, (cpx<T> *)p.tbuf);  \
-    else                                                                                                   \
+    else if (kernel == 1)                                                                                  \
       k_planes2<T, NN><<<dim3(NN, ncols), threads, smem, st>>>(p, ib, (const cpx<T> *)p.z1, (cpx<T> *)p.tbuf); \
+    else                                                                                                   \
+      k_planes3<T, NN><<<dim3(NN, ncols), threads, smem, st>>>(p, ib, (const cpx<T> *)p.z1, (cpx<T> *)p.tbuf); \
     break;
     LTMP2_FOR_EACH_N(LTMP2_CASE)
 #undef LTMP2_CASE
@@ -56,6 +69,13 @@ template <typename T> static cudaError_t launch_planes(const Plan &p, int ncols,
       return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+template <typename T> bool Path<T>::plane_feasible(const Plan &p, int kernel, int ib) {
+  if (kernel < 0 || kernel > 2 || ib < 0) return false;
+  if (ib == 0) ib = plane_ib_default<T>(p, kernel);
+  const int threads = ib * p.n;
+  return threads <= 1024 && plane_smem<T>(p, kernel, ib) <= 200 * 1024;
 }
 
 template <typename T>
@@ -87,6 +107,8 @@ template <typename T> cudaError_t Path<T>::init_device() {
   e = cudaFuncSetAttribute(k_zcol<T, NN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
   if (e != cudaSuccess) return e;                                                                   \
   e = cudaFuncSetAttribute(k_planes2<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
+  if (e != cudaSuccess) return e;                                                                   \
+  e = cudaFuncSetAttribute(k_planes3<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
   if (e != cudaSuccess) return e;
   LTMP2_FOR_EACH_N(LTMP2_SET_SMEM)
 #undef LTMP2_SET_SMEM

@@ -73,7 +73,7 @@ struct Plan {
   double *esum = nullptr;    // [4]: E_d, E_x, imag parts
   int max_prim = 0;          // primary G' per slab (capacity)
   TcResources *tc = nullptr; // precision form: tcgen05 GEMM resources (host pointer), or null
-  int plane_kernel = 0;      // 0: k_planes, 1: k_planes2 (set by the autotuner)
+  int plane_kernel = 2;      // 0: k_planes, 1: k_planes2, 2: k_planes3 (the autotuner may change it)
   // screened exchange pairs (learned form); all null = every pair contracted
   const unsigned char *pair_keep = nullptr;  // [n_occ][n_occ] 1 = contract, symmetric, diagonal kept
   const int *keep_list = nullptr;            // [n_occ][n_occ] kept i for each j (first keep_count[j])
@@ -125,7 +125,9 @@ template <typename T> struct Path {
   // one slab of primary G' [gp0, gp0 + np): everything up to the pair sums, then accumulate
   static cudaError_t slab(const Plan &p, int gp0, int np, double coef, cudaStream_t st,
                           StageTimer *tm);
-  // the plane kernel alone (for the autotuner): kernel 0/1, ib (0 = default)
+  // plane kernel `kernel` with `ib` occupied planes per block fits the launch limits
+  static bool plane_feasible(const Plan &p, int kernel, int ib);
+  // the plane kernel alone (for the autotuner): kernel 0/1/2, ib (0 = default)
   static cudaError_t plane_pass(const Plan &p, int ncols, int kernel, int ib, cudaStream_t st);
   // per-orbital density moments [n_occ][6] and pair density overlaps [n_occ][n_occ] (device)
   static cudaError_t descriptors(const Plan &p, double *moments, double *overlap, cudaStream_t st);

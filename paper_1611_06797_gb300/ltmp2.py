@@ -350,6 +350,17 @@ def ltmp2_get_tuning(ctx: Context) -> dict:
     return {"slab": v[0], "gemm_variant": v[1], "plane_kernel": v[2], "plane_ib": v[3]}
 
 
+def ltmp2_set_tuning(ctx: Context, slab: int = -1, gemm_variant: int = -1, plane_kernel: int = -1,
+                     plane_ib: int = -1) -> None:
+    """Apply tuning settings by hand (-1 keeps the current value)."""
+    lib = load_library()
+    f = lib.ltmp2_set_tuning
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
+    v = (ctypes.c_int * 4)(int(slab), int(gemm_variant), int(plane_kernel), int(plane_ib))
+    _check(f(ctx.handle, v), "ltmp2_set_tuning")
+
+
 def _batch_args(ctxs, taus, ws):
     n = len(ctxs)
     handles = (ctypes.c_void_p * n)(*[c.handle.value for c in ctxs])

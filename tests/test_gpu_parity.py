@@ -142,3 +142,34 @@ def test_cfg2_full_size_sampled_pairs():
     d32, x32, _, _ = _gpu(s, tau, w, L.FP32, real=True)
     tol = MEV_PER_ATOM * s.n_atoms
     assert abs(d32 - ed) < tol and abs(x32 - ex) < tol and abs(d32 + x32 - ed - ex) < tol
+
+
+@pytest.mark.parametrize("name,real", [("cfg1", True), ("tiny2", False)])
+def test_plane_kernels_and_block_shapes_agree(name, real):
+    """The three plane-FFT kernels (full-plane passes, compacted passes, product in
+    registers) with several occupied-plane blocks, including a ragged last block, give
+    the oracle's energies in FP64 and the FP64 energies within the bound in FP32."""
+    s = solid(name)
+    tau, w = _quad(s, 4)
+    ref = _oracle(s, tau, w)
+    base = {}
+    for precision in (L.FP64, L.FP32):
+        ctx = L.setup_from_solid(s, precision=precision, real=real)
+        for pk in (0, 1, 2):
+            for ib in (0, 1, 3):
+                L.ltmp2_set_tuning(ctx, plane_kernel=pk, plane_ib=ib)
+                assert L.ltmp2_get_tuning(ctx)["plane_kernel"] == pk
+                ed, ex, ep = L.ltmp2_energy(ctx, tau, w)
+                if precision == L.FP64:
+                    assert abs(ed - ref["E_d"]) < TOL_FP64 and abs(ex - ref["E_x"]) < TOL_FP64
+                    base.setdefault("ed", ed)
+                    base.setdefault("ex", ex)
+                    assert abs(ed - base["ed"]) < 1e-12 * abs(ed) and abs(ex - base["ex"]) < 1e-12 * abs(ex)
+                else:
+                    bound = MEV_PER_ATOM * s.n_atoms
+                    assert abs(ed - base["ed"]) < bound and abs(ex - base["ex"]) < bound
+        with pytest.raises(L.Ltmp2Error):
+            L.ltmp2_set_tuning(ctx, plane_kernel=3)
+        with pytest.raises(L.Ltmp2Error):
+            L.ltmp2_set_tuning(ctx, plane_kernel=0, plane_ib=2000)
+        L.ltmp2_destroy(ctx)
