@@ -488,39 +488,14 @@ __global__ void k_planes2(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> 
 
 // Same result as k_planes, with the product formed in registers.  Per block of ib
 // occupied i:
-//  x pass : thread (i, y) loads row y of phi_i (vector loads from global memory, L2
-//           resident) and of w_j^{G'} (shared), multiplies conj(phi_i) w in registers,
+//  x pass : thread (i, y) loads row y of phi_i (from the plane-transposed copy, coalesced
+//           across the warp, L2 resident) and of w_j^{G'} (shared), multiplies conj(phi_i) w
+//           in registers,
 //           transforms, and keeps only the m1 of the aux range: a compact
 //           [ib][N][nxa] intermediate (nxa is odd, so the row pitch spreads the banks);
 //  y pass : thread (i, m1) transforms its column and writes the aux-disk entries,
 //           compactly in disk order;
 //  copy   : coalesced copy of the compact plane to tbuf[(col, i)][z][d_aux].
-template <typename T, int N> __device__ __forceinline__ void load_row(const cpx<T> *__restrict__ src, cpx<T> (&a)[N]) {
-  if constexpr (sizeof(cpx<T>) == 8 && N % 2 == 0) {
-    const float4 *s4 = reinterpret_cast<const float4 *>(src);
-#pragma unroll
-    for (int k = 0; k < N / 2; ++k) {
-      const float4 v = __ldg(s4 + k);
-      a[2 * k] = {(T)v.x, (T)v.y};
-      a[2 * k + 1] = {(T)v.z, (T)v.w};
-    }
-  } else if constexpr (sizeof(cpx<T>) == 16) {
-    const double2 *s2 = reinterpret_cast<const double2 *>(src);
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const double2 v = __ldg(s2 + k);
-      a[k] = {(T)v.x, (T)v.y};
-    }
-  } else {
-    const float2 *s2 = reinterpret_cast<const float2 *>(src);
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const float2 v = __ldg(s2 + k);
-      a[k] = {(T)v.x, (T)v.y};
-    }
-  }
-}
-
 template <typename T, int N>
 __global__ void k_planes3(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> *__restrict__ tbuf) {
   constexpr int P = N + 1;
@@ -543,7 +518,7 @@ __global__ void k_planes3(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> 
     if (d == nd - 1 || p.daux[d + 1].x != c.x) xs[3 * xa + 2] = c.y;
   }
   plane_inverse<T, N>(p, z1 + ((size_t)col * N + z) * p.n_dorb, xp);   // ends with a barrier
-  const cpx<T> *u = (const cpx<T> *)p.u;
+  const cpx<T> *ut = (const cpx<T> *)p.ut;
   const int mlo = p.mxlo_aux, mhi = p.mxhi_aux;
   const int jcol = col % no;
   const int ni = p.keep_count ? p.keep_count[jcol] : no;
@@ -554,10 +529,12 @@ __global__ void k_planes3(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> 
       const int il = t / N, y = t - il * N;
       const int iocc = ilist ? ilist[i0 + il] : i0 + il;
       cpx<T> a[N];
-      load_row<T, N>(u + (((size_t)iocc * N + z) * N + y) * N, a);
+      // row y of phi_i from the transposed plane: element x at x N + y, so the threads of
+      // a warp (consecutive y) read consecutive addresses
+      const cpx<T> *ur = ut + ((size_t)iocc * N + z) * N * N + y;
       const cpx<T> *wr = xp + y * P;
 #pragma unroll
-      for (int k = 0; k < N; ++k) a[k] = cmul(cconj(a[k]), wr[k]);
+      for (int k = 0; k < N; ++k) a[k] = cmul(cconj(ur[k * N]), wr[k]);
       LineFFT<T, N, -1>::run(a);
       cpx<T> *row = wk + (size_t)t * nxa - mlo;   // row[m] for m in [mlo, mhi]
 #pragma unroll
@@ -592,8 +569,10 @@ __global__ void k_planes3(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> 
 }
 
 // setup: real-space occupied orbitals u[j][z][y][x] from z1 (cols = occupied orbitals)
+// (and the plane-transposed copy outt[j][z][x][y] that the plane kernel reads row-wise)
 template <typename T, int N>
-__global__ void k_planes_store(Plan p, const cpx<T> *__restrict__ z1, cpx<T> *__restrict__ out) {
+__global__ void k_planes_store(Plan p, const cpx<T> *__restrict__ z1, cpx<T> *__restrict__ out,
+                               cpx<T> *__restrict__ outt) {
   constexpr int P = N + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T> *xp = reinterpret_cast<cpx<T> *>(smem_raw);
@@ -602,6 +581,7 @@ __global__ void k_planes_store(Plan p, const cpx<T> *__restrict__ z1, cpx<T> *__
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int y = e / N, x = e % N;
     out[((size_t)col * N + z) * N * N + e] = xp[y * P + x];
+    outt[((size_t)col * N + z) * N * N + e] = xp[x * P + y];   // e = x' N + y' with x' = y, y' = x
   }
 }
 

@@ -259,6 +259,7 @@ template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys,
   if ((rc = upload_coeff<T>(c, sys->coeff, p.n_pw, 0, p.n_occ, order, &cocc))) return rc;
   if ((rc = dalloc_bytes(c, &p.cgrid, cs * n3 * p.n_occ))) return rc;
   if ((rc = dalloc_bytes(c, &p.u, cs * n3 * p.n_occ))) return rc;
+  if ((rc = dalloc_bytes(c, &p.ut, cs * n3 * p.n_occ))) return rc;
   if ((rc = dalloc_bytes(c, &p.dscale, sizeof(T) * p.n_orb))) return rc;
   if ((rc = dalloc_bytes(c, &p.pt, (p.real_basis ? sizeof(T) : cs) * (size_t)p.n_pw * p.n_pw))) return rc;
   // slab capacity from the free memory

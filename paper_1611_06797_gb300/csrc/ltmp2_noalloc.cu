@@ -151,6 +151,7 @@ int run_noalloc(const ltmp2_system *sys, Plan &p, Arena &ar, const std::vector<i
   p.cv = p.real_basis ? ar.take(hr.size() * sizeof(T)) : ar.take(hv.size() * cs);
   p.cgrid = ar.take(cs * n3 * p.n_occ);
   p.u = ar.take(cs * n3 * p.n_occ);
+  p.ut = ar.take(cs * n3 * p.n_occ);
   p.dscale = ar.take(sizeof(T) * p.n_orb);
   p.pt = ar.take((p.real_basis ? sizeof(T) : cs) * (size_t)p.n_pw * p.n_pw);
   const size_t no2 = (size_t)p.n_occ * p.n_occ;
@@ -159,7 +160,7 @@ int run_noalloc(const ltmp2_system *sys, Plan &p, Arena &ar, const std::vector<i
   p.exi = (double *)ar.take(no2 * sizeof(double));
   p.edi = (double *)ar.take(no2 * sizeof(double));
   p.esum = (double *)ar.take(4 * sizeof(double));
-  if (!cocc || !p.cv || !p.cgrid || !p.u || !p.dscale || !p.pt || !p.ex || !p.ed || !p.exi || !p.edi || !p.esum)
+  if (!cocc || !p.cv || !p.cgrid || !p.u || !p.ut || !p.dscale || !p.pt || !p.ex || !p.ed || !p.exi || !p.edi || !p.esum)
     return LTMP2_ERR_UNSUPPORTED;
   // slab of primary G' sized to what is left of the array
   const int spp = p.slots_per_prim();

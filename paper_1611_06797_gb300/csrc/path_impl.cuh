@@ -133,7 +133,7 @@ cudaError_t Path<T>::setup_occupied(const Plan &p, const void *c_occ_dev, cudaSt
 #define LTMP2_CASE(NN)                                                                            \
   case NN:                                                                                        \
     k_w_zinv<T, NN><<<dim3((p.n_dorb + 127) / 128, p.n_occ), 128, 0, st>>>(p, p.n_pw, c, z1);     \
-    k_planes_store<T, NN><<<dim3(NN, p.n_occ), 128, smem, st>>>(p, z1, (cpx<T> *)p.u);            \
+    k_planes_store<T, NN><<<dim3(NN, p.n_occ), 128, smem, st>>>(p, z1, (cpx<T> *)p.u, (cpx<T> *)p.ut); \
     break;
     LTMP2_FOR_EACH_N(LTMP2_CASE)
 #undef LTMP2_CASE

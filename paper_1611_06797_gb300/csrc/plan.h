@@ -60,6 +60,7 @@ struct Plan {
   void *cv = nullptr;        // [n_v][n_pw] virtual coefficients, internal order (T if real_basis)
   void *cgrid = nullptr;     // [n_occ][n^3] occupied coefficients scattered on the grid
   void *u = nullptr;         // [n_occ][n^3] occupied orbitals in real space, [z][y][x]
+  void *ut = nullptr;        // [n_occ][n^3] the same, each z plane transposed: [z][x][y]
   void *dscale = nullptr;    // [n_orb] T: virtual e^{-(e_a-mu)tau}, occupied e^{(e_j-mu)tau}
   void *pt = nullptr;        // [n_pw][n_pw] transposed Green's function P^T (real P if real_basis)
   void *st = nullptr;        // [max_cols][n_pw] gathered, scaled e^{-iG'r}|j> (S^T)
