@@ -44,8 +44,9 @@ __global__ void k_dscale(int n_orb, int n_occ, const double *__restrict__ eps, d
 // C[m][n] = sum_k opA(m,k) * B[k][n] * s_k,  opA(m,k) = A[m*lda+k] (A_KM) or A[k*lda+m],
 // conjugated if A_CONJ; s_k = kscale[k] or 1.  64x64 tile, 256 threads, 4x4 per thread.
 // Two-level summation (FP32 only): each 8-wide k tile is summed into a fresh partial that
-// is then added to the accumulator.  A single FP32 chain over K ~ 3000 terms biased the MP2
-// energy by ~2e-5 (relative) on the 24^3 workload; the two-level sum brings it to ~1e-6.
+// is then added to the accumulator with compensated (Kahan) summation.  A single FP32
+// chain over K ~ 3000 terms biased the MP2 energy by ~2e-5 (relative) on the 24^3
+// workload; the two-level sum brings it to ~1e-6, the compensation further down.
 template <typename T, bool A_KM, bool A_CONJ>
 __global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cpx<T> *__restrict__ A, int lda,
                                                const cpx<T> *__restrict__ B, int ldb,
@@ -56,11 +57,11 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cpx<T>
   __shared__ cpx<T> Bs[BK][BN];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  cpx<T> acc[4][4];
+  cpx<T> acc[4][4], cmp[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = {T(0), T(0)};
+    for (int j = 0; j < 4; ++j) acc[i][j] = cmp[i][j] = {T(0), T(0)};
   for (int k0 = 0; k0 < K; k0 += BK) {
     for (int e = threadIdx.x; e < BM * BK; e += 256) {
       int mm, kk;
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cpx<T>
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        if (kTwoLevel) { acc[i][j].x += part[i][j].x; acc[i][j].y += part[i][j].y; }
+        if (kTwoLevel) kadd(acc[i][j], cmp[i][j], part[i][j]);
         else acc[i][j] = part[i][j];
       }
     __syncthreads();
@@ -126,7 +127,10 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cpx<T>
 // C[m][n] = sum_k opA(m,k) * B[k][n] * s_k with B real and A (hence C) either real
 // (TA = T) or complex (TA = cpx<T>): the Green's function in the real basis (real x real)
 // and the transformed states (complex x real, two multiply-adds per term).  Same tiling
-// and two-level FP32 summation as k_cgemm.
+// as k_cgemm.  FP32: each 8-wide k tile is summed into a fresh partial, and the partials
+// are added with compensated (Kahan) summation; with a plain FP32 outer sum the FP32
+// Green's function alone left a relative error of 1.2e-6 in the direct energy of the
+// 24^3 workload (most of the precision form's 2e-6).
 template <typename T> __device__ __forceinline__ void rmac(T &c, T a, T b) { c = fma(a, b, c); }
 template <typename T> __device__ __forceinline__ void rmac(cpx<T> &c, cpx<T> a, T b) {
   c.x = fma(a.x, b, c.x);
@@ -134,6 +138,17 @@ template <typename T> __device__ __forceinline__ void rmac(cpx<T> &c, cpx<T> a, 
 }
 template <typename T> __device__ __forceinline__ void radd(T &c, T a) { c += a; }
 template <typename T> __device__ __forceinline__ void radd(cpx<T> &c, cpx<T> a) { c.x += a.x; c.y += a.y; }
+// compensated (Kahan) addition c += a with running compensation e
+template <typename T> __device__ __forceinline__ void kadd(T &c, T &e, T a) {
+  const T y = a - e;
+  const T t = c + y;
+  e = (t - c) - y;
+  c = t;
+}
+template <typename T> __device__ __forceinline__ void kadd(cpx<T> &c, cpx<T> &e, cpx<T> a) {
+  kadd(c.x, e.x, a.x);
+  kadd(c.y, e.y, a.y);
+}
 template <typename X> __device__ __forceinline__ X rzero() { return X{}; }
 
 template <typename T, typename TA, bool A_KM>
@@ -145,11 +160,12 @@ __global__ void __launch_bounds__(256) k_rgemm(int M, int N, int K, const TA *__
   __shared__ T Bs[BK][BN];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  TA acc[4][4];
+  constexpr bool kTwoLevel = std::is_same<T, float>::value;
+  TA acc[4][4], cmp[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = rzero<TA>();
+    for (int j = 0; j < 4; ++j) acc[i][j] = cmp[i][j] = rzero<TA>();
   for (int k0 = 0; k0 < K; k0 += BK) {
     for (int e = threadIdx.x; e < BM * BK; e += 256) {
       int mm, kk;
@@ -170,7 +186,6 @@ __global__ void __launch_bounds__(256) k_rgemm(int M, int N, int K, const TA *__
       Bs[kk][nn] = v;
     }
     __syncthreads();
-    constexpr bool kTwoLevel = std::is_same<T, float>::value;
     TA part[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -193,7 +208,7 @@ __global__ void __launch_bounds__(256) k_rgemm(int M, int N, int K, const TA *__
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        if (kTwoLevel) radd(acc[i][j], part[i][j]);
+        if (kTwoLevel) kadd(acc[i][j], cmp[i][j], part[i][j]);
         else acc[i][j] = part[i][j];
       }
     __syncthreads();
