@@ -66,18 +66,18 @@ def source_sha():
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken
-    from the current kernel sources; else None."""
+def traffic_for(stage: str, precision: int):
+    """DRAM bytes per launch of the stage's kernel from the committed ncu summary, if it was
+    taken from the current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    e = d.get(kernel)
-    if not e or e.get("source_sha") != source_sha():
+    if d.get("source_sha") != source_sha():
         return None
-    return e.get("dram_bytes_per_launch")
+    e = d.get("fp64" if precision == 0 else "fp32", {}).get(stage)
+    return e.get("dram_bytes_per_launch") if e else None
 
 
 # ------------------------------------------------------------------ clocks
@@ -207,7 +207,7 @@ def roofline_of(st, costs, precision, simt, peaks, peak_kind):
     dom = max(st, key=lambda k: st[k]["ms"])
     if dom not in costs or st[dom]["launches"] == 0:
         return {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": traffic_for(dom)}
+                "traffic": traffic_for(dom, precision)}
     per_launch_ms = st[dom]["ms"] / st[dom]["launches"]
     work = costs[dom]["flops"] / st[dom]["launches"]
     if dom == "w_gemm" and precision != 0 and not simt:
@@ -221,7 +221,7 @@ def roofline_of(st, costs, precision, simt, peaks, peak_kind):
         peak, bound, pk = FP32_ALU_TFLOPS, "alu", "derived (128 FP32 FMA/clk/SM x 152 SMs x 2070 MHz)"
     achieved = work / (per_launch_ms / 1e3) / 1e12
     return {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "peak_kind": pk, "traffic": traffic_for(dom),
+            "frac": achieved / peak, "peak_kind": pk, "traffic": traffic_for(dom, precision),
             "work_per_launch": work, "avg_launch_ms": per_launch_ms}
 
 
