@@ -239,6 +239,9 @@ def main():
     ap.add_argument("--ntau", type=int, default=8)
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--slab", type=int, default=0, help="primary G' per slab (0 = library default)")
+    ap.add_argument("--route", default="green", choices=["green", "overlap"],
+                    help="transformed states from the per-tau Green's function (default) or from stored "
+                         "overlap densities (the paper's steps (i)-(iii))")
     ap.add_argument("--workload", default="cfg2", choices=["cfg2", "batch", "learned", "cfg3"],
                     help="cfg2: the 16-well 24^3 system; batch: 8 uneven systems in one graph launch; "
                          "learned: surrogate-screened pairs; cfg3: precision form on the 64-well 36^3 system")
@@ -309,11 +312,22 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    route = L.ROUTE_OVERLAP if args.route == "overlap" else L.ROUTE_GREEN
+    route_info = {}
+
     def time_form(precision, simt=False):
         ctx = L.setup_from_solid(s, precision=precision, real=True, simt_gemm=simt)
         L.ltmp2_set_stream(ctx, stream)
         if args.slab > 0:
             L.ltmp2_set_slab_size(ctx, args.slab)
+        if route == L.ROUTE_OVERLAP:
+            t_r = time.perf_counter()
+            L.ltmp2_set_route(ctx, route)
+            sz = L.ltmp2_sizes(ctx)
+            route_info[precision] = {
+                "overlap_setup_s": time.perf_counter() - t_r,
+                "overlap_bytes": L.ltmp2_num_primary_gprime(ctx) * sz["n_occ"] * (s.n_orb - s.n_occ)
+                * (16 if precision == L.FP64 else 8)}
         for _ in range(args.warmup):
             with torch.cuda.stream(stream):
                 flush.fill_(1.0)
@@ -382,6 +396,10 @@ def main():
         "gpu_launches": r["launches"],
         "peaks_source": peak_kind,
     }
+    out["config"]["route"] = ("overlap densities stored (paper's steps (i)-(iii))" if route == L.ROUTE_OVERLAP
+                              else "per-tau Green's function")
+    if route_info:
+        out["route"] = {("fp64" if k == L.FP64 else "fp32"): v for k, v in route_info.items()}
 
     if rank == 0 and not args.no_forms:
         other = L.FP32 if primary == L.FP64 else L.FP64
@@ -426,6 +444,8 @@ def main():
             t1 = time.perf_counter()
             ctx = L.setup_from_solid(s, precision=primary, real=True)
             L.ltmp2_set_stream(ctx, stream)
+            if route == L.ROUTE_OVERLAP:
+                L.ltmp2_set_route(ctx, route)
             L.ltmp2_energy(ctx, tau, w)
             L.ltmp2_destroy(ctx)
             torch.cuda.synchronize()

@@ -244,6 +244,24 @@ int ltmp2_mlp_train(ltmp2_mlp *net, const float *X, const float *y, int n, int e
 int ltmp2_mlp_predict(const ltmp2_mlp *net, const float *X, int n, float *y);
 void ltmp2_mlp_destroy(ltmp2_mlp *net);
 
+/* ---------------------------------------------------------------- transformed-state route
+ * How step (iii) of Sec. III A builds w_j^{(G' tau)} (Eqs. SCHnewstate, SCHtransmatrix):
+ *   LTMP2_ROUTE_GREEN (default): the virtual Green's function P_v(tau) is built per tau by a
+ *     GEMM over the virtuals and applied to the gathered e^{-iG'r}|j>; nothing is stored.
+ *   LTMP2_ROUTE_OVERLAP: the paper's own route: step (i) computes and stores the overlap
+ *     densities rho_aj(G') = <a|e^{-iG'r}|j> (Eq. SCHovrlp) once for every virtual a,
+ *     occupied j and primary G' (n_prim x n_occ x n_v complex values: 1.35 GB in FP64 for
+ *     3071 plane waves, 32 occupied), and per tau and G' the transformation matrix
+ *     e^{(e_j-mu)tau} rho_aj(G') e^{-(e_a-mu)tau} multiplies the virtual coefficients.
+ * Both give the same energies up to rounding.                                          */
+#define LTMP2_ROUTE_GREEN 0
+#define LTMP2_ROUTE_OVERLAP 1
+/* Select the route for later ltmp2_energy* calls.  LTMP2_ROUTE_OVERLAP computes and stores
+ * the overlap densities during this call (first use allocates them) and needs
+ * LTMP2_FLAG_REAL_ORBITALS (UNSUPPORTED otherwise); its transformed-state product runs on
+ * the CUDA cores in both precisions.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.       */
+int ltmp2_set_route(ltmp2_ctx *ctx, int route);
+
 /* ---------------------------------------------------------------- internal cutoff extrapolation
  * Sec. III D, Eq. CutDecay: the MP2 energy converges with the auxiliary cutoff as
  * E(E_aux) - E(inf) ~ E_aux^(-3/2).  With n_c levels, every later ltmp2_energy* call

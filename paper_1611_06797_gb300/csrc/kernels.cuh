@@ -247,14 +247,15 @@ template <typename T> __device__ __forceinline__ cpx<T> from_real_basis(const in
   return {(wb.x - wq.y) * r2, (wb.y + wq.x) * r2};
 }
 
-// S^T in the real basis: row (slot, j) = U (e^{(e_j-mu)tau} e^{-iG'r} phi_j)
+// S^T in the real basis: row (slot, j) = U (e^{(e_j-mu)tau} e^{-iG'r} phi_j); unscaled
+// (factor 1) for the overlap densities of the paper's route
 template <typename T>
-__global__ void k_gather_s_real(Plan p, int gp0, int np, cpx<T> *__restrict__ st) {
+__global__ void k_gather_s_real(Plan p, int gp0, int np, cpx<T> *__restrict__ st, bool unscaled = false) {
   const int col = blockIdx.y;
   const int slot = col / p.n_occ, j = col % p.n_occ;
   const int g = slot_aux(p, gp0, np, slot);
   const int gx = p.aux_m[3 * g], gy = p.aux_m[3 * g + 1], gz = p.aux_m[3 * g + 2];
-  const T dj = ((const T *)p.dscale)[j];
+  const T dj = unscaled ? T(1) : ((const T *)p.dscale)[j];
   const int n = p.n;
   const cpx<T> *cg = (const cpx<T> *)p.cgrid + (size_t)j * n * n * n;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < p.n_pw; q += gridDim.x * blockDim.x) {
@@ -265,12 +266,31 @@ __global__ void k_gather_s_real(Plan p, int gp0, int np, cpx<T> *__restrict__ st
   }
 }
 
-// W^T rows back from real-basis coordinates to plane-wave coefficients
+// W^T rows back from real-basis coordinates to plane-wave coefficients; with rowscale
+// (the paper's route) row (slot, j) is also multiplied by e^{(e_j-mu)tau}
 template <typename T>
-__global__ void k_from_real_basis(Plan p, const cpx<T> *__restrict__ w, cpx<T> *__restrict__ out) {
+__global__ void k_from_real_basis(Plan p, const cpx<T> *__restrict__ w, cpx<T> *__restrict__ out,
+                                  const T *__restrict__ rowscale = nullptr) {
   const size_t row = (size_t)blockIdx.y * p.n_pw;
+  const T f = rowscale ? rowscale[blockIdx.y % p.n_occ] : T(1);
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < p.n_pw; q += gridDim.x * blockDim.x)
-    out[row + q] = from_real_basis<T>(p.pw_m + 3 * q, w[row + q], w[row + p.pw_pair[q]]);
+    out[row + q] = cscale(from_real_basis<T>(p.pw_m + 3 * q, w[row + q], w[row + p.pw_pair[q]]), f);
+}
+
+// out[c][r] = in[r][c] for a rows x cols matrix of T (32 x 32 tiles through shared memory)
+template <typename T>
+__global__ void k_transpose(int rows, int cols, const T *__restrict__ in, T *__restrict__ out) {
+  __shared__ T tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[k][threadIdx.x] = in[(size_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int c = c0 + k, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[(size_t)c * rows + r] = tile[threadIdx.x][k];
+  }
 }
 
 // ---------------------------------------------------------------- gather S^T

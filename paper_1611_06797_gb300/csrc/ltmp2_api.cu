@@ -1095,6 +1095,28 @@ int ltmp2_energy_batch(ltmp2_ctx *const *ctxs, int n, const int *n_tau, const do
   return rc;
 }
 
+// ---------------------------------------------------------------- transformed-state route
+int ltmp2_set_route(ltmp2_ctx *ctx, int route) {
+  if (!ctx || (route != LTMP2_ROUTE_GREEN && route != LTMP2_ROUTE_OVERLAP)) return LTMP2_ERR_INVALID_ARG;
+  Plan &p = ctx->p;
+  if (route == LTMP2_ROUTE_GREEN) {
+    p.route = 0;
+    return LTMP2_OK;
+  }
+  if (!p.real_basis) return LTMP2_ERR_UNSUPPORTED;
+  DeviceGuard g(ctx->device);
+  const size_t cs = p.precision == LTMP2_FP64 ? 16 : 8;
+  int rc;
+  if (!p.rt && (rc = dalloc_bytes(ctx, &p.rt, cs * (size_t)p.n_prim * p.n_occ * p.n_v))) return rc;
+  cudaError_t e = p.precision == LTMP2_FP64 ? Path<double>::overlap_setup(p, ctx->stream)
+                                             : Path<float>::overlap_setup(p, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  ctx->kernel_launches += 1 + 2 * ((p.n_prim + p.max_prim - 1) / p.max_prim);
+  p.route = 1;
+  return LTMP2_OK;
+}
+
 // ---------------------------------------------------------------- internal cutoff extrapolation
 static_assert(kMaxLevels == LTMP2_MAX_LEVELS, "level capacity");
 int ltmp2_set_extrapolation(ltmp2_ctx *ctx, int n_c, double alpha) {

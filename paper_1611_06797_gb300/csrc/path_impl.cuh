@@ -143,12 +143,35 @@ cudaError_t Path<T>::setup_occupied(const Plan &p, const void *c_occ_dev, cudaSt
   return cudaGetLastError();
 }
 
+template <typename T> cudaError_t Path<T>::overlap_setup(const Plan &p, cudaStream_t st) {
+  // r_a transposed into pt ([n_pw][n_v]); pt is free on this route (no Green's function)
+  k_transpose<T><<<dim3((p.n_pw + 31) / 32, (p.n_v + 31) / 32), dim3(32, 8), 0, st>>>(p.n_v, p.n_pw, (const T *)p.cv,
+                                                                                      (T *)p.pt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  for (int gp0 = 0; gp0 < p.n_prim; gp0 += p.max_prim) {
+    const int np = p.n_prim - gp0 < p.max_prim ? p.n_prim - gp0 : p.max_prim;
+    const int ncols = np * p.n_occ;
+    // rho^T[(G', j)][a] = sum_q (U e^{-iG'r} phi_j)[q] r_a[q]: U is unitary and r_a = U phi_a
+    // is real, so this is <a| e^{-iG'r} |j> (Eq. SCHovrlp), step (i) of Sec. III A
+    k_gather_s_real<T><<<dim3((p.n_pw + 255) / 256, ncols), 256, 0, st>>>(p, gp0, np, (cpx<T> *)p.st, true);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dim3 grid((p.n_v + 63) / 64, (ncols + 63) / 64);
+    k_rgemm<T, cpx<T>, true><<<grid, 256, 0, st>>>(ncols, p.n_v, p.n_pw, (const cpx<T> *)p.st, p.n_pw,
+                                                    (const T *)p.pt, p.n_v, nullptr,
+                                                    (cpx<T> *)p.rt + (size_t)gp0 * p.n_occ * p.n_v, p.n_v);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t Path<T>::green(const Plan &p, double tau, cudaStream_t st, StageTimer *tm) {
   ScopedStage s(tm, kStageGreen);
   k_dscale<T><<<(p.n_orb + 255) / 256, 256, 0, st>>>(p.n_orb, p.n_occ, p.eps, p.mu, tau, (T *)p.dscale);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (p.route == 1) return cudaSuccess;   // no Green's function on the paper's route
   const int M = p.n_pw, N = p.n_pw, K = p.n_v;
   dim3 grid((N + 63) / 64, (M + 63) / 64);
   if (p.real_basis) {
@@ -175,7 +198,7 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
   const int nslots = np * p.slots_per_prim();
   const int ncols = nslots * no;
   cudaError_t e;
-  {
+  if (p.route != 1) {
     ScopedStage s(tm, kStageGatherZ);
     if (p.real_basis)
       k_gather_s_real<T><<<dim3((p.n_pw + 255) / 256, ncols), 256, 0, st>>>(p, gp0, np, (cpx<T> *)p.st);
@@ -186,8 +209,19 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
   {
     ScopedStage s(tm, kStageWGemm);
     bool done = false;
+    if (p.route == 1) {
+      // W (real-basis coordinates, before the e^{(e_j-mu)tau} row factor) =
+      // sum_a rho^T[(G', j)][a] e^{-(e_a-mu)tau} r_a: step (iii) with the stored overlap densities
+      dim3 grid((p.n_pw + 63) / 64, (ncols + 63) / 64);
+      k_rgemm<T, cpx<T>, true><<<grid, 256, 0, st>>>(ncols, p.n_pw, p.n_v,
+                                                      (const cpx<T> *)p.rt + (size_t)gp0 * no * p.n_v, p.n_v,
+                                                      (const T *)p.cv, p.n_pw, (const T *)p.dscale + p.n_occ,
+                                                      (cpx<T> *)p.wt, p.n_pw);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      done = true;
+    }
     if constexpr (std::is_same<T, float>::value) {
-      if (p.tc) {
+      if (p.tc && !done) {
         if ((e = tc_wgemm(*p.tc, p.st, ncols, p.wt, st)) != cudaSuccess) return e;
         done = true;
       }
@@ -209,8 +243,8 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
   const cpx<T> *w_pw = (const cpx<T> *)p.wt;
   if (p.real_basis) {
     ScopedStage s(tm, kStageGatherZ);
-    k_from_real_basis<T><<<dim3((p.n_pw + 255) / 256, ncols), 256, 0, st>>>(p, (const cpx<T> *)p.wt,
-                                                                            (cpx<T> *)p.st);
+    k_from_real_basis<T><<<dim3((p.n_pw + 255) / 256, ncols), 256, 0, st>>>(
+        p, (const cpx<T> *)p.wt, (cpx<T> *)p.st, p.route == 1 ? (const T *)p.dscale : nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     w_pw = (const cpx<T> *)p.st;
   }

@@ -91,6 +91,12 @@ struct Plan {
   double2 *sxl = nullptr, *ydl = nullptr;  // [n_lev][slab cap][n_occ][n_occ] pair sums over A_n
   double *exl = nullptr, *edl = nullptr;   // [n_lev][n_occ][n_occ] level pair energies (n >= 2)
   double *esum_lev = nullptr;              // [2 n_lev]: E_d[n], E_x[n]
+  // Transformed-state route.  0: Green's function P_v(tau) built per tau and applied to the
+  // gathered e^{-iG'r}|j> (W = P_r (U S)).  1: the paper's route, Sec. III A steps (i)-(iii):
+  // overlap densities rho_aj(G') = <a|e^{-iG'r}|j> stored once (rt), and per tau
+  // W = sum_a |a> e^{-(e_a-mu)tau} rho_aj(G') e^{(e_j-mu)tau} (real orbitals only).
+  int route = 0;
+  void *rt = nullptr;        // route 1: [n_prim * n_occ][n_v] cpx<T>, row (G', j), column a
   int slots_per_prim() const { return real_orb ? 1 : 2; }
 };
 
@@ -112,10 +118,14 @@ enum Stage {
 template <typename T> struct Path {
   // kernel launches per Green's function build and per slab (the tcgen05 path of the
   // precision form adds one operand-packing launch to each)
-  static int green_launches(const Plan &p) { return p.tc ? 3 : 2; }
+  static int green_launches(const Plan &p) { return p.route == 1 ? 1 : (p.tc ? 3 : 2); }
   static int slab_launches(const Plan &p) {
+    if (p.route == 1) return 7 + (p.n_lev > 1 ? 1 : 0);   // no gather, CUDA-core product
     return (p.tc ? 8 : 7) + (p.real_basis ? 1 : 0) + (p.n_lev > 1 ? 1 : 0);
   }
+  // route 1 setup: the overlap densities of every primary G' into rt (uses st and pt as
+  // scratch; pt holds the transposed virtual coordinates meanwhile)
+  static cudaError_t overlap_setup(const Plan &p, cudaStream_t st);
   // launches of zero_acc + finish
   static int frame_launches(const Plan &p) { return p.n_lev > 1 ? 3 : 2; }
   static cudaError_t init_device();

@@ -72,6 +72,7 @@ def load_library():
         "ltmp2_destroy": (None, [vp]),
         "ltmp2_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "ltmp2_set_extrapolation": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double]),
+        "ltmp2_set_route": (ctypes.c_int, [vp, ctypes.c_int]),
         "ltmp2_level_energies": (ctypes.c_int, [vp, dp, P(ctypes.c_int), dp, dp]),
         "ltmp2_extrapolate": (ctypes.c_int, [ctypes.c_int, dp, dp, dp, dp, dp]),
     }
@@ -283,6 +284,17 @@ def ltmp2_energy_noalloc(lattice, grid, miller, coeff, eps, n_occ: int, tau, w, 
     _check(f(ctypes.byref(s), len(tau), _dp(tau), _dp(w), _dp(ed), _dp(ex), _dp(ep) if pairs else None,
              ctypes.c_void_p(int(handle) if handle else 0)), "ltmp2_energy_noalloc")
     return float(ed[0]), float(ex[0]), ep
+
+
+# ---------------------------------------------------------------- transformed-state route
+ROUTE_GREEN = 0
+ROUTE_OVERLAP = 1
+
+
+def ltmp2_set_route(ctx: Context, route: int) -> None:
+    """ROUTE_GREEN (per-tau Green's function) or ROUTE_OVERLAP (stored overlap densities,
+    the paper's steps (i)-(iii)); the latter computes the densities now."""
+    _check(load_library().ltmp2_set_route(ctx.handle, int(route)), "ltmp2_set_route")
 
 
 # ---------------------------------------------------------------- internal cutoff extrapolation
