@@ -1,0 +1,52 @@
+"""Edge cases of the C ABI on the GPU: empty outer-loop ranges, the smallest and
+out-of-range slab sizes, a single Laplace point, and rejected quadrature input."""
+import numpy as np
+import pytest
+
+import paper_1611_06797_gb300 as L
+from oracle import OracleSystem, denominator_range, laplace_denominator, mp2_energy, sinc_laplace_quadrature
+from tests.conftest import solid
+
+pytestmark = pytest.mark.gpu
+
+
+def test_empty_gprime_range_gives_zero():
+    s = solid("tiny2")
+    tau, w = sinc_laplace_quadrature(3, *denominator_range(OracleSystem.from_solid(s)))
+    ctx = L.setup_from_solid(s, precision=L.FP64, real=True)
+    n = L.ltmp2_num_primary_gprime(ctx)
+    for k in (0, n // 2, n):
+        ed, ex, pd, px = L.ltmp2_energy_partial(ctx, tau, w, k, k)
+        assert ed == 0.0 and ex == 0.0 and not pd.any() and not px.any()
+    with pytest.raises(L.Ltmp2Error):
+        L.ltmp2_energy_partial(ctx, tau, w, 3, 2)
+    with pytest.raises(L.Ltmp2Error):
+        L.ltmp2_energy_partial(ctx, tau, w, 0, n + 1)
+    L.ltmp2_destroy(ctx)
+
+
+def test_slab_of_one_and_single_tau_match_oracle():
+    s = solid("tiny")
+    tau, w = sinc_laplace_quadrature(1, *denominator_range(OracleSystem.from_solid(s)))
+    ref = mp2_energy(OracleSystem.from_solid(s), laplace_denominator(tau, w))
+    for real in (True, False):
+        ctx = L.setup_from_solid(s, precision=L.FP64, real=real)
+        L.ltmp2_set_slab_size(ctx, 1)
+        ed, ex, _ = L.ltmp2_energy(ctx, tau, w)
+        L.ltmp2_destroy(ctx)
+        assert abs(ed - ref["E_d"]) < 1e-8 and abs(ex - ref["E_x"]) < 1e-8
+
+
+def test_bad_slab_and_quadrature_are_rejected():
+    s = solid("tiny2")
+    ctx = L.setup_from_solid(s, precision=L.FP64, real=True)
+    cap = L.ltmp2_set_slab_size(ctx, 0)          # n <= 0 restores the capacity
+    assert cap >= 1 and L.ltmp2_set_slab_size(ctx, -3) == cap
+    with pytest.raises(L.Ltmp2Error) as e:
+        L.ltmp2_set_slab_size(ctx, cap + 1)
+    assert e.value.name == "INVALID_ARG"
+    for tau, w in [([], []), ([0.0], [1.0]), ([-1.0], [1.0]), ([float("nan")], [1.0]), ([1.0], [float("inf")])]:
+        with pytest.raises(L.Ltmp2Error) as e:
+            L.ltmp2_energy(ctx, np.array(tau, dtype=float), np.array(w, dtype=float))
+        assert e.value.name == "INVALID_ARG"
+    L.ltmp2_destroy(ctx)
