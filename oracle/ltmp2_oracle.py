@@ -364,3 +364,43 @@ def cutoff_extrapolation(ecut: Sequence[float], energy: Sequence[float]) -> Tupl
         s2 = float(np.sum((y - a - b * x) ** 2)) / (n - 2.0)
         sa = math.sqrt(s2 * sxx / det)
     return a, b, sa
+
+
+# ---------------------------------------------------------------------------
+# Spin-unrestricted MP2 (Eqs. MP2direct, MP2exchange with independent spin sums)
+# ---------------------------------------------------------------------------
+def uhf_mp2_energy(sa: OracleSystem, sb: OracleSystem, D: Callable[[np.ndarray], np.ndarray]):
+    """E_d = 1/2 sum_{s s'} sum_{i in occ s, j in occ s'} sum_{a in virt s, b in virt s'}
+                 |<i j|a b>|^2 D(e_i + e_j - e_a - e_b)
+       E_x = -1/2 sum_s sum_{i j in occ s} sum_{a b in virt s} <i j|a b> <a b|j i> D(...)
+    with spatial integrals <ij|ab> (Eq. SCH2EI) between orbitals of the stated spins.
+    sa, sb: the two spin channels (same lattice, grid, plane waves and E_aux); each
+    ``n_occ`` counts singly occupied orbitals and may be 0.  Returns E_d, E_x and the
+    same-spin (alpha alpha, beta beta) and opposite-spin parts of E = E_d + E_x."""
+    mG, _, v = aux_set(sa)
+    neg = _neg_index(mG)
+    spins = [sa, sb]
+    rho = []
+    for s in spins:
+        occ = list(range(s.n_occ))
+        virt = list(range(s.n_occ, s.coeff.shape[0]))
+        rho.append(overlap_densities_conv(s, occ, virt, mG) if occ else [])
+    E_d = E_x = 0.0
+    part = {"aa": 0.0, "bb": 0.0, "ab": 0.0}
+    for x in (0, 1):
+        for y in (0, 1):
+            sx, sy = spins[x], spins[y]
+            ev_x, ev_y = sx.eps[sx.n_occ:], sy.eps[sy.n_occ:]
+            for i in range(sx.n_occ):
+                for j in range(sy.n_occ):
+                    K = pair_integrals(rho[x][i], rho[y][j][:, neg], v, sa.omega)
+                    Dab = D(sx.eps[i] + sy.eps[j] - ev_x[:, None] - ev_y[None, :])
+                    d = 0.5 * float(np.sum((K.real ** 2 + K.imag ** 2) * Dab))
+                    e = d
+                    E_d += d
+                    if x == y:
+                        xx = -0.5 * float(np.sum(K * np.conj(K.T) * Dab).real)
+                        E_x += xx
+                        e += xx
+                    part["ab" if x != y else ("aa" if x == 0 else "bb")] += e
+    return {"E_d": E_d, "E_x": E_x, "E": E_d + E_x, "E_aa": part["aa"], "E_bb": part["bb"], "E_ab": part["ab"]}

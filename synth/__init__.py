@@ -2,7 +2,7 @@
 benchmark and the oracle's tests.  Holds no MP2 / LTMP2 arithmetic: it only
 produces mean-field input (plane-wave orbitals and their energies)."""
 from .model_solid import (ModelSolidSpec, ModelSolid, build_model_solid, spec_by_name,
-                          SPECS, free_electron_solid, BATCH_NAMES)
+                          SPECS, free_electron_solid, BATCH_NAMES, spin_polarized_pair)
 
 __all__ = ["ModelSolidSpec", "ModelSolid", "build_model_solid", "spec_by_name", "SPECS",
-           "free_electron_solid", "BATCH_NAMES"]
+           "free_electron_solid", "BATCH_NAMES", "spin_polarized_pair"]

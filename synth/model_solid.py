@@ -300,3 +300,15 @@ def free_electron_solid(a: float, grid: int, r2: int, n_occ: int = 1) -> ModelSo
         raise ValueError("n_occ does not close a shell")
     return ModelSolid(None, lattice, np.array([grid] * 3, dtype=np.int32), miller, coeff, eps,
                       n_occ, 0.5 * (r2 + 1e-6) * b * b, np.zeros((0, 3)))
+
+
+def spin_polarized_pair(spec: ModelSolidSpec, n_occ_alpha: int, n_occ_beta: int,
+                        depth_beta: Optional[float] = None,
+                        real_orbitals: bool = True) -> Tuple[ModelSolid, ModelSolid]:
+    """Synthetic spin-unrestricted mean field: the same cell, wells and plane-wave set for
+    both spins; the beta electrons see wells of depth ``depth_beta`` (default 0.9 x the
+    alpha depth), so the two orbital sets differ.  ``n_occ_*`` singly occupied orbitals."""
+    a = build_model_solid(dataclasses.replace(spec, n_occ=n_occ_alpha), real_orbitals=real_orbitals)
+    db = 0.9 * spec.depth if depth_beta is None else depth_beta
+    b = build_model_solid(dataclasses.replace(spec, n_occ=n_occ_beta, depth=db), real_orbitals=real_orbitals)
+    return a, b
