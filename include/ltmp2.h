@@ -244,6 +244,29 @@ int ltmp2_mlp_train(ltmp2_mlp *net, const float *X, const float *y, int n, int e
 int ltmp2_mlp_predict(const ltmp2_mlp *net, const float *X, int n, float *y);
 void ltmp2_mlp_destroy(ltmp2_mlp *net);
 
+/* ---------------------------------------------------------------- spin-unrestricted form
+ * Eqs. MP2direct and MP2exchange with the spin sums kept (Sec. II B): alpha and beta
+ * electrons occupy different orbital sets.  With <ij|ab> between orbitals of the stated
+ * spins and D the Laplace denominator of Eq. SCHLT,
+ *   E_direct   = 1/2 sum_{s s'} sum_{i j a b} |<i s, j s'|a s, b s'>|^2 D,
+ *   E_exchange = -1/2 sum_s sum_{i j a b} <i s, j s|a s, b s> <a s, b s|j s, i s> D.
+ * Each channel runs the closed-shell path on its own orbitals (its exchange and same-spin
+ * direct sums, reweighted: 1/2 per (s, s') and per s instead of 2 and 1), and the
+ * opposite-spin direct term contracts the two channels' diagonal co-densities
+ * M^alpha_ii(G;G') and M^beta_jj(-G;-G') at the same tau and G' (the paper notes that
+ * the spin-unrestricted case costs twice the restricted one, Sec. III C).
+ *   alpha, beta: contexts set up from the two channels' orbitals and energies, each with
+ *     its own n_occ (singly occupied orbitals, >= 1) and mid-gap shift; they must share
+ *     the lattice, grid, plane-wave set, auxiliary set, precision and real-orbital flag
+ *     (else INVALID_ARG).  Both run on alpha's stream; extrapolation levels and pair
+ *     masks are not supported here (UNSUPPORTED).  The first call allocates alpha's
+ *     opposite-spin scratch.
+ *   tau, w: a quadrature valid for both channels' denominators.
+ *   e_direct, e_exchange: Ha per cell.  e_spin: NULL or [3] = same-spin alpha, same-spin
+ *     beta and opposite-spin parts of E_direct + E_exchange.                            */
+int ltmp2_energy_uhf(ltmp2_ctx *alpha, ltmp2_ctx *beta, int n_tau, const double *tau, const double *w,
+                     double *e_direct, double *e_exchange, double *e_spin);
+
 /* ---------------------------------------------------------------- transformed-state route
  * How step (iii) of Sec. III A builds w_j^{(G' tau)} (Eqs. SCHnewstate, SCHtransmatrix):
  *   LTMP2_ROUTE_GREEN (default): the virtual Green's function P_v(tau) is built per tau by a

@@ -941,6 +941,66 @@ static __global__ void k_accum_lev(Plan p, int gp0, int np, double coef) {
   }
 }
 
+// ---------------------------------------------------------------- opposite-spin direct term
+// Spin-unrestricted form: the direct energy couples M^a_ii of the alpha channel with M^b_jj
+// of the beta channel at the same tau and G' (Eq. MP2direct with s != s').  Per primary G'
+// and pair (i alpha, j beta): y = Re[Y(G') + Y(-G')], Y(G') = sum_G v(G) M^a_ii(G;G')
+// M^b_jj(-G;-G').  Real orbitals: Y(-G') = conj(Y(G')) and M(-G;-G') = conj(M(G;G')).
+template <typename T>
+__global__ void k_direct_cross(Plan pa, Plan pb, int np, const cpx<T> *__restrict__ ma,
+                               const cpx<T> *__restrict__ mb, double *__restrict__ y) {
+  const int gpl = blockIdx.x, i = blockIdx.y;
+  const int na = pa.n_occ, nb = pb.n_occ, naux = pa.n_aux;
+  const T *v = vtab<T>(pa);
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    double acc = 0.0;
+    for (int pass = 0; pass < (pa.real_orb ? 1 : 2); ++pass) {
+      // general orbitals: pass 0 pairs slot G' of alpha with slot -G' of beta, pass 1 the reverse
+      const int sa = pass == 0 ? gpl : gpl + np, sb = pa.real_orb ? gpl : (pass == 0 ? gpl + np : gpl);
+      const cpx<T> *A = ma + (size_t)sa * naux * na;
+      const cpx<T> *B = mb + (size_t)sb * naux * nb;
+      double ax = 0.0;
+      T cx = T(0);
+      for (int g = 0; g < naux; ++g) {
+        const cpx<T> x = A[(size_t)g * na + i];
+        cpx<T> prod;
+        if (pa.real_orb) prod = cmulconj(x, B[(size_t)g * nb + j]);
+        else prod = cmul(x, B[(size_t)pa.aux_neg[g] * nb + j]);
+        cx += v[g] * prod.x;
+        if ((g & 31) == 31) { ax += (double)cx; cx = T(0); }
+      }
+      ax += (double)cx;
+      acc += pa.real_orb ? 2.0 * ax : ax;
+    }
+    y[((size_t)gpl * na + i) * nb + j] = acc;
+  }
+}
+
+// acc[i][j] += -coef v(G') y over the slab's primary G', fixed order
+static __global__ void k_accum_cross(Plan pa, int nb, int gp0, int np, double coef, const double *__restrict__ y,
+                                     double *__restrict__ acc) {
+  const int na = pa.n_occ;
+  const int ij = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ij >= na * nb) return;
+  double s = 0.0;
+  for (int gpl = 0; gpl < np; ++gpl) s += -coef * pa.v_aux64[pa.prim[gp0 + gpl]] * y[(size_t)gpl * na * nb + ij];
+  acc[ij] += s;
+}
+
+// out[0] = sum of n values, fixed order; one block of 256 threads
+static __global__ void k_sum(int n, const double *__restrict__ x, double *__restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) s += x[k];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
 static __global__ void k_zero_acc(Plan p) {
   const int no2 = p.n_occ * p.n_occ;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < no2; k += gridDim.x * blockDim.x) {

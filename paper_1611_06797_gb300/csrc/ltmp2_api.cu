@@ -99,6 +99,9 @@ struct ltmp2_ctx {
   std::vector<double> lev_ecut;
   std::vector<int> lev_count;
   bool lev_alloc = false, lev_done = false;
+  // spin-unrestricted pairing (this context as the alpha channel): opposite-spin scratch
+  double *d_cross_y = nullptr, *d_cross_acc = nullptr, *d_cross_sum = nullptr;
+  int cross_nb = 0;
   ~ltmp2_ctx() {
     tc_release(tc);
     for (void *q : allocs) cudaFree(q);
@@ -526,6 +529,43 @@ struct ltmp2_batch {
 };
 
 namespace {
+}  // namespace
+
+// spin-unrestricted form: both channels on the alpha context's stream
+namespace {
+template <typename T>
+int enqueue_uhf(ltmp2_ctx *a, ltmp2_ctx *b, int n_tau, const double *tau, const double *w, long long *launches) {
+  Plan &pa = a->p, &pb = b->p;
+  cudaStream_t st = a->stream;
+  cudaError_t e;
+  if ((e = Path<T>::zero_acc(pa, st)) != cudaSuccess || (e = Path<T>::zero_acc(pb, st)) != cudaSuccess)
+    return cuda_status(e);
+  if ((e = cudaMemsetAsync(a->d_cross_acc, 0, sizeof(double) * pa.n_occ * pb.n_occ, st)) != cudaSuccess)
+    return cuda_status(e);
+  *launches += 2;
+  const double nfft = (double)pa.n * pa.n * pa.n;
+  for (int k = 0; k < n_tau; ++k) {
+    if ((e = Path<T>::green(pa, tau[k], st, nullptr)) != cudaSuccess) return cuda_status(e);
+    if ((e = Path<T>::green(pb, tau[k], st, nullptr)) != cudaSuccess) return cuda_status(e);
+    *launches += Path<T>::green_launches(pa) + Path<T>::green_launches(pb);
+    const double coef = w[k] / (pa.omega * pa.omega * nfft * nfft);
+    for (int g0 = 0; g0 < pa.n_prim; g0 += pa.max_prim) {
+      const int np = std::min(pa.max_prim, pa.n_prim - g0);
+      // each channel: its exchange and same-spin direct sums, and its diagonal co-densities
+      if ((e = Path<T>::slab(pa, g0, np, coef, st, nullptr)) != cudaSuccess) return cuda_status(e);
+      if ((e = Path<T>::slab(pb, g0, np, coef, st, nullptr)) != cudaSuccess) return cuda_status(e);
+      if ((e = Path<T>::direct_cross(pa, pb, g0, np, coef, a->d_cross_y, a->d_cross_acc, st)) != cudaSuccess)
+        return cuda_status(e);
+      *launches += Path<T>::slab_launches(pa) + Path<T>::slab_launches(pb) + 2;
+    }
+  }
+  if ((e = Path<T>::finish(pa, st, nullptr)) != cudaSuccess || (e = Path<T>::finish(pb, st, nullptr)) != cudaSuccess)
+    return cuda_status(e);
+  if ((e = Path<T>::sum(pa.n_occ * pb.n_occ, a->d_cross_acc, a->d_cross_sum, st)) != cudaSuccess)
+    return cuda_status(e);
+  *launches += 3;
+  return LTMP2_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -1093,6 +1133,57 @@ int ltmp2_energy_batch(ltmp2_ctx *const *ctxs, int n, const int *n_tau, const do
   rc = ltmp2_batch_run(b, e_direct, e_exchange);
   ltmp2_batch_destroy(b);
   return rc;
+}
+
+// ---------------------------------------------------------------- spin-unrestricted form
+
+int ltmp2_energy_uhf(ltmp2_ctx *alpha, ltmp2_ctx *beta, int n_tau, const double *tau, const double *w,
+                     double *e_direct, double *e_exchange, double *e_spin) {
+  if (!alpha || !beta || alpha == beta || !e_direct || !e_exchange) return LTMP2_ERR_INVALID_ARG;
+  int rc = check_tau(n_tau, tau, w);
+  if (rc) return rc;
+  Plan &pa = alpha->p, &pb = beta->p;
+  // the two channels must share the cell, grid, plane waves and auxiliary set
+  if (alpha->device != beta->device || pa.precision != pb.precision || pa.n != pb.n || pa.n_pw != pb.n_pw ||
+      pa.n_aux != pb.n_aux || pa.n_prim != pb.n_prim || pa.real_orb != pb.real_orb ||
+      alpha->aux_g2 != beta->aux_g2 || std::memcmp(alpha->lattice, beta->lattice, sizeof(alpha->lattice)) != 0)
+    return LTMP2_ERR_INVALID_ARG;
+  if (pa.n_lev > 1 || pb.n_lev > 1 || pa.pair_keep || pb.pair_keep) return LTMP2_ERR_UNSUPPORTED;
+  DeviceGuard g(alpha->device);
+  // a common slab size; restored afterwards
+  const int keep_a = pa.max_prim, keep_b = pb.max_prim;
+  const int slab = std::min(keep_a, keep_b);
+  if (!alpha->d_cross_y || alpha->cross_nb != pb.n_occ) {
+    const size_t nab = (size_t)pa.n_occ * pb.n_occ;
+    if ((rc = dalloc(alpha, &alpha->d_cross_y, (size_t)alpha->slab_capacity * nab))) return rc;
+    if ((rc = dalloc(alpha, &alpha->d_cross_acc, nab))) return rc;
+    if ((rc = dalloc(alpha, &alpha->d_cross_sum, 1))) return rc;
+    alpha->cross_nb = pb.n_occ;
+  }
+  pa.max_prim = pb.max_prim = slab;
+  rc = pa.precision == LTMP2_FP64 ? enqueue_uhf<double>(alpha, beta, n_tau, tau, w, &alpha->kernel_launches)
+                                  : enqueue_uhf<float>(alpha, beta, n_tau, tau, w, &alpha->kernel_launches);
+  cudaError_t e = cudaStreamSynchronize(alpha->stream);
+  pa.max_prim = keep_a;
+  pb.max_prim = keep_b;
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_status(e);
+  if ((rc = check_tc_flag(alpha)) || (rc = check_tc_flag(beta))) return rc;
+  double ea[4], eb[4], ecross = 0.0;
+  if ((e = cudaMemcpy(ea, pa.esum, sizeof(ea), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(eb, pb.esum, sizeof(eb), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(&ecross, alpha->d_cross_sum, sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_status(e);
+  // each channel's sums follow the closed-shell weights (direct 2, exchange 1 per spin sum):
+  // the spin-unrestricted weights are 1/2 per (s, s') and 1/2 per s
+  *e_direct = 0.25 * (ea[0] + eb[0]) + ecross;
+  *e_exchange = 0.5 * (ea[1] + eb[1]);
+  if (e_spin) {
+    e_spin[0] = 0.25 * ea[0] + 0.5 * ea[1];
+    e_spin[1] = 0.25 * eb[0] + 0.5 * eb[1];
+    e_spin[2] = ecross;
+  }
+  return LTMP2_OK;
 }
 
 // ---------------------------------------------------------------- transformed-state route

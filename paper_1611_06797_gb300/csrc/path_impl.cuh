@@ -310,6 +310,23 @@ cudaError_t Path<T>::descriptors(const Plan &p, double *moments, double *overlap
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t Path<T>::direct_cross(const Plan &pa, const Plan &pb, int gp0, int np, double coef, double *y,
+                                  double *acc, cudaStream_t st) {
+  const int th = pb.n_occ < 128 ? ((pb.n_occ + 31) / 32) * 32 : 128;
+  k_direct_cross<T><<<dim3(np, pa.n_occ), th, 0, st>>>(pa, pb, np, (const cpx<T> *)pa.mdiag,
+                                                       (const cpx<T> *)pb.mdiag, y);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_accum_cross<<<(pa.n_occ * pb.n_occ + 127) / 128, 128, 0, st>>>(pa, pb.n_occ, gp0, np, coef, y, acc);
+  return cudaGetLastError();
+}
+
+template <typename T> cudaError_t Path<T>::sum(int n, const double *x, double *out, cudaStream_t st) {
+  k_sum<<<1, 256, 0, st>>>(n, x, out);
+  return cudaGetLastError();
+}
+
 template <typename T> cudaError_t Path<T>::zero_acc(const Plan &p, cudaStream_t st) {
   k_zero_acc<<<(p.n_occ * p.n_occ + 255) / 256, 256, 0, st>>>(p);
   return cudaGetLastError();

@@ -142,6 +142,11 @@ template <typename T> struct Path {
   static cudaError_t plane_pass(const Plan &p, int ncols, int kernel, int ib, cudaStream_t st);
   // per-orbital density moments [n_occ][6] and pair density overlaps [n_occ][n_occ] (device)
   static cudaError_t descriptors(const Plan &p, double *moments, double *overlap, cudaStream_t st);
+  // opposite-spin direct term of one slab (alpha plan pa, beta plan pb, same slab):
+  // y [slab][na][nb] scratch, acc [na][nb] accumulated
+  static cudaError_t direct_cross(const Plan &pa, const Plan &pb, int gp0, int np, double coef, double *y,
+                                  double *acc, cudaStream_t st);
+  static cudaError_t sum(int n, const double *x, double *out, cudaStream_t st);
   // zero accumulators / final reduction
   static cudaError_t zero_acc(const Plan &p, cudaStream_t st);
   static cudaError_t finish(const Plan &p, cudaStream_t st, StageTimer *tm);

@@ -73,6 +73,7 @@ def load_library():
         "ltmp2_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "ltmp2_set_extrapolation": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double]),
         "ltmp2_set_route": (ctypes.c_int, [vp, ctypes.c_int]),
+        "ltmp2_energy_uhf": (ctypes.c_int, [vp, vp, ctypes.c_int, dp, dp, dp, dp, dp]),
         "ltmp2_level_energies": (ctypes.c_int, [vp, dp, P(ctypes.c_int), dp, dp]),
         "ltmp2_extrapolate": (ctypes.c_int, [ctypes.c_int, dp, dp, dp, dp, dp]),
     }
@@ -284,6 +285,17 @@ def ltmp2_energy_noalloc(lattice, grid, miller, coeff, eps, n_occ: int, tau, w, 
     _check(f(ctypes.byref(s), len(tau), _dp(tau), _dp(w), _dp(ed), _dp(ex), _dp(ep) if pairs else None,
              ctypes.c_void_p(int(handle) if handle else 0)), "ltmp2_energy_noalloc")
     return float(ed[0]), float(ex[0]), ep
+
+
+# ---------------------------------------------------------------- spin-unrestricted form
+def ltmp2_energy_uhf(alpha: Context, beta: Context, tau, w):
+    """(E_direct, E_exchange, [E_same_alpha, E_same_beta, E_opposite]) of the two channels."""
+    tau = np.ascontiguousarray(np.asarray(tau, dtype=np.float64))
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    ed, ex, es = np.zeros(1), np.zeros(1), np.zeros(3)
+    _check(load_library().ltmp2_energy_uhf(alpha.handle, beta.handle, len(tau), _dp(tau), _dp(w), _dp(ed), _dp(ex),
+                                           _dp(es)), "ltmp2_energy_uhf")
+    return float(ed[0]), float(ex[0]), es
 
 
 # ---------------------------------------------------------------- transformed-state route
