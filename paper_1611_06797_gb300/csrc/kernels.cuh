@@ -840,6 +840,62 @@ __global__ void k_direct(Plan p, int np, const cpx<T> *__restrict__ mdiag, doubl
 // ---------------------------------------------------------------- pair descriptors
 // Per occupied orbital: z_k = (1/N) sum_t |u(t)|^2 exp(2 pi i t_k / n), k = x, y, z
 // (periodic centroid from arg z_k, spread from |z_k|).  out[i][6] = (Re, Im) x 3.
+// Direct term, tiled: block (G' of the slab, 32 x 32 tile of (i, j)); the G sum runs in
+// chunks of 32 staged in shared memory (M_ii for the tile's i, M_jj at -G or conjugated for
+// its j, v(G)).  Each thread owns one j and four i; every 32-term chunk is summed in T and
+// added to a double accumulator, as in k_direct.
+template <typename T>
+__global__ void __launch_bounds__(256) k_direct_tiled(Plan p, int np, const cpx<T> *__restrict__ mdiag,
+                                                      double2 *__restrict__ yd) {
+  constexpr int TC = 32;
+  __shared__ cpx<T> As[TC][TC + 1], Bs[TC][TC + 1];
+  __shared__ T vs[TC];
+  const int gpl = blockIdx.x, i0 = blockIdx.y * TC, j0 = blockIdx.z * TC;
+  const int no = p.n_occ, naux = p.n_aux;
+  const int tx = threadIdx.x % TC, ty = threadIdx.x / TC;   // 32 x 8 threads
+  const int slotA = gpl, slotB = p.real_orb ? gpl : gpl + np;
+  const T *v = vtab<T>(p);
+  const cpx<T> *MA = mdiag + (size_t)slotA * naux * no;
+  const cpx<T> *MB = mdiag + (size_t)slotB * naux * no;
+  double ax[4] = {0, 0, 0, 0}, ay[4] = {0, 0, 0, 0};
+  for (int g0 = 0; g0 < naux; g0 += TC) {
+    for (int e = threadIdx.x; e < TC * TC; e += blockDim.x) {
+      const int gg = e / TC, c = e % TC, g = g0 + gg;
+      cpx<T> a = {T(0), T(0)}, b = {T(0), T(0)};
+      if (g < naux) {
+        if (i0 + c < no) a = MA[(size_t)g * no + i0 + c];
+        if (j0 + c < no) b = p.real_orb ? MB[(size_t)g * no + j0 + c] : MB[(size_t)p.aux_neg[g] * no + j0 + c];
+      }
+      As[gg][c] = a;
+      Bs[gg][c] = b;
+    }
+    if (threadIdx.x < TC) vs[threadIdx.x] = g0 + threadIdx.x < naux ? v[g0 + threadIdx.x] : T(0);
+    __syncthreads();
+    T cx[4] = {T(0), T(0), T(0), T(0)}, cy[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 8
+    for (int gg = 0; gg < TC; ++gg) {
+      const cpx<T> b = Bs[gg][tx];
+      const T vg = vs[gg];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const cpx<T> a = As[gg][ty + 8 * k];
+        const cpx<T> prod = p.real_orb ? cmulconj(a, b) : cmul(a, b);
+        cx[k] += vg * prod.x;
+        cy[k] += vg * prod.y;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { ax[k] += (double)cx[k]; ay[k] += (double)cy[k]; }
+    __syncthreads();
+  }
+  const int j = j0 + tx;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int i = i0 + ty + 8 * k;
+    if (i < no && j < no) yd[((size_t)gpl * no + i) * no + j] = make_double2(ax[k], ay[k]);
+  }
+}
+
 template <typename T> __global__ void k_orb_moments(Plan p, double *__restrict__ out) {
   const int i = blockIdx.x, n = p.n;
   const size_t n3 = (size_t)n * n * n;
