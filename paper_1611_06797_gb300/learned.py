@@ -9,7 +9,8 @@ ascending order of |e^d_ij| while the screened sum of |e^d_ij| stays within the
 accuracy budget, so dropping their exchange could not exceed the budget; the model
 then estimates it.  The model predicts the bounded ratio e^x_ij / (|e^d_ij| / 2),
 clipped to [-1, 1], so its estimate never leaves the bound.  Training labels are the
-exact kernel's pair energies; the all-pairs contraction stays the fallback and judge.
+exact kernel's pair energies; the all-pairs contraction stays the fallback and the
+reference for the estimate's error.
 """
 from __future__ import annotations
 
