@@ -131,3 +131,59 @@ def test_extrapolation_fit_is_the_oracle_fit():
     assert abs(a - ra) < 1e-12 and abs(b - rb) < 1e-9 * abs(rb) and abs(sg - rs) < 1e-9 * rs
     with pytest.raises(L.Ltmp2Error):
         L.ltmp2_extrapolate([1.0, 1.0], [0.0, 1.0])
+
+
+def test_entry_points_reject_null_contexts():
+    """Every context-taking entry point returns INVALID_ARG for a NULL context before it
+    touches a device (so these checks run on any host)."""
+    import ctypes
+    lib = L.load_library()
+    dp = ctypes.POINTER(ctypes.c_double)
+    d = (ctypes.c_double * 4)()
+    i = (ctypes.c_int * 4)()
+    tau = (ctypes.c_double * 1)(1.0)
+    w = (ctypes.c_double * 1)(1.0)
+    null = ctypes.c_void_p(None)
+    calls = {
+        "ltmp2_energy": lambda f: f(null, 1, tau, w, d, d, None),
+        "ltmp2_energy_partial": lambda f: f(null, 1, tau, w, 0, 1, d, d, None, None),
+        "ltmp2_set_slab_size": lambda f: f(null, 1),
+        "ltmp2_set_route": lambda f: f(null, 1),
+        "ltmp2_set_extrapolation": lambda f: f(null, 8, ctypes.c_double(1.05)),
+        "ltmp2_level_energies": lambda f: f(null, d, i, d, d),
+        "ltmp2_energy_uhf": lambda f: f(null, null, 1, tau, w, d, d, None),
+        "ltmp2_set_tuning": lambda f: f(null, i),
+        "ltmp2_get_tuning": lambda f: f(null, i),
+        "ltmp2_set_pair_mask": lambda f: f(null, None),
+        "ltmp2_pair_descriptors": lambda f: f(null, d),
+        "ltmp2_autotune": lambda f: f(null, i, i),
+        "ltmp2_sizes": lambda f: f(null, i, i, i, i),
+        "ltmp2_last_imag": lambda f: f(null, d, d),
+        "ltmp2_set_profiling": lambda f: f(null, 1),
+        "ltmp2_stage_times": lambda f: f(null, 1, d, None),
+        "ltmp2_reset_stage_times": lambda f: f(null),
+        "ltmp2_set_stream": lambda f: f(null, None),
+        "ltmp2_num_primary_gprime": lambda f: f(null),
+    }
+    for name, call in calls.items():
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int
+        assert call(f) == -1, name
+
+
+def test_extrapolate_and_noalloc_validate_on_the_host():
+    import ctypes
+    lib = L.load_library()
+    e = (ctypes.c_double * 2)(5.0, 4.0)
+    y = (ctypes.c_double * 2)(-1.0, -1.1)
+    out = (ctypes.c_double * 1)()
+    f = lib.ltmp2_extrapolate
+    f.restype = ctypes.c_int
+    assert f(1, e, y, out, None, None) == -1                      # fewer than two points
+    assert f(2, None, y, out, None, None) == -1
+    bad = (ctypes.c_double * 2)(5.0, -4.0)
+    assert f(2, bad, y, out, None, None) == -1                    # non-positive cutoff
+    assert f(2, e, y, out, None, None) == 0
+    g = lib.ltmp2_energy_noalloc
+    g.restype = ctypes.c_int
+    assert g(None, 1, None, None, None, None, None, None) == -1
