@@ -50,3 +50,16 @@ def test_bad_slab_and_quadrature_are_rejected():
             L.ltmp2_energy(ctx, np.array(tau, dtype=float), np.array(w, dtype=float))
         assert e.value.name == "INVALID_ARG"
     L.ltmp2_destroy(ctx)
+
+
+def test_gprime_shares_add_up_to_the_energy():
+    """Three ranks' shares of the outer G' loop (evaluated here one after another) add up
+    to the full energy: the split a multi-GPU run of one system would use."""
+    from paper_1611_06797_gb300.shard import energy_share
+    s = solid("cfg1")
+    tau, w = sinc_laplace_quadrature(4, *denominator_range(OracleSystem.from_solid(s)))
+    ctx = L.setup_from_solid(s, precision=L.FP64, real=True)
+    ed, ex, _ = L.ltmp2_energy(ctx, tau, w)
+    parts = [energy_share(ctx, tau, w, r, 3) for r in range(3)]
+    L.ltmp2_destroy(ctx)
+    assert abs(sum(p[0] for p in parts) - ed) < 1e-12 and abs(sum(p[1] for p in parts) - ex) < 1e-12
