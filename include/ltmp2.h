@@ -244,6 +244,17 @@ int ltmp2_mlp_train(ltmp2_mlp *net, const float *X, const float *y, int n, int e
 int ltmp2_mlp_predict(const ltmp2_mlp *net, const float *X, int n, float *y);
 void ltmp2_mlp_destroy(ltmp2_mlp *net);
 
+/* ---------------------------------------------------------------- failure-path self-test
+ * (no counterpart in the paper)  Every device-side wait of this library (the tcgen05
+ * GEMM's mbarrier waits) is bounded: when its budget runs out the kernel raises a device
+ * error word, finishes and returns, and the entry point reports LTMP2_ERR_TIMEOUT; the
+ * context stays usable.  This call exercises that path on demand: one thread waits, with
+ * the same bounded wait, on an mbarrier that nothing ever completes, for budget_us
+ * microseconds (1 .. 10^6).  Returns LTMP2_ERR_TIMEOUT (the expected outcome: the wait
+ * ran out and was reported), LTMP2_OK only if the wait completed (a broken timer), or
+ * INVALID_ARG / OOM / CUDA.                                                           */
+int ltmp2_selftest_wait(ltmp2_ctx *ctx, int budget_us);
+
 /* ---------------------------------------------------------------- spin-unrestricted form
  * Eqs. MP2direct and MP2exchange with the spin sums kept (Sec. II B): alpha and beta
  * electrons occupy different orbital sets.  With <ij|ab> between orbitals of the stated

@@ -165,4 +165,9 @@ cudaError_t tc_wgemm(const TcResources &r, const void *st_in, int rows, void *wt
   return cudaGetLastError();
 }
 
+cudaError_t tc_wait_selftest(int *err, unsigned long long limit_ns, cudaStream_t st) {
+  tc::k_wait_selftest<<<1, 32, 0, st>>>(err, limit_ns);
+  return cudaGetLastError();
+}
+
 }  // namespace ltmp2

@@ -68,13 +68,25 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
-// bounded wait for the phase with this parity; false when WAIT_LIMIT_NS ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// bounded wait for the phase with this parity; false when limit_ns ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long limit_ns = WAIT_LIMIT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
-  while (global_ns() - t0 < WAIT_LIMIT_NS)
+  while (global_ns() - t0 < limit_ns)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+
+// Failure-path self-test: one thread waits, with the same bounded wait the GEMM kernels
+// use, on an mbarrier that nothing ever arrives on; when the budget runs out it raises the
+// same device error word, and the kernel returns.  Nothing hangs or faults.
+__global__ void k_wait_selftest(int *err, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!mbar_wait(&bar, 0, limit_ns)) atomicExch(err, 1);
 }
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
   asm volatile(

@@ -102,6 +102,7 @@ struct ltmp2_ctx {
   // spin-unrestricted pairing (this context as the alpha channel): opposite-spin scratch
   double *d_cross_y = nullptr, *d_cross_acc = nullptr, *d_cross_sum = nullptr;
   int cross_nb = 0;
+  int *d_selftest_err = nullptr;   // error word of the failure-path self-test
   ~ltmp2_ctx() {
     tc_release(tc);
     for (void *q : allocs) cudaFree(q);
@@ -1135,8 +1136,23 @@ int ltmp2_energy_batch(ltmp2_ctx *const *ctxs, int n, const int *n_tau, const do
   return rc;
 }
 
-// ---------------------------------------------------------------- spin-unrestricted form
+// ---------------------------------------------------------------- failure-path self-test
+int ltmp2_selftest_wait(ltmp2_ctx *ctx, int budget_us) {
+  if (!ctx || budget_us < 1 || budget_us > 1000000) return LTMP2_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  int rc;
+  if (!ctx->d_selftest_err && (rc = dalloc(ctx, &ctx->d_selftest_err, 1))) return rc;
+  cudaError_t e = cudaMemsetAsync(ctx->d_selftest_err, 0, sizeof(int), ctx->stream);
+  if (e == cudaSuccess) e = tc_wait_selftest(ctx->d_selftest_err, 1000ull * (unsigned long long)budget_us, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  int flag = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&flag, ctx->d_selftest_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  ctx->kernel_launches += 1;
+  return flag ? LTMP2_ERR_TIMEOUT : LTMP2_OK;
+}
 
+// ---------------------------------------------------------------- spin-unrestricted form
 int ltmp2_energy_uhf(ltmp2_ctx *alpha, ltmp2_ctx *beta, int n_tau, const double *tau, const double *w,
                      double *e_direct, double *e_exchange, double *e_spin) {
   if (!alpha || !beta || alpha == beta || !e_direct || !e_exchange) return LTMP2_ERR_INVALID_ARG;

@@ -22,6 +22,8 @@ int tc_variant_bn(int variant);
 void tc_release(TcResources &r);
 cudaError_t tc_pack_b(const TcResources &r, const void *pt, cudaStream_t st);
 cudaError_t tc_wgemm(const TcResources &r, const void *st_in, int rows, void *wt, cudaStream_t st);
+// one bounded wait on an mbarrier that never completes (failure-path self-test)
+cudaError_t tc_wait_selftest(int *err, unsigned long long limit_ns, cudaStream_t st);
 
 // One column of a plane-wave sphere at fixed (m1, m2): m3 runs over [zlo, zhi].
 // Columns are stored in order; the sphere's points follow column by column

@@ -74,6 +74,7 @@ def load_library():
         "ltmp2_set_extrapolation": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double]),
         "ltmp2_set_route": (ctypes.c_int, [vp, ctypes.c_int]),
         "ltmp2_energy_uhf": (ctypes.c_int, [vp, vp, ctypes.c_int, dp, dp, dp, dp, dp]),
+        "ltmp2_selftest_wait": (ctypes.c_int, [vp, ctypes.c_int]),
         "ltmp2_level_energies": (ctypes.c_int, [vp, dp, P(ctypes.c_int), dp, dp]),
         "ltmp2_extrapolate": (ctypes.c_int, [ctypes.c_int, dp, dp, dp, dp, dp]),
     }
@@ -285,6 +286,13 @@ def ltmp2_energy_noalloc(lattice, grid, miller, coeff, eps, n_occ: int, tau, w, 
     _check(f(ctypes.byref(s), len(tau), _dp(tau), _dp(w), _dp(ed), _dp(ex), _dp(ep) if pairs else None,
              ctypes.c_void_p(int(handle) if handle else 0)), "ltmp2_energy_noalloc")
     return float(ed[0]), float(ex[0]), ep
+
+
+# ---------------------------------------------------------------- failure-path self-test
+def ltmp2_selftest_wait(ctx: Context, budget_us: int) -> int:
+    """Status of one bounded device wait on a barrier that never completes (expected:
+    the TIMEOUT code, -7)."""
+    return int(load_library().ltmp2_selftest_wait(ctx.handle, int(budget_us)))
 
 
 # ---------------------------------------------------------------- spin-unrestricted form

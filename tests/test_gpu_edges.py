@@ -63,3 +63,20 @@ def test_gprime_shares_add_up_to_the_energy():
     parts = [energy_share(ctx, tau, w, r, 3) for r in range(3)]
     L.ltmp2_destroy(ctx)
     assert abs(sum(p[0] for p in parts) - ed) < 1e-12 and abs(sum(p[1] for p in parts) - ex) < 1e-12
+
+
+def test_bounded_wait_runs_out_and_is_reported():
+    """A device wait on a barrier nothing completes runs out after its budget, raises the
+    error word and the library reports TIMEOUT; the context stays usable afterwards."""
+    import time
+    s = solid("tiny2")
+    tau, w = sinc_laplace_quadrature(3, *denominator_range(OracleSystem.from_solid(s)))
+    ctx = L.setup_from_solid(s, precision=L.FP32, real=True)
+    e0 = L.ltmp2_energy(ctx, tau, w)
+    t0 = time.perf_counter()
+    assert L.ltmp2_selftest_wait(ctx, 20000) == -7          # LTMP2_ERR_TIMEOUT after 20 ms
+    assert time.perf_counter() - t0 >= 0.019
+    assert L.ltmp2_selftest_wait(ctx, 0) == -1
+    e1 = L.ltmp2_energy(ctx, tau, w)
+    L.ltmp2_destroy(ctx)
+    assert e1[0] == e0[0] and e1[1] == e0[1]
