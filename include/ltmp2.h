@@ -3,7 +3,11 @@
  *
  * Method: Schaefer, Ramberger, Kresse, "Quartic scaling MP2 for solids: a highly
  * parallelized algorithm in the plane wave basis" (arXiv:1611.06797).  Gamma
- * point, closed shell, spin restricted (Sec. II B: sum over spins -> 2).
+ * point; closed shell, spin restricted (Sec. II B: sum over spins -> 2), with a
+ * spin-unrestricted pairing of two contexts (ltmp2_energy_uhf).  Beside the
+ * Green's-function route below, the paper's own stored-overlap-density route
+ * (ltmp2_set_route) and its internal auxiliary-cutoff extrapolation
+ * (ltmp2_set_extrapolation) are available.
  *
  * For each Laplace point tau (Eq. SCHLT) the library builds the tau-scaled
  * virtual Green's function P_v(tau) = sum_a |a> e^{-(e_a - mu) tau} <a| in the
