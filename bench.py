@@ -242,7 +242,7 @@ def main():
     ap.add_argument("--route", default="green", choices=["green", "overlap"],
                     help="transformed states from the per-tau Green's function (default) or from stored "
                          "overlap densities (the paper's steps (i)-(iii))")
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "batch", "learned", "cfg3", "uhf"],
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "batch", "learned", "cfg3", "uhf", "fftcmp"],
                     help="cfg2: the 16-well 24^3 system; batch: 8 uneven systems in one graph launch; "
                          "learned: surrogate-screened pairs; cfg3: precision form on the 64-well 36^3 system")
     args = ap.parse_args()
@@ -265,6 +265,9 @@ def main():
         return
     if args.workload == "uhf" and args.impl == "ours":
         run_uhf(args, local)
+        return
+    if args.workload == "fftcmp" and args.impl == "ours":
+        run_fftcmp(args, local)
         return
     from synth import SPECS
     spec = SPECS[WORKLOAD]
@@ -800,6 +803,54 @@ def run_uhf(args, local):
                                "E_x": abs(r32["result"][1] - ex) * per_atom,
                                "E": abs(r32["result"][0] + r32["result"][1] - ed - ex) * per_atom}}},
     }
+    print(json.dumps(out), flush=True)
+
+
+def run_fftcmp(args, local):
+    """cuFFT, timed only as a comparison: batched complex 3D FFTs of the co-density size
+    (torch.fft.fftn, inputs larger than L2), scaled to the number of co-density transforms
+    one Laplace point needs on the 24^3 workload (one per (G', j, i) item), against the
+    library's plane + column stages, which also form the products conj(phi_i) w_j, prune to
+    the auxiliary sphere and contract.  Both precisions."""
+    import torch
+    import paper_1611_06797_gb300 as L
+    from synth import SPECS, build_model_solid
+    spec = SPECS["cfg2"]
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    s = build_model_solid(spec)
+    tau, w, _ = L.ltmp2_laplace_grid(s.gap, s.width, spec.n_tau)
+    n = spec.grid
+    out = {"metric": "cuFFT comparison", "config": {"workload": _workload_desc(spec)}, "results": {}}
+    for prec, dt in ((L.FP32, torch.complex64), (L.FP64, torch.complex128)):
+        ctx = L.setup_from_solid(s, precision=prec, real=True)
+        L.ltmp2_set_profiling(ctx, True)
+        L.ltmp2_energy(ctx, tau[:1], w[:1], pairs=False)
+        L.ltmp2_reset_stage_times(ctx)
+        L.ltmp2_energy(ctx, tau[:2], w[:2], pairs=False)
+        st = L.ltmp2_stage_times(ctx)
+        items = L.ltmp2_num_primary_gprime(ctx) * s.n_occ * s.n_occ
+        L.ltmp2_destroy(ctx)
+        ours = (st["plane_fft"]["ms"] + st["column_fft_contract"]["ms"]) / 2
+        batch = 1024 if prec == L.FP32 else 512   # 113 MB in, 113 MB out: above the L2
+        x = torch.randn(batch, n, n, n, dtype=dt, device=dev)
+        for _ in range(3):
+            y = torch.fft.fftn(x, dim=(1, 2, 3))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        reps = 5
+        for _ in range(reps):
+            y = torch.fft.fftn(x, dim=(1, 2, 3))
+        b.record()
+        torch.cuda.synchronize()
+        per_fft_ms = a.elapsed_time(b) / reps / batch
+        del x, y
+        out["results"]["fp32" if prec == L.FP32 else "fp64"] = {
+            "cufft_ms_per_fft": per_fft_ms, "ffts_per_tau": items,
+            "cufft_transforms_only_ms_per_tau": per_fft_ms * items,
+            "ours_plane_plus_column_ms_per_tau": ours,
+            "ratio_cufft_over_ours": per_fft_ms * items / ours}
     print(json.dumps(out), flush=True)
 
 
