@@ -851,6 +851,39 @@ def run_fftcmp(args, local):
             "cufft_transforms_only_ms_per_tau": per_fft_ms * items,
             "ours_plane_plus_column_ms_per_tau": ours,
             "ratio_cufft_over_ours": per_fft_ms * items / ours}
+    # cuBLAS on the transformed-state product of one full slab (4096 complex columns =
+    # 8192 stacked real rows times the real n_pw x n_pw Green's function), against the
+    # library's kernel for the same launch (bench stage time per launch)
+    npw = s.n_pw
+    rows = 2 * 128 * s.n_occ
+    torch.backends.cuda.matmul.allow_tf32 = False
+    for prec, dt in ((L.FP64, torch.float64), (L.FP32, torch.float32)):
+        A = torch.randn(rows, npw, dtype=dt, device=dev)
+        B = torch.randn(npw, npw, dtype=dt, device=dev)
+        for _ in range(3):
+            C = A @ B
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(5):
+            C = A @ B
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 5
+        ctx = L.setup_from_solid(s, precision=prec, real=True)
+        L.ltmp2_set_profiling(ctx, True)
+        L.ltmp2_energy(ctx, tau[:1], w[:1], pairs=False)
+        L.ltmp2_reset_stage_times(ctx)
+        L.ltmp2_energy(ctx, tau[:1], w[:1], pairs=False)
+        st = L.ltmp2_stage_times(ctx)["w_gemm"]
+        L.ltmp2_destroy(ctx)
+        key = "gemm_fp64" if prec == L.FP64 else "gemm_fp32"
+        out["results"][key] = {
+            "shape": [rows, npw, npw], "cublas": "DGEMM" if prec == L.FP64 else "SGEMM (TF32 off)",
+            "cublas_ms": ms, "cublas_tflops": 2.0 * rows * npw * npw / ms / 1e9,
+            "ours_ms_per_launch": st["ms"] / max(1, st["launches"]),
+            "ours": "k_rgemm FP64 (SIMT)" if prec == L.FP64 else "tcgen05 3xTF32 (k_tc_cgemm_stacked + packing)"}
+        del A, B, C
     print(json.dumps(out), flush=True)
 
 
