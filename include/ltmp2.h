@@ -356,6 +356,21 @@ int ltmp2_reset_stage_times(ltmp2_ctx *ctx);
 /* Cumulative number of this library's kernel launches made for ctx (all calls). */
 int ltmp2_kernel_launches(const ltmp2_ctx *ctx, long long *count);
 
+/* 64-bit hash of every input that determines the energies of ctx: lattice, grid,
+ * plane-wave set, coefficients, eigenvalues, n_occ, the resolved E_aux, precision and
+ * flags (the paper has no counterpart; checkpoint files are keyed by it).  Two set-ups
+ * of the same inputs give the same value.  Errors: INVALID_ARG.                      */
+int ltmp2_fingerprint(const ltmp2_ctx *ctx, unsigned long long *out);
+
+/* Fixed-order FP64 sum of the results of n ltmp2_energy_partial calls over disjoint G'
+ * ranges (Sec. III B: the pieces are additive), chunk 0 first, so that a checkpointed
+ * and resumed evaluation sums exactly as an uninterrupted one.
+ *   e [n][2] (E_d, E_x per chunk); pd, px: NULL or [n][n_occ][n_occ] pair energies.
+ *   e_out [2]; pd_out, px_out: NULL or [n_occ][n_occ].  Host arithmetic only.
+ * Errors: INVALID_ARG (sizes, NULL where outputs are asked for, non-finite totals). */
+int ltmp2_sum_partials(int n, int n_occ, const double *e, const double *pd, const double *px, double *e_out,
+                       double *pd_out, double *px_out);
+
 /* ltmp2_setup + ltmp2_energy in one call that makes no device allocation (the paper
  * has no counterpart; this serves callers that cannot call cudaMalloc: a process whose
  * device-memory budget is already held by its own pool, code that must not trigger
@@ -371,11 +386,14 @@ int ltmp2_kernel_launches(const ltmp2_ctx *ctx, long long *count);
  * In LTMP2_FP32 the transformed-state GEMM runs on the CUDA cores, as it does in
  * ltmp2_energy with LTMP2_FLAG_SIMT_GEMM (so that flag is not accepted here).
  * The first call on a device looks up the array's device address and uploads the FFT
- * tables; make that first call before any stream capture.  Every call reuses the same
- * array (the previous call's contents stay until overwritten; the accumulators are
- * cleared by each call), so calls whose GPU work overlaps, from any thread or stream,
- * race and must be serialised by the caller.  The call returns after the results
- * are on the host.  Errors: as ltmp2_setup and ltmp2_energy, plus UNSUPPORTED.       */
+ * tables; make that first call before any stream capture.  The address is cached per
+ * device, so calls after a cudaDeviceReset of that device are not supported.  Every
+ * call reuses the same array (the previous call's contents stay until overwritten; the
+ * accumulators are cleared by each call), so calls whose GPU work overlaps, from any
+ * thread or stream, race and must be serialised by the caller.  The call returns after
+ * the results are on the host.  Input validation is ltmp2_setup's (the same checks,
+ * the orthonormality sample included).  Errors: as ltmp2_setup and ltmp2_energy, plus
+ * UNSUPPORTED.                                                                       */
 int ltmp2_energy_noalloc(const ltmp2_system *sys, int n_tau, const double *tau, const double *w,
                          double *e_direct, double *e_exchange, double *e_pair, void *stream);
 

@@ -40,10 +40,10 @@ int make_map(CUtensorMap *m, float *base, int rows, int kpad, int box_rows, int 
 }
 }  // namespace
 
-// Variants: 0-3 single-pass accumulators (tile N 128/64, 1-4 regions, for tests of the
-// accumulation drift), 4 drained (N 64, two-stage ring), 5 stacked Re/Im rows with a
-// six-stage 64-byte-swizzle ring (the default).
-int tc_variant_bn(int variant) { return variant <= 1 ? 128 : (variant == 5 ? tc::S_BN : 64); }
+// Layouts the autotuner chooses from: 4 drained (separate Re / Im operands, N 64, two-stage
+// ring), 5 stacked Re / Im rows with a three-stage 64-byte-swizzle ring (the default and
+// the only layout for real orbitals).
+int tc_variant_bn(int variant) { return variant == 5 ? tc::S_BN : 64; }
 
 int tc_kpad(int npw) { return ((2 * npw + tc::BK - 1) / tc::BK) * tc::BK; }
 
@@ -55,6 +55,7 @@ size_t tc_bytes(int rows_cap, int npw) {
 }
 
 cudaError_t tc_init(TcResources &r, void *mem, int rows_cap, int npw, int variant, bool real) {
+  if (variant != 4 && variant != 5) return cudaErrorInvalidValue;
   if (real && variant != 5) return cudaErrorInvalidValue;  // only the stacked kernel has a real form
   r.variant = variant;
   r.real = real;
@@ -88,17 +89,7 @@ cudaError_t tc_init(TcResources &r, void *mem, int rows_cap, int npw, int varian
     return cudaErrorInvalidValue;
   }
   r.maps = mp;
-  cudaError_t e;
-#define LTMP2_TC_ATTR(BN, NR)                                                                  \
-  e = cudaFuncSetAttribute(tc::k_tc_cgemm<BN, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                           tc::TcCfg<BN, NR>::SMEM_BYTES);                                     \
-  if (e != cudaSuccess) return e;
-  LTMP2_TC_ATTR(128, 1)
-  LTMP2_TC_ATTR(128, 2)
-  LTMP2_TC_ATTR(64, 2)
-  LTMP2_TC_ATTR(64, 4)
-#undef LTMP2_TC_ATTR
-  e = cudaFuncSetAttribute(tc::k_tc_cgemm_drain<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(tc::k_tc_cgemm_drain<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            tc::TcCfg<64, 2>::SMEM_BYTES);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(tc::k_tc_cgemm_stacked, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::S_SMEM);
@@ -144,24 +135,10 @@ cudaError_t tc_wgemm(const TcResources &r, const void *st_in, int rows, void *wt
   tc::k_pack_a<<<dim3((r.kpad / 2 + 255) / 256, rows), 256, 0, st>>>(static_cast<const float2 *>(st_in), rows,
                                                                        r.npw, r.kpad, r.a1h, r.a1l, r.a2h, r.a2l);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-#define LTMP2_TC_LAUNCH(BN, NR)                                                                              \
-  {                                                                                                          \
-    dim3 grid((r.npw + BN - 1) / BN, (rows + tc::BM - 1) / tc::BM);                                          \
-    tc::k_tc_cgemm<BN, NR><<<grid, 128, tc::TcCfg<BN, NR>::SMEM_BYTES, st>>>(                                \
-        m.a1h, m.a1l, m.a2h, m.a2l, m.bh, m.bl, rows, r.npw, r.kpad / tc::BK, static_cast<float2 *>(wt), r.npw, \
-        r.err);                                                                                              \
-  }
-  if (variant == 0) LTMP2_TC_LAUNCH(128, 1)
-  else if (variant == 1) LTMP2_TC_LAUNCH(128, 2)
-  else if (variant == 2) LTMP2_TC_LAUNCH(64, 2)
-  else if (variant == 3) LTMP2_TC_LAUNCH(64, 4)
-  else {
-    dim3 grid((r.npw + 63) / 64, (rows + tc::BM - 1) / tc::BM);
-    tc::k_tc_cgemm_drain<64><<<grid, 160, tc::TcCfg<64, 2>::SMEM_BYTES, st>>>(
-        m.a1h, m.a1l, m.a2h, m.a2l, m.bh, m.bl, rows, r.npw, r.kpad / tc::BK, static_cast<float2 *>(wt), r.npw,
-        r.err);
-  }
-#undef LTMP2_TC_LAUNCH
+  dim3 grid((r.npw + 63) / 64, (rows + tc::BM - 1) / tc::BM);
+  tc::k_tc_cgemm_drain<64><<<grid, 160, tc::TcCfg<64, 2>::SMEM_BYTES, st>>>(
+      m.a1h, m.a1l, m.a2h, m.a2l, m.bh, m.bl, rows, r.npw, r.kpad / tc::BK, static_cast<float2 *>(wt), r.npw,
+      r.err);
   return cudaGetLastError();
 }
 

@@ -11,10 +11,12 @@
 // Each operand x is split as x_hi = tf32(x), x_lo = tf32(x - x_hi) (round to nearest),
 // and every product is x_hi y_hi + x_hi y_lo + x_lo y_hi, accumulated in FP32 in tensor
 // memory.  Operands arrive by TMA into a shared-memory ring; one thread issues the TMA
-// copies and the MMAs; four warps read the accumulators.  The production kernel is
-// k_tc_cgemm_stacked (end of file); the earlier variants stay for the accumulation-drift
-// measurements.  Every wait is bounded: on expiry the kernel raises an error flag instead
-// of hanging.
+// copies and the MMAs; four warps read the accumulators.  Two layouts, both chosen
+// between by the autotuner: k_tc_cgemm_drain (separate Re / Im operands, N = 64) and
+// k_tc_cgemm_stacked (Re / Im rows stacked in one MMA tile; the default, and the only
+// one for real orbitals).  Every wait is bounded: on expiry the kernel raises an error
+// flag, waits (bounded) for the TMA copies it issued, writes no output, frees its
+// tensor memory and returns, instead of hanging.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -27,10 +29,10 @@ constexpr int BM = 128;             // rows of A per tile (complex rows of W^T)
 constexpr int BK = 32;              // fp32 elements per k block = one 128-byte swizzle row
 constexpr int A_TILE_BYTES = BM * 128;
 constexpr int STAGES = 2;
-// Tile of BN columns with NREG accumulator pairs (Re, Im) in tensor memory.  Consecutive
-// 8-wide k steps go round-robin to the NREG pairs, which the epilogue sums in FP32: the
-// tensor core's internal accumulation is not round-to-nearest, and a single chain over
-// K' ~ 6000 drifted by ~1e-4 (relative) on the transformed states.
+// Tile of BN columns with NREG accumulator pairs (Re, Im) in tensor memory.  The tensor
+// core's internal accumulation is not round-to-nearest: a single chain over K' ~ 6000
+// drifted by ~1e-4 (relative) on the transformed states, so the kernels below drain every
+// k block's partial into FP32 register sums.
 template <int BN, int NREG> struct TcCfg {
   static constexpr int B_TILE_BYTES = BN * 128;
   static constexpr int STAGE_BYTES = 4 * A_TILE_BYTES + 2 * B_TILE_BYTES;
@@ -195,123 +197,15 @@ __global__ void k_pack_b(const float2 *__restrict__ pt, int npw, int kpad, float
   }
 }
 
-// ---------------------------------------------------------------- the GEMM
 struct TcMaps {
   CUtensorMap a1h, a1l, a2h, a2l, bh, bl;
 };
 
-template <int BN, int NREG>
-__global__ void __launch_bounds__(128, 1)
-    k_tc_cgemm(const __grid_constant__ CUtensorMap ta1h, const __grid_constant__ CUtensorMap ta1l,
-               const __grid_constant__ CUtensorMap ta2h, const __grid_constant__ CUtensorMap ta2l,
-               const __grid_constant__ CUtensorMap tbh, const __grid_constant__ CUtensorMap tbl, int M, int N,
-               int kblocks, float2 *__restrict__ C, int ldc, int *__restrict__ err) {
-  using Cfg = TcCfg<BN, NREG>;
-  extern __shared__ unsigned char smem_raw[];
-  __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
-  __shared__ uint32_t tmem_slot;
-  unsigned char *smem = reinterpret_cast<unsigned char *>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-
-  if (warp == 0) tmem_alloc(&tmem_slot, Cfg::TMEM_COLS);
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
-    }
-    mbar_init(&done_bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = tmem_slot;
-
-  bool ok = true;
-  if (threadIdx.x == 0) {
-    auto issue = [&](int kb, int s) {
-      unsigned char *st = smem + s * Cfg::STAGE_BYTES;
-      mbar_expect_tx(&full_bar[s], Cfg::STAGE_BYTES);
-      const int x = kb * BK;
-      tma_load_2d(st + 0 * A_TILE_BYTES, &ta1h, &full_bar[s], x, m0);
-      tma_load_2d(st + 1 * A_TILE_BYTES, &ta1l, &full_bar[s], x, m0);
-      tma_load_2d(st + 2 * A_TILE_BYTES, &ta2h, &full_bar[s], x, m0);
-      tma_load_2d(st + 3 * A_TILE_BYTES, &ta2l, &full_bar[s], x, m0);
-      tma_load_2d(st + 4 * A_TILE_BYTES, &tbh, &full_bar[s], x, n0);
-      tma_load_2d(st + 4 * A_TILE_BYTES + Cfg::B_TILE_BYTES, &tbl, &full_bar[s], x, n0);
-    };
-    // Stage s holds k block kb; the other stage already holds kb + 1.  MMAs of kb are
-    // queued before waiting for those of kb - 1, whose stage then takes kb + 1.
-    for (int s = 0; s < STAGES && s < kblocks; ++s) issue(s, s);
-    for (int kb = 0; kb < kblocks; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
-      if (!mbar_wait(&full_bar[s], ph)) { ok = false; break; }
-      fence_after();
-      const uint32_t base = smem_u32(smem + s * Cfg::STAGE_BYTES);
-#pragma unroll
-      for (int k = 0; k < BK / 8; ++k) {
-        const uint32_t ko = k * 32;  // 8 tf32 elements = 32 bytes along K
-        const uint64_t a1h = sdesc_sw128(base + 0 * A_TILE_BYTES + ko);
-        const uint64_t a1l = sdesc_sw128(base + 1 * A_TILE_BYTES + ko);
-        const uint64_t a2h = sdesc_sw128(base + 2 * A_TILE_BYTES + ko);
-        const uint64_t a2l = sdesc_sw128(base + 3 * A_TILE_BYTES + ko);
-        const uint64_t bh = sdesc_sw128(base + 4 * A_TILE_BYTES + ko);
-        const uint64_t bl = sdesc_sw128(base + 4 * A_TILE_BYTES + Cfg::B_TILE_BYTES + ko);
-        const int step = kb * (BK / 8) + k;
-        const uint32_t reg = (uint32_t)(step % NREG) * (2 * BN);
-        const uint32_t first = (step >= NREG) ? 1u : 0u;
-        mma_tf32(tmem + reg, a1h, bh, Cfg::IDESC, first);
-        mma_tf32(tmem + reg, a1h, bl, Cfg::IDESC, 1u);
-        mma_tf32(tmem + reg, a1l, bh, Cfg::IDESC, 1u);
-        mma_tf32(tmem + reg + BN, a2h, bh, Cfg::IDESC, first);
-        mma_tf32(tmem + reg + BN, a2h, bl, Cfg::IDESC, 1u);
-        mma_tf32(tmem + reg + BN, a2l, bh, Cfg::IDESC, 1u);
-      }
-      mma_commit(&empty_bar[s]);
-      if (kb >= 1 && kb + 1 < kblocks) {
-        const int sp = (kb - 1) % STAGES;
-        if (!mbar_wait(&empty_bar[sp], (uint32_t)(((kb - 1) / STAGES) & 1))) { ok = false; break; }
-        issue(kb + 1, sp);
-      }
-    }
-    mma_commit(&done_bar);
-  }
-  const bool done_ok = mbar_wait(&done_bar, 0);
-  if ((!ok || !done_ok) && lane == 0) atomicExch(err, 1);
-  fence_after();
-  // epilogue: lane r of warp w holds row 32 w + r of every accumulator
-  const int row = warp * 32 + lane;
-  const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
-  const int nsteps = kblocks * (BK / 8);
-#pragma unroll 1
-  for (int c = 0; c < BN / 32; ++c) {
-    float re[32], im[32], tr[32], ti[32];
-    tmem_ld32(t_lane + c * 32, re);
-    tmem_ld32(t_lane + BN + c * 32, im);
-#pragma unroll 1
-    for (int r = 1; r < NREG; ++r) {
-      tmem_ld32(t_lane + r * 2 * BN + c * 32, tr);
-      tmem_ld32(t_lane + r * 2 * BN + BN + c * 32, ti);
-      if (r < nsteps) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) { re[j] += tr[j]; im[j] += ti[j]; }
-      }
-    }
-    const int gm = m0 + row;
-    if (done_ok && gm < M) {
-      float2 *dst = C + (size_t)gm * ldc + n0 + c * 32;
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (n0 + c * 32 + j < N) dst[j] = make_float2(re[j], im[j]);
-    }
-  }
-  fence_before();
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
+// After a failed wait the producer still owns the TMA copies it issued for k blocks
+// [consumed, issued): wait for each (bounded) before the CTA leaves or reuses the ring.
+template <int NSTAGES>
+__device__ __forceinline__ void drain_issued(uint64_t *full_bar, int consumed, int issued) {
+  for (int kb = consumed; kb < issued; ++kb) mbar_wait(&full_bar[kb % NSTAGES], (uint32_t)((kb / NSTAGES) & 1));
 }
 
 // ---------------------------------------------------------------- drained variant
@@ -334,6 +228,7 @@ __global__ void __launch_bounds__(160, 1)
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2], done_bar;
   __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;   // any bounded wait of the CTA ran out: no output is written
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -341,6 +236,7 @@ __global__ void __launch_bounds__(160, 1)
 
   if (warp == 0) tmem_alloc(&tmem_slot, Cfg::TMEM_COLS);
   if (threadIdx.x == 0) {
+    s_fail = 0;
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
@@ -358,6 +254,9 @@ __global__ void __launch_bounds__(160, 1)
   fence_after();
   const uint32_t tmem = tmem_slot;
   bool ok = true;
+  float sr[BN], si[BN];   // epilogue warps: the tile row's Re / Im sums
+#pragma unroll
+  for (int j = 0; j < BN; ++j) { sr[j] = 0.f; si[j] = 0.f; }
 
   if (warp == 4) {
     if (lane == 0) {
@@ -372,10 +271,12 @@ __global__ void __launch_bounds__(160, 1)
         tma_load_2d(st + 4 * A_TILE_BYTES, &tbh, &full_bar[s], x, n0);
         tma_load_2d(st + 4 * A_TILE_BYTES + Cfg::B_TILE_BYTES, &tbl, &full_bar[s], x, n0);
       };
-      for (int s = 0; s < STAGES && s < kblocks; ++s) issue(s, s);
+      int issued = 0, consumed = 0;
+      for (int s = 0; s < STAGES && s < kblocks; ++s) issue(s, s), issued = s + 1;
       for (int kb = 0; kb < kblocks; ++kb) {
         const int s = kb % STAGES, r = kb & 1;
         if (!mbar_wait(&full_bar[s], (uint32_t)((kb / STAGES) & 1))) { ok = false; break; }
+        consumed = kb + 1;
         if (kb >= 2 && !mbar_wait(&acce_bar[r], (uint32_t)(((kb - 2) >> 1) & 1))) { ok = false; break; }
         fence_after();
         const uint32_t base = smem_u32(smem + s * Cfg::STAGE_BYTES);
@@ -403,16 +304,18 @@ __global__ void __launch_bounds__(160, 1)
           const int sp = (kb - 1) % STAGES;
           if (!mbar_wait(&empty_bar[sp], (uint32_t)(((kb - 1) / STAGES) & 1))) { ok = false; break; }
           issue(kb + 1, sp);
+          issued = kb + 2;
         }
       }
       mma_commit(&done_bar);
-      if (!ok) atomicExch(err, 1);
+      if (!ok) {
+        s_fail = 1;
+        atomicExch(err, 1);
+        drain_issued<STAGES>(full_bar, consumed, issued);
+      }
     }
   } else {
     // epilogue warps: drain every k block's partial into FP32 register sums
-    float sr[BN], si[BN];
-#pragma unroll
-    for (int j = 0; j < BN; ++j) { sr[j] = 0.f; si[j] = 0.f; }
     const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
     for (int kb = 0; kb < kblocks; ++kb) {
       const int r = kb & 1;
@@ -431,20 +334,28 @@ __global__ void __launch_bounds__(160, 1)
       fence_before();
       mbar_arrive(&acce_bar[r]);
     }
-    if (!ok && lane == 0) atomicExch(err, 1);
+    if (!ok) {
+      s_fail = 1;
+      if (lane == 0) atomicExch(err, 1);
+    }
+  }
+  const bool done_ok = mbar_wait(&done_bar, 0);
+  if (!done_ok) {
+    s_fail = 1;
+    if (lane == 0) atomicExch(err, 1);
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp < 4 && !s_fail) {
     const int gm = m0 + warp * 32 + lane;
-    if (ok && gm < M) {
+    if (gm < M) {
       float2 *dst = C + (size_t)gm * ldc + n0;
 #pragma unroll
       for (int j = 0; j < BN; ++j)
         if (n0 + j < N) dst[j] = make_float2(sr[j], si[j]);
     }
   }
-  const bool done_ok = mbar_wait(&done_bar, 0);
-  if (!done_ok && lane == 0) atomicExch(err, 1);
-  fence_before();
-  __syncthreads();
-  fence_after();
   if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
 
@@ -547,6 +458,7 @@ __global__ void __launch_bounds__(160, 2)
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t full_bar[S_STAGES], empty_bar[S_STAGES], accf_bar[2], acce_bar[2], done_bar;
   __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;   // any bounded wait of the CTA ran out: no output is written
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -557,6 +469,7 @@ __global__ void __launch_bounds__(160, 2)
 
   if (warp == 0) tmem_alloc(&tmem_slot, S_TMEM_COLS);
   if (threadIdx.x == 0) {
+    s_fail = 0;
     for (int s = 0; s < S_STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
@@ -574,6 +487,9 @@ __global__ void __launch_bounds__(160, 2)
   fence_after();
   const uint32_t tmem = tmem_slot;
   bool ok = true;
+  float sum[S_BN];   // epilogue warps: the lane's row of the tile
+#pragma unroll
+  for (int j = 0; j < S_BN; ++j) sum[j] = 0.f;
 
   if (warp == 4) {
     if (lane == 0) {
@@ -586,11 +502,13 @@ __global__ void __launch_bounds__(160, 2)
         tma_load_2d(st + 2 * S_TILE, &tbh, &full_bar[s], x, n0);
         tma_load_2d(st + 3 * S_TILE, &tbl, &full_bar[s], x, n0);
       };
-      for (int s = 0; s < S_STAGES && s < kblocks; ++s) issue(s, s);
+      int issued = 0, consumed = 0;
+      for (int s = 0; s < S_STAGES && s < kblocks; ++s) issue(s, s), issued = s + 1;
       for (int kb = 0; kb < kblocks; ++kb) {
         const int s = kb % S_STAGES;
         const int db = kb / S_DRAIN, r = db & 1;
         if (!mbar_wait(&full_bar[s], (uint32_t)((kb / S_STAGES) & 1))) { ok = false; break; }
+        consumed = kb + 1;
         if (kb % S_DRAIN == 0 && db >= 2 && !mbar_wait(&acce_bar[r], (uint32_t)(((db - 2) >> 1) & 1))) {
           ok = false;
           break;
@@ -615,15 +533,17 @@ __global__ void __launch_bounds__(160, 2)
           const int sp = (kb - 1) % S_STAGES;
           if (!mbar_wait(&empty_bar[sp], (uint32_t)(((kb - 1) / S_STAGES) & 1))) { ok = false; break; }
           issue(kb - 1 + S_STAGES, sp);
+          issued = kb - 1 + S_STAGES + 1;
         }
       }
       mma_commit(&done_bar);
-      if (!ok) atomicExch(err, 1);
+      if (!ok) {
+        s_fail = 1;
+        atomicExch(err, 1);
+        drain_issued<S_STAGES>(full_bar, consumed, issued);
+      }
     }
   } else {
-    float sum[S_BN];
-#pragma unroll
-    for (int j = 0; j < S_BN; ++j) sum[j] = 0.f;
     const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
     for (int db = 0; db < ndrain; ++db) {
       const int r = db & 1;
@@ -645,10 +565,21 @@ __global__ void __launch_bounds__(160, 2)
       fence_before();
       mbar_arrive(&acce_bar[r]);
     }
-    if (!ok && lane == 0) atomicExch(err, 1);
-    // pair Re (warps 0, 1) with Im (warps 2, 3) through shared memory: the ring is idle
-    const bool done_ok = mbar_wait(&done_bar, 0);
-    if (!done_ok && lane == 0) atomicExch(err, 1);
+    if (!ok) {
+      s_fail = 1;
+      if (lane == 0) atomicExch(err, 1);
+    }
+    if (!mbar_wait(&done_bar, 0)) {
+      s_fail = 1;
+      if (lane == 0) atomicExch(err, 1);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  // every MMA has completed and every TMA copy has landed unless s_fail is set; only then
+  // is the ring reused as staging: Re (warps 0, 1) paired with Im (warps 2, 3)
+  if (warp < 4 && !s_fail) {
     float *stage = reinterpret_cast<float *>(smem);   // [128][S_BN + 1]
     const int row = warp * 32 + lane;
 #pragma unroll
@@ -657,7 +588,7 @@ __global__ void __launch_bounds__(160, 2)
     for (int e = threadIdx.x; e < 64 * S_BN; e += 128) {
       const int rr = e / S_BN, cc = e % S_BN;
       const int gm = m0 + rr, gn = n0 + cc;
-      if (ok && done_ok && gm < M && gn < N)
+      if (gm < M && gn < N)
         C[(size_t)gm * ldc + gn] = make_float2(stage[rr * (S_BN + 1) + cc], stage[(rr + 64) * (S_BN + 1) + cc]);
     }
   }

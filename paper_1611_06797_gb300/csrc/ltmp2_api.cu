@@ -10,6 +10,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <tuple>
@@ -17,6 +18,7 @@
 
 #include "../../include/ltmp2.h"
 #include "fft.cuh"
+#include "host_plan.h"
 #include "plan.h"
 
 using namespace ltmp2;
@@ -103,6 +105,8 @@ struct ltmp2_ctx {
   double *d_cross_y = nullptr, *d_cross_acc = nullptr, *d_cross_sum = nullptr;
   int cross_nb = 0;
   int *d_selftest_err = nullptr;   // error word of the failure-path self-test
+  unsigned long long fingerprint = 0;  // hash of the set-up inputs (ltmp2_fingerprint)
+  unsigned long long mask_hash = 0;    // hash of the pair mask, 0 = every pair kept
   ~ltmp2_ctx() {
     tc_release(tc);
     for (void *q : allocs) cudaFree(q);
@@ -151,59 +155,6 @@ int dalloc_bytes(ltmp2_ctx *c, void **ptr, size_t bytes) {
   c->allocs.push_back(q);
   *ptr = q;
   return LTMP2_OK;
-}
-
-struct Col {
-  int m1, m2, zlo, zhi, off;
-};
-
-// Group a set of Miller indices into (m1, m2) columns with contiguous m3 ranges.
-// order[k] = original index of the k-th point in column order.  false if a column
-// has a gap.
-bool build_columns(const std::vector<std::array<int, 3>> &m, std::vector<Col> &cols,
-                   std::vector<int> &order) {
-  const int n = (int)m.size();
-  order.resize(n);
-  for (int k = 0; k < n; ++k) order[k] = k;
-  std::sort(order.begin(), order.end(), [&](int a, int b) { return m[a] < m[b]; });
-  cols.clear();
-  for (int k = 0; k < n; ++k) {
-    const auto &q = m[order[k]];
-    if (cols.empty() || cols.back().m1 != q[0] || cols.back().m2 != q[1]) {
-      cols.push_back({q[0], q[1], q[2], q[2], k});
-    } else {
-      if (q[2] != cols.back().zhi + 1) return false;
-      cols.back().zhi = q[2];
-    }
-  }
-  return true;
-}
-
-void reciprocal(const double *A, double B[9], double *omega) {
-  // rows a_i; B rows b_k with a_i . b_k = 2 pi delta_ik: B = 2 pi (A^{-1})^T
-  const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
-                     A[2] * (A[3] * A[7] - A[4] * A[6]);
-  *omega = std::fabs(det);
-  double inv[9];
-  inv[0] = (A[4] * A[8] - A[5] * A[7]) / det;
-  inv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
-  inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
-  inv[3] = (A[5] * A[6] - A[3] * A[8]) / det;
-  inv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
-  inv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
-  inv[6] = (A[3] * A[7] - A[4] * A[6]) / det;
-  inv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
-  inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
-  const double tp = 6.283185307179586476925286766559;
-  for (int k = 0; k < 3; ++k)
-    for (int c = 0; c < 3; ++c) B[k * 3 + c] = tp * inv[c * 3 + k];
-}
-
-double g2_of(const double B[9], int m1, int m2, int m3) {
-  const double gx = m1 * B[0] + m2 * B[3] + m3 * B[6];
-  const double gy = m1 * B[1] + m2 * B[4] + m3 * B[7];
-  const double gz = m1 * B[2] + m2 * B[5] + m3 * B[8];
-  return gx * gx + gy * gy + gz * gz;
 }
 
 template <typename T> struct CT { T x, y; };
@@ -591,194 +542,43 @@ const char *ltmp2_strerror(int code) {
 int ltmp2_setup(const ltmp2_system *sys, ltmp2_ctx **out) {
   if (!sys || !out) return LTMP2_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!sys->miller || !sys->coeff || !sys->eps) return LTMP2_ERR_INVALID_ARG;
-  if (sys->n_pw < 2 || sys->n_orb < 2 || sys->n_occ < 1 || sys->n_occ >= sys->n_orb || sys->n_orb > sys->n_pw)
-    return LTMP2_ERR_INVALID_ARG;
-  if (sys->precision != LTMP2_FP64 && sys->precision != LTMP2_FP32) return LTMP2_ERR_INVALID_ARG;
-  if (sys->flags & ~(LTMP2_FLAG_REAL_ORBITALS | LTMP2_FLAG_SIMT_GEMM)) return LTMP2_ERR_INVALID_ARG;
-  for (int k = 0; k < 9; ++k)
-    if (!std::isfinite(sys->lattice[k])) return LTMP2_ERR_INVALID_ARG;
-  const int n = sys->grid[0];
-  if (sys->grid[1] != n || sys->grid[2] != n || !fft_size_supported(n)) return LTMP2_ERR_GRID;
-  // eigenvalues
-  for (int k = 0; k < sys->n_orb; ++k) {
-    if (!std::isfinite(sys->eps[k])) return LTMP2_ERR_INVALID_ARG;
-    if (k > 0 && sys->eps[k] < sys->eps[k - 1]) return LTMP2_ERR_INVALID_ARG;
-  }
-  const int no = sys->n_occ, npw = sys->n_pw, norb = sys->n_orb;
-  if (sys->eps[no] - sys->eps[no - 1] < 1e-6) return LTMP2_ERR_GAP;
-  double B[9], omega;
-  reciprocal(sys->lattice, B, &omega);
-  if (!(omega > 0.0) || !std::isfinite(omega)) return LTMP2_ERR_INVALID_ARG;
-  // plane-wave set
-  std::vector<std::array<int, 3>> m(npw);
-  std::map<std::array<int, 3>, int> where;
-  double g2max = 0.0;
-  for (int q = 0; q < npw; ++q) {
-    for (int k = 0; k < 3; ++k) {
-      m[q][k] = sys->miller[3 * q + k];
-      if (2 * std::abs(m[q][k]) >= n) return LTMP2_ERR_GRID;
-    }
-    if (!where.emplace(m[q], q).second) return LTMP2_ERR_INVALID_ARG;
-    g2max = std::max(g2max, g2_of(B, m[q][0], m[q][1], m[q][2]));
-  }
-  std::vector<int> negpw(npw);
-  for (int q = 0; q < npw; ++q) {
-    auto it = where.find({-m[q][0], -m[q][1], -m[q][2]});
-    if (it == where.end()) return LTMP2_ERR_GRID;
-    negpw[q] = it->second;
-  }
-  std::vector<Col> ocols;
-  std::vector<int> order;
-  if (!build_columns(m, ocols, order)) return LTMP2_ERR_GRID;
-  // orthonormality on a deterministic sample of orbitals
-  {
-    std::vector<int> pick;
-    const int S = std::min(norb, 40);
-    for (int s = 0; s < S; ++s) pick.push_back((int)((long long)s * (norb - 1) / std::max(1, S - 1)));
-    pick.push_back(no - 1);
-    pick.push_back(no);
-    std::sort(pick.begin(), pick.end());
-    pick.erase(std::unique(pick.begin(), pick.end()), pick.end());
-    for (size_t a = 0; a < pick.size(); ++a)
-      for (size_t b = a; b < pick.size(); ++b) {
-        const double *ca = sys->coeff + (size_t)pick[a] * npw * 2, *cb = sys->coeff + (size_t)pick[b] * npw * 2;
-        double re = 0, im = 0;
-        for (int q = 0; q < npw; ++q) {
-          re += ca[2 * q] * cb[2 * q] + ca[2 * q + 1] * cb[2 * q + 1];
-          im += ca[2 * q] * cb[2 * q + 1] - ca[2 * q + 1] * cb[2 * q];
-        }
-        if (!std::isfinite(re) || !std::isfinite(im)) return LTMP2_ERR_INVALID_ARG;
-        if (std::fabs(re - (a == b ? 1.0 : 0.0)) > 1e-8 || std::fabs(im) > 1e-8) return LTMP2_ERR_NOT_ORTHONORMAL;
-      }
-  }
-  const bool real_orb = (sys->flags & LTMP2_FLAG_REAL_ORBITALS) != 0;
-  if (real_orb) {
-    for (int r = 0; r < norb; ++r) {
-      const double *c = sys->coeff + (size_t)r * npw * 2;
-      for (int q = 0; q < npw; ++q) {
-        const int qn = negpw[q];
-        if (std::fabs(c[2 * q] - c[2 * qn]) > 1e-10 || std::fabs(c[2 * q + 1] + c[2 * qn + 1]) > 1e-10)
-          return LTMP2_ERR_NOT_REAL;
-      }
-    }
-  }
-  // auxiliary set A (Sec. II A) in column order, v(G) = 4 pi / |G|^2 (Eq. SCH2EI)
-  const double ecut_aux = sys->ecut_aux > 0.0 ? sys->ecut_aux : (2.0 / 3.0) * 0.5 * g2max;
-  std::vector<std::array<int, 3>> am;
-  {
-    const double gmax = std::sqrt(2.0 * ecut_aux);
-    int lim[3];
-    for (int k = 0; k < 3; ++k) {
-      const double an = std::sqrt(sys->lattice[3 * k] * sys->lattice[3 * k] +
-                                  sys->lattice[3 * k + 1] * sys->lattice[3 * k + 1] +
-                                  sys->lattice[3 * k + 2] * sys->lattice[3 * k + 2]);
-      lim[k] = (int)std::floor(gmax * an / 6.283185307179586476925286766559) + 1;
-    }
-    for (int a = -lim[0]; a <= lim[0]; ++a)
-      for (int b = -lim[1]; b <= lim[1]; ++b)
-        for (int d = -lim[2]; d <= lim[2]; ++d) {
-          const double g2 = g2_of(B, a, b, d);
-          // G = 0 is kept as a table entry with v(0) := 0 so that every column of the
-          // sphere is one contiguous m3 range; it never contributes.
-          if (0.5 * g2 <= ecut_aux) {
-            if (2 * std::abs(a) >= n || 2 * std::abs(b) >= n || 2 * std::abs(d) >= n) return LTMP2_ERR_GRID;
-            am.push_back({a, b, d});
-          }
-        }
-  }
-  if (am.size() < 3) return LTMP2_ERR_INVALID_ARG;
-  std::vector<Col> acols;
-  std::vector<int> aorder;
-  if (!build_columns(am, acols, aorder)) return LTMP2_ERR_GRID;
-  const int naux = (int)am.size();
-  std::vector<std::array<int, 3>> amo(naux);
-  for (int k = 0; k < naux; ++k) amo[k] = am[aorder[k]];
-  std::map<std::array<int, 3>, int> awhere;
-  for (int k = 0; k < naux; ++k) awhere[amo[k]] = k;
-  std::vector<int> aneg(naux), prim;
-  std::vector<double> v64(naux), ag2(naux);
-  std::vector<float> v32(naux);
-  for (int k = 0; k < naux; ++k) {
-    auto it = awhere.find({-amo[k][0], -amo[k][1], -amo[k][2]});
-    if (it == awhere.end()) return LTMP2_ERR_GRID;
-    aneg[k] = it->second;
-    const double g2 = g2_of(B, amo[k][0], amo[k][1], amo[k][2]);
-    ag2[k] = g2;
-    v64[k] = (g2 > 0.0) ? 12.566370614359172953850573533118 / g2 : 0.0;
-    v32[k] = (float)v64[k];
-    const int first = amo[k][0] != 0 ? amo[k][0] : (amo[k][1] != 0 ? amo[k][1] : amo[k][2]);
-    if (first > 0) prim.push_back(k);
-  }
-
-  ltmp2_ctx *c = new (std::nothrow) ltmp2_ctx();
+  try {
+  HostPlan hp;
+  int rc = build_host_plan(sys, LTMP2_FLAG_REAL_ORBITALS | LTMP2_FLAG_SIMT_GEMM, hp);
+  if (rc) return rc;
+  const int no = sys->n_occ;
+  std::unique_ptr<ltmp2_ctx> owner(new (std::nothrow) ltmp2_ctx());
+  ltmp2_ctx *c = owner.get();
   if (!c) return LTMP2_ERR_OOM;
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     cudaGetLastError();
-    delete c;
     return LTMP2_ERR_CUDA;
   }
   Plan &p = c->p;
+  p = hp.p;
   std::memcpy(c->lattice, sys->lattice, sizeof(c->lattice));
-  c->ecut_aux = ecut_aux;
-  c->aux_g2 = ag2;
-  p.n = n;
-  p.n_occ = no;
-  p.n_orb = norb;
-  p.n_pw = npw;
-  p.n_v = norb - no;
-  p.n_dorb = (int)ocols.size();
-  p.n_daux = (int)acols.size();
-  p.n_aux = naux;
-  p.n_prim = (int)prim.size();
-  p.real_orb = real_orb;
-  p.real_basis = real_orb;
-  p.precision = sys->precision;
-  p.omega = omega;
-  p.mu = 0.5 * (sys->eps[no - 1] + sys->eps[no]);
-  p.mxlo_orb = ocols.front().m1;
-  p.mxhi_orb = ocols.back().m1;
-  p.mxlo_aux = acols.front().m1;
-  p.mxhi_aux = acols.back().m1;
-  std::vector<int4> hdorb(p.n_dorb), hdaux(p.n_daux);
-  std::vector<int> hdorb_off(p.n_dorb), hdaux_off(p.n_daux), hpw(3 * (size_t)npw), haux(3 * (size_t)naux);
-  for (int d = 0; d < p.n_dorb; ++d) {
-    hdorb[d] = make_int4(ocols[d].m1, ocols[d].m2, ocols[d].zlo, ocols[d].zhi);
-    hdorb_off[d] = ocols[d].off;
-  }
-  for (int d = 0; d < p.n_daux; ++d) {
-    hdaux[d] = make_int4(acols[d].m1, acols[d].m2, acols[d].zlo, acols[d].zhi);
-    hdaux_off[d] = acols[d].off;
-  }
-  for (int q = 0; q < npw; ++q)
-    for (int k = 0; k < 3; ++k) hpw[3 * q + k] = m[order[q]][k];
-  for (int q = 0; q < naux; ++q)
-    for (int k = 0; k < 3; ++k) haux[3 * q + k] = amo[q][k];
-  int rc = LTMP2_OK;
+  c->ecut_aux = hp.ecut_aux;
+  c->aux_g2 = hp.aux_g2;
+  c->fingerprint = hp.fingerprint;
+  const std::vector<int> &order = hp.order;
   auto up = [&](auto **dptr, const auto &vec) -> int {
     using X = typename std::remove_reference<decltype(vec)>::type::value_type;
     int r = dalloc(c, dptr, vec.size());
     if (r) return r;
     return cuda_status(cudaMemcpy(*dptr, vec.data(), vec.size() * sizeof(X), cudaMemcpyHostToDevice));
   };
-  std::vector<double> heps(sys->eps, sys->eps + norb);
-  if (!rc) rc = up(&p.dorb, hdorb);
-  if (!rc) rc = up(&p.dorb_off, hdorb_off);
-  if (!rc) rc = up(&p.daux, hdaux);
-  if (!rc) rc = up(&p.daux_off, hdaux_off);
-  if (!rc) rc = up(&p.pw_m, hpw);
-  if (!rc && p.real_basis) {
-    // internal position of -G_q for every internal q
-    std::vector<int> pos(npw), hpair(npw);
-    for (int q = 0; q < npw; ++q) pos[order[q]] = q;
-    for (int q = 0; q < npw; ++q) hpair[q] = pos[negpw[order[q]]];
-    rc = up(&p.pw_pair, hpair);
-  }
-  if (!rc) rc = up(&p.aux_m, haux);
-  if (!rc) rc = up(&p.aux_neg, aneg);
-  if (!rc) rc = up(&p.prim, prim);
-  if (!rc) rc = up(&p.v_aux64, v64);
-  if (!rc) rc = up(&p.v_aux32, v32);
+  std::vector<double> heps(sys->eps, sys->eps + sys->n_orb);
+  if (!rc) rc = up(&p.dorb, hp.dorb);
+  if (!rc) rc = up(&p.dorb_off, hp.dorb_off);
+  if (!rc) rc = up(&p.daux, hp.daux);
+  if (!rc) rc = up(&p.daux_off, hp.daux_off);
+  if (!rc) rc = up(&p.pw_m, hp.pw_m);
+  if (!rc && p.real_basis) rc = up(&p.pw_pair, hp.pw_pair);   // internal position of -G_q
+  if (!rc) rc = up(&p.aux_m, hp.aux_m);
+  if (!rc) rc = up(&p.aux_neg, hp.aux_neg);
+  if (!rc) rc = up(&p.prim, hp.prim);
+  if (!rc) rc = up(&p.v_aux64, hp.v64);
+  if (!rc) rc = up(&p.v_aux32, hp.v32);
   if (!rc) rc = up(&p.eps, heps);
   const size_t no2 = (size_t)no * no;
   if (!rc) rc = dalloc(c, &p.ex, no2);
@@ -791,11 +591,15 @@ int ltmp2_setup(const ltmp2_system *sys, ltmp2_ctx **out) {
                                         : setup_precision<float>(c, sys, order);
   if (rc) {
     cudaGetLastError();
-    delete c;
     return rc;
   }
-  *out = c;
+  *out = owner.release();
   return LTMP2_OK;
+  } catch (const std::bad_alloc &) {
+    return LTMP2_ERR_OOM;
+  } catch (...) {
+    return LTMP2_ERR_INVALID_ARG;
+  }
 }
 
 int ltmp2_set_stream(ltmp2_ctx *ctx, void *stream) {
@@ -860,6 +664,40 @@ int ltmp2_kernel_launches(const ltmp2_ctx *ctx, long long *count) {
   return LTMP2_OK;
 }
 
+int ltmp2_fingerprint(const ltmp2_ctx *ctx, unsigned long long *out) {
+  if (!ctx || !out) return LTMP2_ERR_INVALID_ARG;
+  unsigned long long h = ctx->fingerprint;
+  if (ctx->mask_hash) h = (h ^ ctx->mask_hash) * 0xff51afd7ed558ccdull;
+  *out = h;
+  return LTMP2_OK;
+}
+
+int ltmp2_sum_partials(int n, int n_occ, const double *e, const double *pd, const double *px, double *e_out,
+                       double *pd_out, double *px_out) {
+  if (n < 0 || n_occ < 1 || (n > 0 && !e) || !e_out) return LTMP2_ERR_INVALID_ARG;
+  if ((pd_out && n > 0 && !pd) || (px_out && n > 0 && !px)) return LTMP2_ERR_INVALID_ARG;
+  const size_t no2 = (size_t)n_occ * n_occ;
+  double ed = 0.0, ex = 0.0;
+  for (int c = 0; c < n; ++c) {
+    ed += e[2 * c];
+    ex += e[2 * c + 1];
+  }
+  if (!std::isfinite(ed) || !std::isfinite(ex)) return LTMP2_ERR_INVALID_ARG;
+  for (int q = 0; q < 2; ++q) {
+    double *out = q == 0 ? pd_out : px_out;
+    const double *in = q == 0 ? pd : px;
+    if (!out) continue;
+    for (size_t k = 0; k < no2; ++k) {
+      double s = 0.0;
+      for (int c = 0; c < n; ++c) s += in[(size_t)c * no2 + k];
+      out[k] = s;
+    }
+  }
+  e_out[0] = ed;
+  e_out[1] = ex;
+  return LTMP2_OK;
+}
+
 int ltmp2_set_profiling(ltmp2_ctx *ctx, int on) {
   if (!ctx) return LTMP2_ERR_INVALID_ARG;
   ctx->timer.on = (on != 0);
@@ -909,6 +747,7 @@ int ltmp2_set_pair_mask(ltmp2_ctx *ctx, const unsigned char *keep) {
     p.pair_keep = nullptr;
     p.keep_list = nullptr;
     p.keep_count = nullptr;
+    ctx->mask_hash = 0;
     return LTMP2_OK;
   }
   const int no = p.n_occ;
@@ -938,6 +777,10 @@ int ltmp2_set_pair_mask(ltmp2_ctx *ctx, const unsigned char *keep) {
   p.pair_keep = ctx->d_keep;
   p.keep_list = ctx->d_keep_list;
   p.keep_count = ctx->d_keep_count;
+  // the mask changes the exchange energy, so it enters the fingerprint
+  unsigned long long h = 0xcbf29ce484222325ull;
+  for (unsigned char b : k01) h = (h ^ b) * 0x100000001b3ull;
+  ctx->mask_hash = h | 1ull;
   return LTMP2_OK;
 }
 
@@ -1022,7 +865,7 @@ int ltmp2_set_tuning(ltmp2_ctx *ctx, const int *values) {
   const int ib = values[3] < 0 ? p.plane_ib : values[3];
   if (slab < 1 || slab > ctx->slab_capacity) return LTMP2_ERR_INVALID_ARG;
   if (variant >= 0) {
-    if (!p.tc || variant > 5 || (ctx->tc.real && variant != 5)) return LTMP2_ERR_INVALID_ARG;
+    if (!p.tc || (variant != 4 && variant != 5) || (ctx->tc.real && variant != 5)) return LTMP2_ERR_INVALID_ARG;
   }
   const bool ok = p.precision == LTMP2_FP64 ? Path<double>::plane_feasible(p, pk, ib)
                                              : Path<float>::plane_feasible(p, pk, ib);

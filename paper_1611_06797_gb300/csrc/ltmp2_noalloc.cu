@@ -18,13 +18,14 @@
 #include <array>
 #include <cmath>
 #include <cstring>
-#include <map>
 #include <mutex>
+#include <new>
 #include <type_traits>
 #include <vector>
 
 #include "../../include/ltmp2.h"
 #include "fft.cuh"
+#include "host_plan.h"
 #include "plan.h"
 
 using namespace ltmp2;
@@ -44,7 +45,9 @@ std::mutex g_scratch_mutex;
 void *g_scratch_ptr[64] = {nullptr};
 
 // Device address of the scratch array on the current device (host code cannot use the
-// array's name as an address).  Looked up once per device.
+// array's name as an address).  Looked up once per device and cached; a cudaDeviceReset
+// of that device invalidates the cached address, so calls after a reset are not
+// supported.
 int scratch_base(void **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -80,35 +83,6 @@ struct Arena {
   }
   size_t left() const { return cap - used; }
 };
-
-struct NaCol {
-  int m1, m2, zlo, zhi, off;
-};
-
-bool na_columns(const std::vector<std::array<int, 3>> &m, std::vector<NaCol> &cols, std::vector<int> &order) {
-  const int n = (int)m.size();
-  order.resize(n);
-  for (int k = 0; k < n; ++k) order[k] = k;
-  std::sort(order.begin(), order.end(), [&](int a, int b) { return m[a] < m[b]; });
-  cols.clear();
-  for (int k = 0; k < n; ++k) {
-    const auto &q = m[order[k]];
-    if (cols.empty() || cols.back().m1 != q[0] || cols.back().m2 != q[1]) {
-      cols.push_back({q[0], q[1], q[2], q[2], k});
-    } else {
-      if (q[2] != cols.back().zhi + 1) return false;
-      cols.back().zhi = q[2];
-    }
-  }
-  return true;
-}
-
-double na_g2(const double B[9], int a, int b, int c) {
-  const double x = a * B[0] + b * B[3] + c * B[6];
-  const double y = a * B[1] + b * B[4] + c * B[7];
-  const double z = a * B[2] + b * B[5] + c * B[8];
-  return x * x + y * y + z * z;
-}
 
 int copy_in(void *dst, const void *src, size_t bytes, cudaStream_t st) {
   if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
@@ -221,149 +195,21 @@ int run_noalloc(const ltmp2_system *sys, Plan &p, Arena &ar, const std::vector<i
   return LTMP2_OK;
 }
 
-}  // namespace
-
-extern "C" int ltmp2_energy_noalloc(const ltmp2_system *sys, int n_tau, const double *tau, const double *w,
-                                    double *e_direct, double *e_exchange, double *e_pair, void *stream) {
+int energy_noalloc(const ltmp2_system *sys, int n_tau, const double *tau, const double *w, double *e_direct,
+                   double *e_exchange, double *e_pair, void *stream) {
   if (!sys || !e_direct || !e_exchange || !tau || !w || n_tau < 1) return LTMP2_ERR_INVALID_ARG;
   for (int k = 0; k < n_tau; ++k)
     if (!(tau[k] > 0.0) || !std::isfinite(tau[k]) || !std::isfinite(w[k])) return LTMP2_ERR_INVALID_ARG;
-  if (!sys->miller || !sys->coeff || !sys->eps) return LTMP2_ERR_INVALID_ARG;
-  if (sys->n_pw < 2 || sys->n_orb < 2 || sys->n_occ < 1 || sys->n_occ >= sys->n_orb || sys->n_orb > sys->n_pw)
-    return LTMP2_ERR_INVALID_ARG;
-  if (sys->precision != LTMP2_FP64 && sys->precision != LTMP2_FP32) return LTMP2_ERR_INVALID_ARG;
-  if (sys->flags & ~LTMP2_FLAG_REAL_ORBITALS) return LTMP2_ERR_INVALID_ARG;
-  const int n = sys->grid[0];
-  if (sys->grid[1] != n || sys->grid[2] != n || !fft_size_supported(n)) return LTMP2_ERR_GRID;
-  const int no = sys->n_occ, npw = sys->n_pw, norb = sys->n_orb;
-  for (int k = 0; k < norb; ++k) {
-    if (!std::isfinite(sys->eps[k])) return LTMP2_ERR_INVALID_ARG;
-    if (k > 0 && sys->eps[k] < sys->eps[k - 1]) return LTMP2_ERR_INVALID_ARG;
-  }
-  if (sys->eps[no] - sys->eps[no - 1] < 1e-6) return LTMP2_ERR_GAP;
-  // reciprocal lattice
-  const double *A = sys->lattice;
-  const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
-                     A[2] * (A[3] * A[7] - A[4] * A[6]);
-  if (!std::isfinite(det) || det == 0.0) return LTMP2_ERR_INVALID_ARG;
-  double inv[9] = {(A[4] * A[8] - A[5] * A[7]) / det, (A[2] * A[7] - A[1] * A[8]) / det,
-                   (A[1] * A[5] - A[2] * A[4]) / det, (A[5] * A[6] - A[3] * A[8]) / det,
-                   (A[0] * A[8] - A[2] * A[6]) / det, (A[2] * A[3] - A[0] * A[5]) / det,
-                   (A[3] * A[7] - A[4] * A[6]) / det, (A[1] * A[6] - A[0] * A[7]) / det,
-                   (A[0] * A[4] - A[1] * A[3]) / det};
-  double B[9];
-  const double tp = 6.283185307179586476925286766559;
-  for (int k = 0; k < 3; ++k)
-    for (int c = 0; c < 3; ++c) B[k * 3 + c] = tp * inv[c * 3 + k];
-  // plane-wave set
-  std::vector<std::array<int, 3>> m(npw);
-  std::map<std::array<int, 3>, int> where;
-  double g2max = 0.0;
-  for (int q = 0; q < npw; ++q) {
-    for (int k = 0; k < 3; ++k) {
-      m[q][k] = sys->miller[3 * q + k];
-      if (2 * std::abs(m[q][k]) >= n) return LTMP2_ERR_GRID;
-    }
-    if (!where.emplace(m[q], q).second) return LTMP2_ERR_INVALID_ARG;
-    g2max = std::max(g2max, na_g2(B, m[q][0], m[q][1], m[q][2]));
-  }
-  std::vector<int> negpw(npw);
-  for (int q = 0; q < npw; ++q) {
-    auto it = where.find({-m[q][0], -m[q][1], -m[q][2]});
-    if (it == where.end()) return LTMP2_ERR_GRID;
-    negpw[q] = it->second;
-  }
-  const bool real_orb = (sys->flags & LTMP2_FLAG_REAL_ORBITALS) != 0;
-  if (real_orb)
-    for (int r = 0; r < norb; ++r) {
-      const double *c = sys->coeff + (size_t)r * npw * 2;
-      for (int q = 0; q < npw; ++q) {
-        const int qn = negpw[q];
-        if (std::fabs(c[2 * q] - c[2 * qn]) > 1e-10 || std::fabs(c[2 * q + 1] + c[2 * qn + 1]) > 1e-10)
-          return LTMP2_ERR_NOT_REAL;
-      }
-    }
-  std::vector<NaCol> ocols;
-  std::vector<int> order;
-  if (!na_columns(m, ocols, order)) return LTMP2_ERR_GRID;
-  // auxiliary set in column order, G = 0 kept with v = 0
-  const double ecut_aux = sys->ecut_aux > 0.0 ? sys->ecut_aux : (2.0 / 3.0) * 0.5 * g2max;
-  std::vector<std::array<int, 3>> am;
-  {
-    const double gmax = std::sqrt(2.0 * ecut_aux);
-    int lim[3];
-    for (int k = 0; k < 3; ++k) {
-      const double an = std::sqrt(A[3 * k] * A[3 * k] + A[3 * k + 1] * A[3 * k + 1] + A[3 * k + 2] * A[3 * k + 2]);
-      lim[k] = (int)std::floor(gmax * an / tp) + 1;
-    }
-    for (int a = -lim[0]; a <= lim[0]; ++a)
-      for (int b = -lim[1]; b <= lim[1]; ++b)
-        for (int d = -lim[2]; d <= lim[2]; ++d)
-          if (0.5 * na_g2(B, a, b, d) <= ecut_aux) {
-            if (2 * std::abs(a) >= n || 2 * std::abs(b) >= n || 2 * std::abs(d) >= n) return LTMP2_ERR_GRID;
-            am.push_back({a, b, d});
-          }
-  }
-  if (am.size() < 3) return LTMP2_ERR_INVALID_ARG;
-  std::vector<NaCol> acols;
-  std::vector<int> aorder;
-  if (!na_columns(am, acols, aorder)) return LTMP2_ERR_GRID;
-  const int naux = (int)am.size();
-  std::vector<std::array<int, 3>> amo(naux);
-  for (int k = 0; k < naux; ++k) amo[k] = am[aorder[k]];
-  std::map<std::array<int, 3>, int> awhere;
-  for (int k = 0; k < naux; ++k) awhere[amo[k]] = k;
-  std::vector<int> aneg(naux), prim;
-  std::vector<double> v64(naux);
-  std::vector<float> v32(naux);
-  for (int k = 0; k < naux; ++k) {
-    aneg[k] = awhere.at({-amo[k][0], -amo[k][1], -amo[k][2]});
-    const double g2 = na_g2(B, amo[k][0], amo[k][1], amo[k][2]);
-    v64[k] = g2 > 0.0 ? 12.566370614359172953850573533118 / g2 : 0.0;
-    v32[k] = (float)v64[k];
-    const int first = amo[k][0] != 0 ? amo[k][0] : (amo[k][1] != 0 ? amo[k][1] : amo[k][2]);
-    if (first > 0) prim.push_back(k);
-  }
-
-  void *base = nullptr;
-  int rc = scratch_base(&base);
+  // the same validation and tables as ltmp2_setup; the CUDA-core GEMM flag is implied here
+  HostPlan hp;
+  int rc = build_host_plan(sys, LTMP2_FLAG_REAL_ORBITALS, hp);
   if (rc) return rc;
+  void *base = nullptr;
+  if ((rc = scratch_base(&base))) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Arena ar(base, kNoAllocScratchBytes);
-  Plan p;
-  p.n = n;
-  p.n_occ = no;
-  p.n_orb = norb;
-  p.n_pw = npw;
-  p.n_v = norb - no;
-  p.n_dorb = (int)ocols.size();
-  p.n_daux = (int)acols.size();
-  p.n_aux = naux;
-  p.n_prim = (int)prim.size();
-  p.real_orb = real_orb;
-  p.real_basis = real_orb;
-  p.precision = sys->precision;
-  p.omega = std::fabs(det);
-  p.mu = 0.5 * (sys->eps[no - 1] + sys->eps[no]);
-  p.mxlo_orb = ocols.front().m1;
-  p.mxhi_orb = ocols.back().m1;
-  p.mxlo_aux = acols.front().m1;
-  p.mxhi_aux = acols.back().m1;
-  std::vector<int4> hdorb(p.n_dorb), hdaux(p.n_daux);
-  std::vector<int> hdorb_off(p.n_dorb), hdaux_off(p.n_daux), hpw(3 * (size_t)npw), haux(3 * (size_t)naux);
-  for (int d = 0; d < p.n_dorb; ++d) {
-    hdorb[d] = make_int4(ocols[d].m1, ocols[d].m2, ocols[d].zlo, ocols[d].zhi);
-    hdorb_off[d] = ocols[d].off;
-  }
-  for (int d = 0; d < p.n_daux; ++d) {
-    hdaux[d] = make_int4(acols[d].m1, acols[d].m2, acols[d].zlo, acols[d].zhi);
-    hdaux_off[d] = acols[d].off;
-  }
-  for (int q = 0; q < npw; ++q)
-    for (int k = 0; k < 3; ++k) hpw[3 * q + k] = m[order[q]][k];
-  for (int q = 0; q < naux; ++q)
-    for (int k = 0; k < 3; ++k) haux[3 * q + k] = amo[q][k];
-  std::vector<double> heps(sys->eps, sys->eps + norb);
+  Plan p = hp.p;
+  std::vector<double> heps(sys->eps, sys->eps + sys->n_orb);
   auto put = [&](auto **dst, const auto &vec) -> int {
     using X = typename std::remove_reference<decltype(vec)>::type::value_type;
     void *q = ar.take(vec.size() * sizeof(X));
@@ -371,24 +217,33 @@ extern "C" int ltmp2_energy_noalloc(const ltmp2_system *sys, int n_tau, const do
     *dst = reinterpret_cast<typename std::remove_reference<decltype(*dst)>::type>(q);
     return copy_in(q, vec.data(), vec.size() * sizeof(X), st);
   };
-  if ((rc = put(&p.dorb, hdorb))) return rc;
-  if ((rc = put(&p.dorb_off, hdorb_off))) return rc;
-  if ((rc = put(&p.daux, hdaux))) return rc;
-  if ((rc = put(&p.daux_off, hdaux_off))) return rc;
-  if ((rc = put(&p.pw_m, hpw))) return rc;
-  if (real_orb) {
-    std::vector<int> pos(npw), hpair(npw);
-    for (int q = 0; q < npw; ++q) pos[order[q]] = q;
-    for (int q = 0; q < npw; ++q) hpair[q] = pos[negpw[order[q]]];
-    if ((rc = put(&p.pw_pair, hpair))) return rc;
-  }
-  if ((rc = put(&p.aux_m, haux))) return rc;
-  if ((rc = put(&p.aux_neg, aneg))) return rc;
-  if ((rc = put(&p.prim, prim))) return rc;
-  if ((rc = put(&p.v_aux64, v64))) return rc;
-  if ((rc = put(&p.v_aux32, v32))) return rc;
+  if ((rc = put(&p.dorb, hp.dorb))) return rc;
+  if ((rc = put(&p.dorb_off, hp.dorb_off))) return rc;
+  if ((rc = put(&p.daux, hp.daux))) return rc;
+  if ((rc = put(&p.daux_off, hp.daux_off))) return rc;
+  if ((rc = put(&p.pw_m, hp.pw_m))) return rc;
+  if (p.real_basis && (rc = put(&p.pw_pair, hp.pw_pair))) return rc;
+  if ((rc = put(&p.aux_m, hp.aux_m))) return rc;
+  if ((rc = put(&p.aux_neg, hp.aux_neg))) return rc;
+  if ((rc = put(&p.prim, hp.prim))) return rc;
+  if ((rc = put(&p.v_aux64, hp.v64))) return rc;
+  if ((rc = put(&p.v_aux32, hp.v32))) return rc;
   if ((rc = put(&p.eps, heps))) return rc;
   return sys->precision == LTMP2_FP64
-             ? run_noalloc<double>(sys, p, ar, order, n_tau, tau, w, st, e_direct, e_exchange, e_pair)
-             : run_noalloc<float>(sys, p, ar, order, n_tau, tau, w, st, e_direct, e_exchange, e_pair);
+             ? run_noalloc<double>(sys, p, ar, hp.order, n_tau, tau, w, st, e_direct, e_exchange, e_pair)
+             : run_noalloc<float>(sys, p, ar, hp.order, n_tau, tau, w, st, e_direct, e_exchange, e_pair);
+}
+
+}  // namespace
+
+extern "C" int ltmp2_energy_noalloc(const ltmp2_system *sys, int n_tau, const double *tau, const double *w,
+                                    double *e_direct, double *e_exchange, double *e_pair, void *stream) {
+  // host-side containers may throw; nothing may cross the C boundary
+  try {
+    return energy_noalloc(sys, n_tau, tau, w, e_direct, e_exchange, e_pair, stream);
+  } catch (const std::bad_alloc &) {
+    return LTMP2_ERR_OOM;
+  } catch (...) {
+    return LTMP2_ERR_INVALID_ARG;
+  }
 }

@@ -1,6 +1,7 @@
 // Launchers of the hot path for one real type T.  Included once per precision by
 // kernels_f64.cu / kernels_f32.cu, which explicitly instantiate Path<T>.
 #pragma once
+#include <mutex>
 #include <type_traits>
 
 #include "kernels.cuh"
@@ -91,7 +92,10 @@ struct ScopedStage {
 };
 
 template <typename T> cudaError_t Path<T>::init_device() {
+  // once per device and process; contexts set up from several host threads serialise here
   static bool done[64] = {false};
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;

@@ -9,7 +9,7 @@ namespace ltmp2 {
 // Operands, tensor maps and error flag of the tcgen05 3xTF32 GEMM (precision form).
 struct TcResources {
   int rows_cap = 0, npw = 0, kpad = 0;
-  int variant = 5;         // 0-3 single-pass (tests), 4 drained N=64, 5 stacked Re/Im deep ring
+  int variant = 5;         // 4 drained N=64, 5 stacked Re/Im rows (default; the only one for real orbitals)
   bool real = false;       // real-basis Green's function: K = n_pw (variant 5 only)
   float *a1h = nullptr, *a1l = nullptr, *a2h = nullptr, *a2l = nullptr, *bh = nullptr, *bl = nullptr;
   int *err = nullptr;      // device flag: a bounded wait ran out

@@ -67,6 +67,8 @@ def load_library():
         "ltmp2_last_imag": (ctypes.c_int, [vp, dp, dp]),
         "ltmp2_set_profiling": (ctypes.c_int, [vp, ctypes.c_int]),
         "ltmp2_kernel_launches": (ctypes.c_int, [vp, P(ctypes.c_longlong)]),
+        "ltmp2_fingerprint": (ctypes.c_int, [vp, P(ctypes.c_ulonglong)]),
+        "ltmp2_sum_partials": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp]),
         "ltmp2_stage_times": (ctypes.c_int, [vp, ctypes.c_int, dp, P(ctypes.c_longlong)]),
         "ltmp2_reset_stage_times": (ctypes.c_int, [vp]),
         "ltmp2_destroy": (None, [vp]),
@@ -226,6 +228,30 @@ def ltmp2_kernel_launches(ctx: Context) -> int:
     n = ctypes.c_longlong()
     _check(load_library().ltmp2_kernel_launches(ctx.handle, ctypes.byref(n)), "ltmp2_kernel_launches")
     return int(n.value)
+
+
+def ltmp2_fingerprint(ctx: Context) -> int:
+    """64-bit hash of the context's inputs and pair mask (checkpoint keys)."""
+    n = ctypes.c_ulonglong()
+    _check(load_library().ltmp2_fingerprint(ctx.handle, ctypes.byref(n)), "ltmp2_fingerprint")
+    return int(n.value)
+
+
+def ltmp2_sum_partials(e, pd, px):
+    """Fixed-order sum of chunk results: e [n][2], pd / px [n][n_occ][n_occ].
+    Returns (E_d, E_x, e^d_ij, e^x_ij)."""
+    e = np.ascontiguousarray(np.asarray(e, dtype=np.float64).reshape(-1, 2))
+    pd = np.ascontiguousarray(np.asarray(pd, dtype=np.float64))
+    px = np.ascontiguousarray(np.asarray(px, dtype=np.float64))
+    n, no = e.shape[0], pd.shape[-1]
+    if pd.shape != (n, no, no) or px.shape != (n, no, no):
+        raise ValueError("pd and px must be [n][n_occ][n_occ]")
+    eo = np.zeros(2)
+    pdo = np.zeros((no, no))
+    pxo = np.zeros((no, no))
+    _check(load_library().ltmp2_sum_partials(n, no, _dp(e), _dp(pd), _dp(px), _dp(eo), _dp(pdo), _dp(pxo)),
+           "ltmp2_sum_partials")
+    return float(eo[0]), float(eo[1]), pdo, pxo
 
 
 def ltmp2_set_profiling(ctx: Context, on: bool) -> None:

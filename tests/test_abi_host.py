@@ -187,3 +187,30 @@ def test_extrapolate_and_noalloc_validate_on_the_host():
     g = lib.ltmp2_energy_noalloc
     g.restype = ctypes.c_int
     assert g(None, 1, None, None, None, None, None, None) == -1
+
+
+def test_noalloc_rejects_bad_systems_with_the_setup_codes():
+    """The allocation-free entry point validates its input with ltmp2_setup's own checks
+    (one shared host routine): a non-orthonormal set, a NaN coefficient, a missing gap,
+    a bad grid and a wrong real-orbital flag get the same status from both, on the host,
+    before any device work."""
+    s = solid("tiny")
+    tau, w = np.array([0.5, 2.0]), np.array([0.4, 0.9])
+    c_bad = s.coeff.copy(); c_bad[1] *= 1.01
+    c_nan = s.coeff.copy(); c_nan[2, 5] = complex(np.nan, 0.0)
+    eps_gap = s.eps.copy(); eps_gap[s.n_occ] = eps_gap[s.n_occ - 1]
+    cases = [("NOT_ORTHONORMAL", dict(coeff=c_bad)), ("INVALID_ARG", dict(coeff=c_nan)),
+             ("GAP", dict(eps=eps_gap)), ("GRID", dict(grid=[8, 8, 10]))]
+    for name, kw in cases:
+        _expect(name, s, **kw)
+        args = dict(lattice=s.lattice, grid=s.grid, miller=s.miller, coeff=s.coeff, eps=s.eps, n_occ=s.n_occ)
+        args.update(kw)
+        with pytest.raises(L.Ltmp2Error) as e:
+            L.ltmp2_energy_noalloc(args["lattice"], args["grid"], args["miller"], args["coeff"], args["eps"],
+                                   args["n_occ"], tau, w)
+        assert e.value.name == name, (name, e.value.name)
+    sp = solid("tiny", random_phases=True)
+    with pytest.raises(L.Ltmp2Error) as e:
+        L.ltmp2_energy_noalloc(sp.lattice, sp.grid, sp.miller, sp.coeff, sp.eps, sp.n_occ, tau, w,
+                               flags=L.FLAG_REAL_ORBITALS)
+    assert e.value.name == "NOT_REAL"
