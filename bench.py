@@ -41,7 +41,8 @@ FP32_ALU_TFLOPS = 128 * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
 TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense tensor-rate ratio (tf32 / bf16)
 
 WORKLOAD = "cfg2"
-CPU_SAMPLE_ORBITALS = (0, 1)   # oracle sample: pairs (0,0), (0,1), (1,1)
+CPU_SAMPLE_ORBITALS = (0, 1)   # oracle sample: ordered pairs (0,0), (0,1), (1,0), (1,1)
+E2E_REPS = 3                   # end-to-end repetitions (each a full setup + energy + destroy)
 
 
 def log(*a):
@@ -133,46 +134,70 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
-def cpu_worker(workload: str, orbitals, n_tau: int, reps: int = 1):
-    """Runs in a fresh process: time the FP64 oracle on a bounded sample of the workload,
-    `reps` times (nothing is cached between repetitions)."""
+def cpu_worker(workload: str, orbitals, quad_json: str, reps: int = 1):
+    """Runs in a fresh process: time the FP64 oracle on a bounded sample of the workload
+    (every ordered pair (i, j) of the sampled occupied orbitals), `reps` times (nothing is
+    cached between repetitions), with the quadrature (tau, w) the GPU arm uses."""
     import numpy as np
-    from oracle import OracleSystem, denominator_range, laplace_denominator, mp2_energy, sinc_laplace_quadrature
+    from oracle import OracleSystem, laplace_denominator, mp2_energy
     from synth import SPECS, build_model_solid
+    q = json.loads(quad_json)
+    tau, w = np.array(q["tau"]), np.array(q["w"])
     s = build_model_solid(SPECS[workload])
     o = OracleSystem.from_solid(s)
-    tau, w = sinc_laplace_quadrature(n_tau, *denominator_range(o))
     pairs = [(i, j) for i in orbitals for j in orbitals]
     secs = []
     for _ in range(reps):
         t0 = time.perf_counter()
         r = mp2_energy(o, laplace_denominator(tau, w), pairs=pairs, method="fft")
         secs.append(time.perf_counter() - t0)
-    unordered = len(orbitals) * (len(orbitals) + 1) // 2
-    print(json.dumps({"seconds": secs, "unordered_pairs": unordered, "n_tau": n_tau,
-                      "e00": float(r["e_d"][orbitals[0], orbitals[0]] + r["e_x"][orbitals[0], orbitals[0]])}))
+    e = {f"{i},{j}": float(r["e_d"][i, j] + r["e_x"][i, j]) for i, j in pairs}
+    print(json.dumps({"seconds": secs, "ordered_pairs": len(pairs), "n_tau": len(tau), "e_pair": e}))
 
 
-def run_cpu_baseline(workload: str, n_tau: int, reps: int = 1, skip: int = 0):
-    """The oracle in a fresh process on all host cores; the first `skip` repetitions are warm-up."""
+def run_cpu_baseline(workload: str, tau, w, reps: int = 1, skip: int = 0):
+    """The oracle in a fresh process on all host cores; the first `skip` repetitions are warm-up.
+
+    The sample evaluates o ordered pairs; the whole workload has n_occ^2 ordered pairs
+    (each costs the oracle the same N_v^2 N_G multiply-adds), so one E_MP2 takes
+    t_sample * n_occ^2 / o, and the throughput in the metric's unit is
+    (n_occ (n_occ + 1) / 2) * n_tau / that time."""
+    from synth import SPECS
+    spec = SPECS[workload]
     cores = os.cpu_count() or 1
     env = dict(os.environ, OPENBLAS_NUM_THREADS=str(cores), OMP_NUM_THREADS=str(cores),
                MKL_NUM_THREADS=str(cores), CUDA_VISIBLE_DEVICES="")
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", workload, "--ntau", str(n_tau),
+    quad = json.dumps({"tau": [float(x) for x in tau], "w": [float(x) for x in w]})
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", workload, "--quad", quad,
            "--reps", str(reps)]
     r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
     if r.returncode != 0:
         raise RuntimeError("cpu baseline failed: " + r.stderr[-2000:])
     d = json.loads(r.stdout.strip().splitlines()[-1])
     secs = d["seconds"][skip:]
-    total = sum(secs)
-    value = d["unordered_pairs"] * d["n_tau"] * len(secs) / total
-    sample = (f"oracle (canonical MP2 with the Laplace denominator, explicit sums over i,j,a,b; numpy "
-              f"FFT overlap densities + BLAS pair integrals) for occupied orbitals {list(CPU_SAMPLE_ORBITALS)}: "
-              f"{d['unordered_pairs']} unordered pairs x {d['n_tau']} tau of the {workload} workload, "
-              f"{total / len(secs):.2f} s per sample")
+    t_sample = sum(secs) / len(secs)
+    ordered_full = spec.n_occ * spec.n_occ
+    t_full = t_sample * ordered_full / d["ordered_pairs"]
+    value = spec.n_occ * (spec.n_occ + 1) // 2 * d["n_tau"] / t_full
+    sample = (f"oracle (canonical MP2 with the Laplace denominator of the GPU arm's own (tau, w), explicit "
+              f"sums over i,j,a,b; numpy FFT overlap densities + BLAS pair integrals): the "
+              f"{d['ordered_pairs']} ordered pairs of occupied orbitals {list(CPU_SAMPLE_ORBITALS)} x "
+              f"{d['n_tau']} tau of the {workload} workload, {t_sample:.2f} s per sample, scaled by "
+              f"{ordered_full}/{d['ordered_pairs']} ordered pairs to one E_MP2 ({t_full:.0f} s)")
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-            "seconds": secs, "unordered_pairs": d["unordered_pairs"]}
+            "seconds": secs, "ordered_pairs": d["ordered_pairs"], "s_per_E_MP2_extrapolated": t_full,
+            "e_pair": d["e_pair"]}
+
+
+def oracle_check(cb, e_pair):
+    """Sampled pair energies of the timed GPU run against the oracle's (same inputs, same
+    quadrature): the 1e-8 Ha parity bound, checked inside the benchmark."""
+    diffs = {}
+    for key, ref in cb["e_pair"].items():
+        i, j = (int(x) for x in key.split(","))
+        diffs[key] = abs(float(e_pair[i][j]) - ref)
+    worst = max(diffs.values())
+    return {"pairs": sorted(diffs), "max_abs_diff_Ha": worst, "within_1e-8_Ha": worst <= 1e-8}
 
 
 # ------------------------------------------------------------------ cost model
@@ -201,7 +226,13 @@ def aux_nxa(spec):
     return 2 * int(math.floor(math.sqrt(2.0 * spec.r2 / 3.0) + 1e-12)) + 1
 
 
-def roofline_of(st, costs, precision, simt, peaks, peak_kind):
+def measured_alu(L):
+    """FP64 / FP32 FMA rates of this GPU, measured now (ltmp2_alu_peak, CUDA events)."""
+    return {"fp64": L.ltmp2_alu_peak(L.FP64), "fp32": L.ltmp2_alu_peak(L.FP32),
+            "kind": "measured in this run: independent FMA chains over a full grid, CUDA events, best of 5"}
+
+
+def roofline_of(st, costs, precision, simt, peaks, peak_kind, alu):
     """Dominant stage against its bound: achieved = algorithmic work per launch / mean
     launch time (CUDA events around each launch on the library's stream)."""
     dom = max(st, key=lambda k: st[k]["ms"])
@@ -216,9 +247,9 @@ def roofline_of(st, costs, precision, simt, peaks, peak_kind):
         peak = peaks["bf16_tflops"] * TF32_OVER_BF16
         bound, pk = "tensor", f"tf32 = {peak_kind} bf16 {peaks['bf16_tflops']} x nominal 1.1/2.25"
     elif precision == 0:
-        peak, bound, pk = FP64_ALU_TFLOPS, "alu", "derived (2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz)"
+        peak, bound, pk = alu["fp64"], "alu", "FP64 FMA rate " + alu["kind"]
     else:
-        peak, bound, pk = FP32_ALU_TFLOPS, "alu", "derived (128 FP32 FMA/clk/SM x 152 SMs x 2070 MHz)"
+        peak, bound, pk = alu["fp32"], "alu", "FP32 FMA rate " + alu["kind"]
     achieved = work / (per_launch_ms / 1e3) / 1e12
     return {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "peak_kind": pk, "traffic": traffic_for(dom, precision),
@@ -232,11 +263,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP32 forms on the 24^3 workload")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the forms on their own workloads (36^3 precision form, 8-system batch)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-worker", default=None)
-    ap.add_argument("--ntau", type=int, default=8)
+    ap.add_argument("--quad", default=None)
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--slab", type=int, default=0, help="primary G' per slab (0 = library default)")
     ap.add_argument("--route", default="green", choices=["green", "overlap"],
@@ -248,54 +281,56 @@ def main():
     args = ap.parse_args()
 
     if args.cpu_worker:
-        cpu_worker(args.cpu_worker, CPU_SAMPLE_ORBITALS, args.ntau, args.reps)
+        cpu_worker(args.cpu_worker, CPU_SAMPLE_ORBITALS, args.quad, args.reps)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.workload == "batch" and args.impl == "ours":
-        run_batch(args, local)
+    if args.impl == "ours" and args.workload in ("batch", "learned", "cfg3", "uhf", "fftcmp"):
+        import torch
+        import paper_1611_06797_gb300 as L
+        torch.cuda.set_device(local)
+        if args.workload == "batch":
+            out = form_batch(L, torch, local, args.steps, args.warmup)
+        elif args.workload == "cfg3":
+            out = form_cfg3(L, torch, local, args.steps, args.warmup)
+        elif args.workload == "learned":
+            out = run_learned(args, local)
+        elif args.workload == "uhf":
+            out = run_uhf(args, local)
+        else:
+            out = run_fftcmp(args, local)
+        print(json.dumps(out), flush=True)
         return
-    if args.workload == "learned" and args.impl == "ours":
-        run_learned(args, local)
-        return
-    if args.workload == "cfg3" and args.impl == "ours":
-        run_cfg3(args, local)
-        return
-    if args.workload == "uhf" and args.impl == "ours":
-        run_uhf(args, local)
-        return
-    if args.workload == "fftcmp" and args.impl == "ours":
-        run_fftcmp(args, local)
-        return
-    from synth import SPECS
+    from synth import SPECS, build_model_solid
+    import paper_1611_06797_gb300 as L
     spec = SPECS[WORKLOAD]
     n_tau = spec.n_tau
     pairs = spec.n_occ * (spec.n_occ + 1) // 2
 
     if args.impl == "reference":
-        # The reference arm: the FP64 oracle on the host cores, rank 0 only.
+        # The reference arm: the FP64 oracle on the host cores, rank 0 only, on the GPU
+        # arm's workload and quadrature (ltmp2_laplace_grid is host code: no device).
         if rank != 0:
             return
-        cb = run_cpu_baseline(WORKLOAD, n_tau, reps=args.warmup + args.steps, skip=args.warmup)
-        secs = sum(cb["seconds"])
+        s = build_model_solid(spec)
+        tau, w, _ = L.ltmp2_laplace_grid(s.gap, s.width, n_tau)
+        cb = run_cpu_baseline(WORKLOAD, tau, w, reps=args.warmup + args.steps, skip=args.warmup)
         value = cb["value"]
-        vals = [cb]
         out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
-               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * cb["s_per_E_MP2_extrapolated"],
+               "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
                "data": "synthetic", "config": {"workload": _workload_desc(spec)},
-               "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
-                                "sample": vals[0]["sample"]},
+               "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                                "sample": cb["sample"]},
                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(out), flush=True)
         return
 
     import numpy as np
     import torch
-    import paper_1611_06797_gb300 as L
-    from synth import build_model_solid
+    from paper_1611_06797_gb300.shard import sharded_energy
 
     dist = None
     if world > 1:
@@ -310,6 +345,8 @@ def main():
     log(f"fixture {time.time() - t0:.1f} s; gap {s.gap:.5f} Ha, width {s.width:.3f} Ha")
     tau, w, qerr = L.ltmp2_laplace_grid(s.gap, s.width, n_tau)
     peaks, peak_kind = measured_peaks()
+    alu = measured_alu(L)
+    log(f"measured FMA rates: FP64 {alu['fp64']:.3f} TFLOP/s, FP32 {alu['fp32']:.2f} TFLOP/s")
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
@@ -320,6 +357,18 @@ def main():
 
     route = L.ROUTE_OVERLAP if args.route == "overlap" else L.ROUTE_GREEN
     route_info = {}
+
+    def evaluate(ctx):
+        """One E_MP2: the whole loop on one GPU, or this rank's contiguous share of the outer
+        G' loop (Sec. III B) and one FP64 sum all-reduce of (E_d, E_x, e_ij) over NCCL."""
+        if dist is None:
+            return L.ltmp2_energy(ctx, tau, w)
+
+        def all_reduce_sum(v):
+            t = torch.from_numpy(v).to(dev)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            return t.cpu().numpy()
+        return sharded_energy(ctx, tau, w, rank, world, all_reduce_sum)
 
     def time_form(precision, simt=False):
         ctx = L.setup_from_solid(s, precision=precision, real=True, simt_gemm=simt)
@@ -337,7 +386,7 @@ def main():
         for _ in range(args.warmup):
             with torch.cuda.stream(stream):
                 flush.fill_(1.0)
-            L.ltmp2_energy(ctx, tau, w)
+            evaluate(ctx)
         barrier()
         L.ltmp2_reset_stage_times(ctx)
         L.ltmp2_set_profiling(ctx, True)
@@ -351,7 +400,7 @@ def main():
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                res = L.ltmp2_energy(ctx, tau, w)
+                res = evaluate(ctx)
                 b.record(stream)
                 evs.append((a, b))
             barrier()
@@ -366,8 +415,13 @@ def main():
                 "n_prim": n_prim, "clocks": clk.summary()}
 
     def roofline(r, precision, simt):
-        costs = stage_costs(r["sizes"], r["n_prim"], True, n_tau * args.steps, s.n_orb - s.n_occ, aux_nxa(spec))
-        return roofline_of(r["stages"], costs, precision, simt, peaks, peak_kind)
+        n_prim = r["n_prim"]
+        if dist is not None:   # this rank's share of the G' loop
+            from paper_1611_06797_gb300.shard import gprime_share
+            b0, e0 = gprime_share(n_prim, rank, world)
+            n_prim = e0 - b0
+        costs = stage_costs(r["sizes"], n_prim, True, n_tau * args.steps, s.n_orb - s.n_occ, aux_nxa(spec))
+        return roofline_of(r["stages"], costs, precision, simt, peaks, peak_kind, alu)
 
     primary = L.FP64 if args.form == "fp64" else L.FP32
     r = time_form(primary)
@@ -376,7 +430,7 @@ def main():
         t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
-    value = world * pairs * n_tau / (ms_step / 1e3)
+    value = pairs * n_tau / (ms_step / 1e3)   # one E_MP2 per step, on all ranks together
     ed, ex, ep = r["result"]
     sizes = r["sizes"]
 
@@ -386,14 +440,16 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "s_per_E_MP2": ms_step / 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": "f64" if primary == L.FP64 else "c64/tf32x3/f64-sum",
         "data": "synthetic: seeded Gaussian-well model solid, orbitals from dense diagonalisation",
         "config": {"workload": _workload_desc(spec), "n_pw": sizes["n_pw"], "n_aux": sizes["n_aux"],
                    "n_occ": sizes["n_occ"], "grid": sizes["grid"], "n_tau": n_tau, "pairs": pairs,
                    "form": "plain FP64" if primary == L.FP64 else "precision (FP32 FFT, split GEMM)",
                    "time_reversal": True, "l2": "flushed (256 MiB write) before every timed step",
-                   "laplace_max_rel_err": qerr},
+                   "laplace_max_rel_err": qerr,
+                   "parallelism": (f"outer G' loop split over {world} GPUs (contiguous balanced shares), one "
+                                   "FP64 sum all-reduce per E_MP2" if world > 1 else "one GPU")},
         "energy": {"E_d": ed, "E_x": ex, "E": ed + ex, "meV_per_atom": (ed + ex) * HARTREE_TO_MEV / s.n_atoms},
         "roofline": roof,
         "stages": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] // args.steps}
@@ -401,13 +457,14 @@ def main():
         "clocks": r["clocks"],
         "gpu_launches": r["launches"],
         "peaks_source": peak_kind,
+        "alu_peaks_tflops": alu,
     }
     out["config"]["route"] = ("overlap densities stored (paper's steps (i)-(iii))" if route == L.ROUTE_OVERLAP
                               else "per-tau Green's function")
     if route_info:
         out["route"] = {("fp64" if k == L.FP64 else "fp32"): v for k, v in route_info.items()}
 
-    if rank == 0 and not args.no_forms:
+    if rank == 0 and world == 1 and not args.no_forms:
         other = L.FP32 if primary == L.FP64 else L.FP64
         ro = time_form(other)
         ms_o = ro["ms_total"] / args.steps
@@ -429,7 +486,6 @@ def main():
         if other == L.FP32:
             rs = time_form(L.FP32, simt=True)
             ms_s = rs["ms_total"] / args.steps
-            es = (abs(rs["result"][0] - d64[0]) + 0.0) * HARTREE_TO_MEV / s.n_atoms
             out["forms"]["fp32_simt_gemm"] = {
                 "value": pairs * n_tau / (ms_s / 1e3), "s_per_E_MP2": ms_s / 1e3,
                 "speedup_vs_fp64": ms_step / ms_s,
@@ -440,12 +496,13 @@ def main():
                 "gemm": "SIMT FP32 two-level sum",
                 "stages": {k: {"ms_per_step": v["ms"] / args.steps} for k, v in rs["stages"].items()}}
 
-    if rank == 0 and not args.no_e2e:
+    if rank == 0 and world == 1 and not args.no_e2e:
         # end to end through the public API: host arrays in, host results out, every step
         times = []
         h2d = s.coeff.nbytes + s.eps.nbytes + s.miller.nbytes
         d2h = 8 * (2 + s.n_occ * s.n_occ)
-        for k in range(args.steps):
+        reps = min(args.steps, E2E_REPS)
+        for k in range(reps):
             barrier()
             t1 = time.perf_counter()
             ctx = L.setup_from_solid(s, precision=primary, real=True)
@@ -458,14 +515,28 @@ def main():
             times.append(time.perf_counter() - t1)
         out["e2e"] = {"value": pairs * n_tau / statistics.mean(times), "unit": UNIT,
                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                      "s_per_step": statistics.mean(times)}
+                      "s_per_step": statistics.mean(times), "steps": reps}
 
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            out["cpu_baseline"] = run_cpu_baseline(WORKLOAD, n_tau)
+            cb = run_cpu_baseline(WORKLOAD, tau, w)
+            if primary == L.FP64 and ep is not None:
+                out["oracle_check"] = oracle_check(cb, ep)
+            cb.pop("e_pair", None)
+            out["cpu_baseline"] = cb
         except Exception as e:  # reported, never fatal
             out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                    "sample": f"failed: {e}"[:300]}
+
+    if rank == 0 and world == 1 and not args.no_workloads:
+        # the metric's forms on their own workloads, fixed repeat counts (steps / warm-up
+        # below), so that the default run stays within minutes at any --steps
+        out.setdefault("forms", {})
+        for key, fn in (("cfg3_precision", form_cfg3), ("cfg4_batch", form_batch)):
+            try:
+                out["forms"][key] = fn(L, torch, local, 1, 1, alu=alu)
+            except Exception as e:  # reported, never fatal
+                out["forms"][key] = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     if dist is not None:
         dist.barrier()
@@ -474,32 +545,32 @@ def main():
         print(json.dumps(out), flush=True)
 
 
-def run_batch(args, local):
+def form_batch(L, torch, local, steps, warmup, alu=None):
     """Batching form: the 8 uneven model solids (4..48 wells, 16^3..32^3 grids, 8..96
-    occupied, 6..10 tau), precision form, every system's evaluation in one CUDA graph."""
-    import numpy as np
-    import torch
-    import paper_1611_06797_gb300 as L
+    occupied, 6..10 tau), precision form, every system's evaluation in one CUDA graph per
+    step; compared with the same systems evaluated one after another."""
     from synth import SPECS, BATCH_NAMES, build_model_solid
     dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
     t0 = time.time()
-    solids = [build_model_solid(SPECS[n]) for n in BATCH_NAMES]
-    log(f"batch fixtures {time.time() - t0:.1f} s")
+    solids = [build_model_solid(SPECS[n], device="cuda") for n in BATCH_NAMES]
+    t_fix = time.time() - t0
+    log(f"batch fixtures {t_fix:.1f} s")
     quads = [L.ltmp2_laplace_grid(s.gap, s.width, s.spec.n_tau)[:2] for s in solids]
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     ctxs = [L.setup_from_solid(s, precision=L.FP32, real=True) for s in solids]
     for c in ctxs:
         L.ltmp2_set_stream(c, stream)
+    t1 = time.time()
     tune = [L.ltmp2_autotune(c) for c in ctxs]
+    t_tune = time.time() - t1
     units = sum(s.n_occ * (s.n_occ + 1) // 2 * s.spec.n_tau for s in solids)
     # one after another (same kernels, same tuning)
     seq = []
     for c, (t, w) in zip(ctxs, quads):
         L.ltmp2_energy(c, t, w, pairs=False)
     torch.cuda.synchronize()
-    for _ in range(1):
+    for _ in range(steps):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -511,12 +582,12 @@ def run_batch(args, local):
         seq.append(a.elapsed_time(b))
     ref = [L.ltmp2_energy(c, t, w, pairs=False)[:2] for c, (t, w) in zip(ctxs, quads)]
     batch = L.ltmp2_batch_create(ctxs, [q[0] for q in quads], [q[1] for q in quads])
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch.run()
     torch.cuda.synchronize()
     times = []
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+        for _ in range(steps):
             with torch.cuda.stream(stream):
                 flush.fill_(1.0)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -527,6 +598,8 @@ def run_batch(args, local):
             times.append(a.elapsed_time(b))
     ms = sum(times) / len(times)
     maxdiff = max(max(abs(ed[k] - ref[k][0]), abs(ex[k] - ref[k][1])) for k in range(len(solids)))
+    nodes = batch.kernel_nodes()
+    batch.destroy()
     # end to end: setup from host arrays + autotune (cached) + one batch evaluation + destroy
     t1 = time.perf_counter()
     c2 = [L.setup_from_solid(s, precision=L.FP32, real=True) for s in solids]
@@ -535,11 +608,13 @@ def run_batch(args, local):
     L.ltmp2_energy_batch(c2, [q[0] for q in quads], [q[1] for q in quads])
     for c in c2:
         L.ltmp2_destroy(c)
+    for c in ctxs:
+        L.ltmp2_destroy(c)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t1
-    out = {
-        "metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+    return {
+        "metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64/tf32x3/f64-sum",
         "data": "synthetic: 8 seeded Gaussian-well model solids, orbitals from dense diagonalisation",
         "config": {"workload": "batching form: " + ", ".join(
@@ -548,14 +623,13 @@ def run_batch(args, local):
                    "l2": "flushed (256 MiB write) before every timed step",
                    "autotune": [{"slab": t[0], "gemm_variant": t[1]} for t in tune]},
         "sequential_ms_per_step": sum(seq) / len(seq), "speedup_vs_sequential": (sum(seq) / len(seq)) / ms,
-        "max_abs_diff_vs_sequential_Ha": maxdiff, "graph_kernel_nodes": batch.kernel_nodes(),
-        "gpu_launches": batch.kernel_nodes() * args.steps, "graph_launches": args.steps, "clocks": clk.summary(),
+        "max_abs_diff_vs_sequential_Ha": maxdiff, "graph_kernel_nodes": nodes,
+        "gpu_launches": nodes * steps, "graph_launches": steps, "clocks": clk.summary(),
+        "setup_s": {"fixtures": t_fix, "autotune": t_tune},
         "e2e": {"value": units / e2e_s, "unit": UNIT, "s_per_step": e2e_s,
                 "h2d_bytes_per_step": int(sum(s.coeff.nbytes + s.eps.nbytes + s.miller.nbytes for s in solids)),
                 "d2h_bytes_per_step": 16 * len(solids)},
     }
-    batch.destroy()
-    print(json.dumps(out), flush=True)
 
 
 def run_learned(args, local):
@@ -635,27 +709,26 @@ def run_learned(args, local):
         "mlp": {"train_loss_std_units": loss, "train_s": t_train, "label_s": t_label},
         "weakest_10pct_screened": diag10,
     }
-    print(json.dumps(out), flush=True)
+    return out
 
 
-def run_cfg3(args, local):
+def form_cfg3(L, torch, local, steps, warmup, alu=None):
     """Precision form on its own workload: 64 wells, 36^3 grid, 10059 plane waves, 128
     occupied orbitals, 10 Laplace points (FP32 FFTs, 3xTF32 tcgen05 GEMM, FP64 sums).
-    The full FP64 evaluation of this system takes about 45 minutes on one GB300, so the
+    A full FP64 evaluation of this system takes about 45 minutes on one GB300, so the
     error against the FP64 path is measured on the same inputs over four spread ranges
-    of the outer G' loop (ltmp2_energy_partial, 32 of 2724 primary G'), where both
-    paths run; it is reported as meV/atom on the sample and scaled to the full G' loop
-    as if every sampled error had the same sign (a conservative estimate)."""
-    import numpy as np
-    import torch
-    import paper_1611_06797_gb300 as L
+    of the outer G' loop (ltmp2_energy_partial, 24 of 2724 primary G'), where both paths
+    run; it is reported in meV/atom on the sample and scaled to the full G' loop as if
+    every sampled error had the same sign (a conservative estimate)."""
     from synth import SPECS, build_model_solid
     spec = SPECS["cfg3"]
     dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
+    if alu is None:
+        alu = measured_alu(L)
     t0 = time.time()
-    s = build_model_solid(spec)
-    log(f"cfg3 fixture {time.time() - t0:.1f} s; gap {s.gap:.6f} Ha, width {s.width:.3f} Ha")
+    s = build_model_solid(spec, device="cuda")
+    t_fix = time.time() - t0
+    log(f"cfg3 fixture {t_fix:.1f} s; gap {s.gap:.6f} Ha, width {s.width:.3f} Ha")
     n_tau = spec.n_tau
     tau, w, qerr = L.ltmp2_laplace_grid(s.gap, s.width, n_tau)
     peaks, peak_kind = measured_peaks()
@@ -664,7 +737,7 @@ def run_cfg3(args, local):
     pairs = s.n_occ * (s.n_occ + 1) // 2
     ctx = L.setup_from_solid(s, precision=L.FP32, real=True)
     L.ltmp2_set_stream(ctx, stream)
-    for _ in range(args.warmup):   # one Laplace point per warm-up step
+    for _ in range(warmup):   # one Laplace point per warm-up step
         L.ltmp2_energy(ctx, tau[:1], w[:1], pairs=False)
     torch.cuda.synchronize()
     L.ltmp2_reset_stage_times(ctx)
@@ -673,7 +746,7 @@ def run_cfg3(args, local):
     evs = []
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
-        for _ in range(args.steps):
+        for _ in range(steps):
             with torch.cuda.stream(stream):
                 flush.fill_(1.0)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -683,16 +756,16 @@ def run_cfg3(args, local):
             evs.append((a, b))
         torch.cuda.synchronize()
     L.ltmp2_set_profiling(ctx, False)
-    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
-    launches = (L.ltmp2_kernel_launches(ctx) - n0) // args.steps
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    launches = (L.ltmp2_kernel_launches(ctx) - n0) // steps
     st = L.ltmp2_stage_times(ctx)
     sizes = L.ltmp2_sizes(ctx)
     n_prim = L.ltmp2_num_primary_gprime(ctx)
     tuning = L.ltmp2_get_tuning(ctx)
-    costs = stage_costs(sizes, n_prim, True, n_tau * args.steps, s.n_orb - s.n_occ, aux_nxa(spec))
-    roof = roofline_of(st, costs, L.FP32, False, peaks, peak_kind)
+    costs = stage_costs(sizes, n_prim, True, n_tau * steps, s.n_orb - s.n_occ, aux_nxa(spec))
+    roof = roofline_of(st, costs, L.FP32, False, peaks, peak_kind, alu)
     # FP32 vs FP64 on the same inputs, over sampled G' ranges
-    width = 8
+    width = 6
     starts = [0, n_prim // 3, (2 * n_prim) // 3, n_prim - width]
     t1 = time.time()
     c64 = L.setup_from_solid(s, precision=L.FP64, real=True)
@@ -712,9 +785,9 @@ def run_cfg3(args, local):
     err = {"E_d": abs(samp["fp32"][0] - samp["fp64"][0]) * per_atom,
            "E_x": abs(samp["fp32"][1] - samp["fp64"][1]) * per_atom,
            "E": abs(sum(samp["fp32"]) - sum(samp["fp64"])) * per_atom}
-    out = {
-        "metric": METRIC, "value": pairs * n_tau / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "s_per_E_MP2": ms / 1e3, "higher_is_better": True,
+    return {
+        "metric": METRIC, "value": pairs * n_tau / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms, "s_per_E_MP2": ms / 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64/tf32x3/f64-sum",
         "data": "synthetic: seeded Gaussian-well model solid, orbitals from dense diagonalisation",
         "config": {"workload": _workload_desc(spec), "n_pw": sizes["n_pw"], "n_aux": sizes["n_aux"],
@@ -724,9 +797,10 @@ def run_cfg3(args, local):
                    "laplace_max_rel_err": qerr, "tuning": tuning},
         "energy": {"E_d": ed, "E_x": ex, "E": ed + ex, "meV_per_atom": (ed + ex) * per_atom},
         "roofline": roof,
-        "stages": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] // args.steps}
+        "stages": {k: {"ms_per_step": v["ms"] / steps, "launches_per_step": v["launches"] // steps}
                    for k, v in st.items()},
         "clocks": clk.summary(), "gpu_launches": launches, "peaks_source": peak_kind,
+        "setup_s": {"fixture": t_fix},
         "err_vs_fp64_sampled": {
             "sample": f"primary G' [{', '.join(f'{g}..{g + width - 1}' for g in starts)}] of {n_prim}, all "
                       f"{n_tau} tau, all pairs; FP32 and FP64 paths on the same inputs",
@@ -738,7 +812,6 @@ def run_cfg3(args, local):
                          "sample": "not run: one occupied pair of this system costs the oracle ~5e11 complex "
                                    "multiply-adds (N_v^2 N_G), beyond a bounded sample"},
     }
-    print(json.dumps(out), flush=True)
 
 
 def run_uhf(args, local):
@@ -750,7 +823,6 @@ def run_uhf(args, local):
     from synth import SPECS, spin_polarized_pair
     spec = SPECS["cfg2"]
     dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
     a, b = spin_polarized_pair(spec, 33, 31)
     n_tau = spec.n_tau
     lo, hi = min(a.gap, b.gap), max(a.width, b.width)
@@ -803,7 +875,7 @@ def run_uhf(args, local):
                                "E_x": abs(r32["result"][1] - ex) * per_atom,
                                "E": abs(r32["result"][0] + r32["result"][1] - ed - ex) * per_atom}}},
     }
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def run_fftcmp(args, local):
@@ -884,7 +956,7 @@ def run_fftcmp(args, local):
             "ours_ms_per_launch": st["ms"] / max(1, st["launches"]),
             "ours": "k_rgemm FP64 (SIMT)" if prec == L.FP64 else "tcgen05 3xTF32 (k_tc_cgemm_stacked + packing)"}
         del A, B, C
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def _workload_desc(spec):

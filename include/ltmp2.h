@@ -397,6 +397,13 @@ int ltmp2_sum_partials(int n, int n_occ, const double *e, const double *pd, cons
 int ltmp2_energy_noalloc(const ltmp2_system *sys, int n_tau, const double *tau, const double *w,
                          double *e_direct, double *e_exchange, double *e_pair, void *stream);
 
+/* Measured FMA rate of the current GPU's CUDA cores (the paper has no counterpart):
+ * independent FMA chains in every thread of a full grid, timed with CUDA events, best of
+ * five launches after one warm-up.  precision: LTMP2_FP64 or LTMP2_FP32; *tflops receives
+ * 2 x FMAs / s / 1e12.  The roofline denominators of the CUDA-core kernels.  Allocates and
+ * frees a small device buffer.  Errors: INVALID_ARG, OOM, CUDA.                      */
+int ltmp2_alu_peak(int precision, double *tflops);
+
 /* Free all device memory of ctx.  NULL is ignored.                              */
 void ltmp2_destroy(ltmp2_ctx *ctx);
 

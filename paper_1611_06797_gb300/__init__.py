@@ -6,7 +6,7 @@ library's CUDA kernels.  See ``include/ltmp2.h`` for the contract.
 from .ltmp2 import (Context, Ltmp2Error, LIB_PATH, load_library, ltmp2_setup, ltmp2_set_stream,
                     ltmp2_laplace_grid, ltmp2_energy, ltmp2_energy_partial, ltmp2_num_primary_gprime, ltmp2_set_slab_size,
                     ltmp2_sizes, ltmp2_last_imag, ltmp2_kernel_launches, ltmp2_set_profiling, ltmp2_stage_times,
-                    ltmp2_fingerprint, ltmp2_sum_partials, ltmp2_reset_stage_times, ltmp2_destroy, ltmp2_energy_noalloc,
+                    ltmp2_fingerprint, ltmp2_sum_partials, ltmp2_alu_peak, ltmp2_reset_stage_times, ltmp2_destroy, ltmp2_energy_noalloc,
                     ltmp2_set_extrapolation, ltmp2_level_energies, ltmp2_extrapolate,
                     ltmp2_set_route, ROUTE_GREEN, ROUTE_OVERLAP, ltmp2_energy_uhf, ltmp2_selftest_wait,
                     ltmp2_autotune, ltmp2_get_tuning, ltmp2_set_tuning, ltmp2_batch_create,
@@ -16,7 +16,7 @@ from .ltmp2 import (Context, Ltmp2Error, LIB_PATH, load_library, ltmp2_setup, lt
 __all__ = ["Context", "Ltmp2Error", "LIB_PATH", "load_library", "ltmp2_setup", "ltmp2_set_stream",
            "ltmp2_laplace_grid", "ltmp2_energy", "ltmp2_energy_partial", "ltmp2_num_primary_gprime", "ltmp2_set_slab_size",
            "ltmp2_sizes", "ltmp2_last_imag", "ltmp2_kernel_launches", "ltmp2_set_profiling", "ltmp2_stage_times",
-           "ltmp2_fingerprint", "ltmp2_sum_partials", "ltmp2_reset_stage_times", "ltmp2_destroy", "ltmp2_energy_noalloc",
+           "ltmp2_fingerprint", "ltmp2_sum_partials", "ltmp2_alu_peak", "ltmp2_reset_stage_times", "ltmp2_destroy", "ltmp2_energy_noalloc",
            "ltmp2_set_extrapolation", "ltmp2_level_energies", "ltmp2_extrapolate",
            "ltmp2_set_route", "ROUTE_GREEN", "ROUTE_OVERLAP", "ltmp2_energy_uhf", "ltmp2_selftest_wait",
            "ltmp2_autotune", "ltmp2_get_tuning", "ltmp2_set_tuning", "ltmp2_batch_create",

@@ -68,6 +68,7 @@ def load_library():
         "ltmp2_set_profiling": (ctypes.c_int, [vp, ctypes.c_int]),
         "ltmp2_kernel_launches": (ctypes.c_int, [vp, P(ctypes.c_longlong)]),
         "ltmp2_fingerprint": (ctypes.c_int, [vp, P(ctypes.c_ulonglong)]),
+        "ltmp2_alu_peak": (ctypes.c_int, [ctypes.c_int, dp]),
         "ltmp2_sum_partials": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp]),
         "ltmp2_stage_times": (ctypes.c_int, [vp, ctypes.c_int, dp, P(ctypes.c_longlong)]),
         "ltmp2_reset_stage_times": (ctypes.c_int, [vp]),
@@ -252,6 +253,13 @@ def ltmp2_sum_partials(e, pd, px):
     _check(load_library().ltmp2_sum_partials(n, no, _dp(e), _dp(pd), _dp(px), _dp(eo), _dp(pdo), _dp(pxo)),
            "ltmp2_sum_partials")
     return float(eo[0]), float(eo[1]), pdo, pxo
+
+
+def ltmp2_alu_peak(precision: int) -> float:
+    """Measured FMA rate (TFLOP/s) of the current GPU's CUDA cores in FP64 or FP32."""
+    t = np.zeros(1)
+    _check(load_library().ltmp2_alu_peak(int(precision), _dp(t)), "ltmp2_alu_peak")
+    return float(t[0])
 
 
 def ltmp2_set_profiling(ctx: Context, on: bool) -> None:

@@ -1,6 +1,7 @@
-"""The N > 1 path on the CPU: world size 2 over gloo.  Each rank evaluates its share of the
-outer G' loop of the working form (Sec. III B) and one sum all-reduce combines them; the
-result equals the single-process energy.  The bench's timing reduction (max over ranks)
+"""The N > 1 path on the CPU: world size 2 over gloo.  Each rank runs the benchmark's own
+sharded evaluation (``shard.sharded_energy``: its share of the outer G' loop, Sec. III B,
+and one FP64 sum all-reduce), with the oracle's working form standing in for the library's
+partial-range call; the result equals the single-process energy.  The bench's timing reduction (max over ranks)
 is checked the same way.  No GPU is used."""
 import os
 import socket
@@ -9,7 +10,7 @@ from datetime import timedelta
 import numpy as np
 import pytest
 
-from paper_1611_06797_gb300.shard import gprime_share
+from paper_1611_06797_gb300.shard import gprime_share, sharded_energy
 
 
 def test_gprime_share_partitions_the_loop():
@@ -42,14 +43,24 @@ def _rank_main(rank, world, port, out):
     o = OracleSystem.from_solid(solid("tiny"))
     tau, w = sinc_laplace_quadrature(3, *denominator_range(o))
     n = len(aux_set(o)[0])
-    b, e = gprime_share(n, rank, world)
-    ed, ex = _working_form(o, tau, w, range(b, e))
-    t = torch.tensor([ed, ex], dtype=torch.float64)
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+
+    # the library's partial-range call, stood in for by the oracle's working form on the
+    # same G' range (pair matrices: E_d and E_x on the diagonal entry (0, 0) / (1, 1))
+    def partial(sys_, tau_, w_, b, e):
+        ed_, ex_ = _working_form(sys_, tau_, w_, range(b, e))
+        pd, px = np.zeros((2, 2)), np.zeros((2, 2))
+        pd[0, 0], px[1, 1] = ed_, ex_
+        return ed_, ex_, pd, px
+
+    def all_reduce_sum(v):
+        t = torch.from_numpy(v)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return t.numpy()
+    ed, ex, ep = sharded_energy(o, tau, w, rank, world, all_reduce_sum, partial=partial, n_prim=n, n_occ=2)
     ms = torch.tensor([10.0 + rank], dtype=torch.float64)      # per-rank step time
     dist.all_reduce(ms, op=dist.ReduceOp.MAX)
     if rank == 0:
-        out.put((float(t[0]), float(t[1]), float(ms[0])))
+        out.put((ed, ex, float(ms[0]), float(ep[0, 0]), float(ep[1, 1])))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -72,9 +83,10 @@ def test_two_rank_gprime_split_over_gloo():
     for p in alive:
         p.kill()
     assert not alive and all(p.exitcode == 0 for p in procs)
-    ed, ex, ms = out.get(timeout=10)
+    ed, ex, ms, ep00, ep11 = out.get(timeout=10)
     o = OracleSystem.from_solid(solid("tiny"))
     tau, w = sinc_laplace_quadrature(3, *denominator_range(o))
     ed1, ex1 = _working_form(o, tau, w)
     assert abs(ed - ed1) < 1e-13 * abs(ed1) and abs(ex - ex1) < 1e-13 * abs(ex1)
+    assert abs(ep00 - ed1) < 1e-13 * abs(ed1) and abs(ep11 - ex1) < 1e-13 * abs(ex1)
     assert ms == 11.0
