@@ -404,3 +404,131 @@ def uhf_mp2_energy(sa: OracleSystem, sb: OracleSystem, D: Callable[[np.ndarray],
                         e += xx
                     part["ab" if x != y else ("aa" if x == 0 else "bb")] += e
     return {"E_d": E_d, "E_x": E_x, "E": E_d + E_x, "E_aa": part["aa"], "E_bb": part["bb"], "E_ab": part["ab"]}
+
+
+# ---------------------------------------------------------------------------
+# k-point sampling (Sec. II C-D): Eqs. (MP2direct), (MP2exchange) per unit cell with the
+# integrals of Eq. (2eIPLWV) and crystal-momentum conservation k1 + k2 = k3 + k4 + G
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class KPointOracleSystem:
+    """Closed-shell mean field on a Gamma-centred k-mesh (k = sum_i kappa_i / n_i b_i).
+
+    lattice (3,3) unit-cell rows; grid (3,) unit-cell FFT grid; mesh (3,); kappa (N_k,3);
+    miller (N_pw,3) plane-wave set shared by every k; coeff (N_k, N_orb, N_pw) with
+    phi_nk = e^{ikr} sum_m c_nk(m) e^{iG_m r} / sqrt(N_k Omega_0); eps (N_k, N_orb); n_occ
+    per k; ecut_aux (Ha): the auxiliary set is {Q : |Q|^2/2 <= E_aux, Q != 0} over all
+    momentum transfers Q = G + k' - k.
+    """
+    lattice: np.ndarray
+    grid: np.ndarray
+    mesh: np.ndarray
+    kappa: np.ndarray
+    miller: np.ndarray
+    coeff: np.ndarray
+    eps: np.ndarray
+    n_occ: int
+    ecut_aux: float
+
+    @property
+    def n_k(self) -> int:
+        return int(self.kappa.shape[0])
+
+    @property
+    def omega0(self) -> float:
+        return abs(float(np.linalg.det(self.lattice)))
+
+    @property
+    def recip(self) -> np.ndarray:
+        return 2.0 * math.pi * np.linalg.inv(self.lattice).T
+
+    @classmethod
+    def from_solid(cls, ks, ecut_aux: Optional[float] = None) -> "KPointOracleSystem":
+        if ecut_aux is None:
+            ecut_aux = 2.0 * ks.ecut / 3.0
+        return cls(np.asarray(ks.lattice, float), np.asarray(ks.grid, int), np.asarray(ks.mesh, int),
+                   np.asarray(ks.kappa, int), np.asarray(ks.miller, int), np.asarray(ks.coeff, complex),
+                   np.asarray(ks.eps, float), int(ks.n_occ), float(ecut_aux))
+
+
+def kpoint_aux_class(sys: KPointOracleSystem, delta: np.ndarray):
+    """The auxiliary momentum transfers of one class: Q = g + delta / mesh for the integer
+    vector delta = kappa' - kappa (each component in (-n_i, n_i)), |Q|^2/2 <= E_aux, Q != 0.
+    Returns integer g (n,3), the supercell Miller indices M = mesh g + delta (n,3), and
+    v(Q) = 4 pi / |Q|^2 (Eq. 2eIPLWV, Eq. CoulombFourier)."""
+    B = sys.recip
+    gmax = math.sqrt(2.0 * sys.ecut_aux)
+    lim = [int(math.floor(gmax * np.linalg.norm(sys.lattice[k]) / (2 * math.pi))) + 2 for k in range(3)]
+    rng = [np.arange(-l, l + 1) for l in lim]
+    g = np.stack(np.meshgrid(*rng, indexing="ij"), -1).reshape(-1, 3)
+    s = np.asarray(delta, float) / sys.mesh
+    Q = (g + s[None, :]) @ B
+    q2 = (Q ** 2).sum(1)
+    keep = (0.5 * q2 <= sys.ecut_aux) & (q2 > 1e-20)
+    g, q2 = g[keep], q2[keep]
+    if len(np.unique(_flat(g, sys.grid))) != len(g):
+        raise ValueError("auxiliary sphere does not fit the FFT grid")
+    return g, g * sys.mesh[None, :] + np.asarray(delta)[None, :], 4.0 * math.pi / q2
+
+
+def kpoint_overlap_densities(sys: KPointOracleSystem, kl: int, left: Sequence[int], kr: int,
+                             right: Sequence[int], gvec: np.ndarray) -> np.ndarray:
+    """rho[l, r, g] = sum_p conj(c_{l,kl}(p)) c_{r,kr}((G_p + g) mod grid): the overlap density
+    <l kl| e^{-iQr} |r kr> of Eq. (OverlapDens) at Q = g + k_r - k_l, grid-discrete like the
+    Gamma-point densities (the wrap of G_p + g on the FFT grid)."""
+    n = sys.grid
+    ngrid = int(np.prod(n))
+    cgrid = np.zeros((len(right), ngrid), dtype=np.complex128)
+    cgrid[:, _flat(sys.miller, n)] = sys.coeff[kr][list(right)]
+    cl = np.conj(sys.coeff[kl][list(left)])
+    out = np.empty((len(left), len(right), len(gvec)), dtype=np.complex128)
+    for gi, gg in enumerate(gvec):
+        out[:, :, gi] = cl @ cgrid[:, _flat(sys.miller + gg[None, :], n)].T
+    return out
+
+
+def kpoint_mp2_energy(sys: KPointOracleSystem, D: Callable[[np.ndarray], np.ndarray]):
+    """Closed-shell MP2 per unit cell on the k-mesh, explicit sums over k1, k2, k3 (k4 fixed
+    by crystal-momentum conservation, Eq. 2eIPLWV), i, j, a, b:
+       <i k1, j k2|a k3, b k4> = (1/Omega) sum_Q v(Q) rho_{i k1, a k3}(Q) rho_{j k2, b k4}(-Q),
+       Omega = N_k Omega_0,  Q over the class of k3 - k1,
+       E_d = (2 / N_k) sum |<ij|ab>|^2 D,   E_x = -(1 / N_k) sum <ij|ab> <ab|ji> D,
+    <ab|ji> = conj(<ij|ba>), D = D(e_{i k1} + e_{j k2} - e_{a k3} - e_{b k4}).
+    Returns E_d, E_x, E (Ha per unit cell) and pair matrices e_d, e_x over composite
+    occupied indices k n_occ + i."""
+    nk, no = sys.n_k, sys.n_occ
+    norb = sys.coeff.shape[1]
+    occ, virt = list(range(no)), list(range(no, norb))
+    index = {tuple(k): n for n, k in enumerate(sys.kappa.tolist())}
+    omega = nk * sys.omega0
+    cache = {}
+
+    def dens(k, kp):
+        if (k, kp) not in cache:
+            g, M, v = kpoint_aux_class(sys, sys.kappa[kp] - sys.kappa[k])
+            rho = kpoint_overlap_densities(sys, k, occ, kp, virt, g)
+            cache[(k, kp)] = (rho, M, v, {tuple(m): q for q, m in enumerate(M.tolist())})
+        return cache[(k, kp)]
+
+    e_d = np.zeros((nk * no, nk * no))
+    e_x = np.zeros((nk * no, nk * no))
+    for k1 in range(nk):
+        for k2 in range(nk):
+            for k3 in range(nk):
+                k4 = index[tuple(np.mod(sys.kappa[k1] + sys.kappa[k2] - sys.kappa[k3], sys.mesh))]
+                rA, MA, vA, _ = dens(k1, k3)          # i k1 -> a k3 at Q
+                rB, _, _, dB = dens(k2, k4)           # j k2 -> b k4 at -Q
+                rC, MC, vC, _ = dens(k1, k4)          # i k1 -> b k4 at Q   (exchange integral)
+                rD, _, _, dD = dens(k2, k3)           # j k2 -> a k3 at -Q
+                nb = [dB[tuple(-m)] for m in MA]
+                nd = [dD[tuple(-m)] for m in MC]
+                ev3, ev4 = sys.eps[k3, no:], sys.eps[k4, no:]
+                for i in range(no):
+                    for j in range(no):
+                        K = (rA[i] * (vA / omega)[None, :]) @ rB[j][:, nb].T        # <i k1, j k2|a k3, b k4>[a, b]
+                        Kx = (rC[i] * (vC / omega)[None, :]) @ rD[j][:, nd].T       # <i k1, j k2|b k4, a k3>[b, a]
+                        Dab = D(sys.eps[k1, i] + sys.eps[k2, j] - ev3[:, None] - ev4[None, :])
+                        e_d[k1 * no + i, k2 * no + j] += 2.0 * float(np.sum((K.real ** 2 + K.imag ** 2) * Dab)) / nk
+                        e_x[k1 * no + i, k2 * no + j] -= float(np.sum(K * np.conj(Kx.T) * Dab).real) / nk
+    Ed, Ex = float(e_d.sum()), float(e_x.sum())
+    return {"E_d": Ed, "E_x": Ex, "E": Ed + Ex, "e_d": e_d, "e_x": e_x}

@@ -15,7 +15,11 @@
 
 namespace ltmp2 {
 
-template <typename T> struct cpx { T x, y; };
+// Aligned to its full size, so that a complex value moves as one 64-bit (float) or 128-bit
+// (double) access in shared and global memory: with 4-byte alignment every complex load
+// split into two 32-bit accesses, which 2-way bank-conflict at the even word strides of the
+// plane and column layouts.
+template <typename T> struct alignas(2 * sizeof(T)) cpx { T x, y; };
 
 template <typename T> __host__ __device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
 template <typename T> __host__ __device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }

@@ -525,12 +525,13 @@ __global__ void k_planes2(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> 
 // occupied i:
 //  x pass : thread (i, y) loads row y of phi_i (from the plane-transposed copy, coalesced
 //           across the warp, L2 resident) and of w_j^{G'} (shared), multiplies conj(phi_i) w
-//           in registers,
-//           transforms, and keeps only the m1 of the aux range: a compact
+//           in registers, transforms, and keeps only the m1 of the aux range: a compact
 //           [ib][N][nxa] intermediate (nxa is odd, so the row pitch spreads the banks);
-//  y pass : thread (i, m1) transforms its column and writes the aux-disk entries,
-//           compactly in disk order;
-//  copy   : coalesced copy of the compact plane to tbuf[(col, i)][z][d_aux].
+//  y pass : thread (i, m1) transforms its column and writes it back in place (consecutive
+//           threads, consecutive addresses);
+//  copy   : the aux-disk entries gathered through a per-block table (consecutive disk
+//           columns of one m1 are nxa apart: no bank conflicts) and written coalesced to
+//           tbuf[(col, i)][z][d_aux].
 template <typename T, int N>
 __global__ void k_planes3(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> *__restrict__ tbuf) {
   constexpr int P = N + 1;
@@ -539,22 +540,17 @@ __global__ void k_planes3(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> 
   const int nxa = p.mxhi_aux - p.mxlo_aux + 1;   // odd: the aux sphere is symmetric
   const int nd = p.n_daux;
   cpx<T> *wk = xp + N * P;                    // [ib][N][nxa]
-  cpx<T> *ob = wk + (size_t)ib * N * nxa;     // [ib][nd]
-  int *xs = reinterpret_cast<int *>(ob + (size_t)ib * nd);   // per m1: first disk column, m2 lo, m2 hi
+  int *ytab = reinterpret_cast<int *>(wk + (size_t)ib * N * nxa);   // [nd] position of disk column d in a plane of wk
   const int z = blockIdx.x, col = blockIdx.y;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int no = p.n_occ;
-  for (int t = tid; t < nxa; t += nth) { xs[3 * t] = 0; xs[3 * t + 1] = 1; xs[3 * t + 2] = 0; }
-  __syncthreads();
+  const int mlo = p.mxlo_aux, mhi = p.mxhi_aux;
   for (int d = tid; d < nd; d += nth) {
     const int4 c = p.daux[d];
-    const int xa = c.x - p.mxlo_aux;
-    if (d == 0 || p.daux[d - 1].x != c.x) { xs[3 * xa] = d; xs[3 * xa + 1] = c.y; }
-    if (d == nd - 1 || p.daux[d + 1].x != c.x) xs[3 * xa + 2] = c.y;
+    ytab[d] = wrapn(c.y, N) * nxa + (c.x - mlo);
   }
   plane_inverse<T, N>(p, z1 + ((size_t)col * N + z) * p.n_dorb, xp);   // ends with a barrier
   const cpx<T> *ut = (const cpx<T> *)p.ut;
-  const int mlo = p.mxlo_aux, mhi = p.mxhi_aux;
   const int jcol = col % no;
   const int ni = p.keep_count ? p.keep_count[jcol] : no;
   const int *ilist = p.keep_count ? p.keep_list + (size_t)jcol * no : nullptr;
@@ -581,25 +577,21 @@ __global__ void k_planes3(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> 
     __syncthreads();
     for (int t = tid; t < nb * nxa; t += nth) {
       const int il = t / nxa, xa = t - il * nxa;
-      const cpx<T> *src = wk + (size_t)il * N * nxa + xa;
+      cpx<T> *src = wk + (size_t)il * N * nxa + xa;
       cpx<T> b[N];
 #pragma unroll
       for (int k = 0; k < N; ++k) b[k] = src[k * nxa];
       LineFFT<T, N, -1>::run(b);
-      const int d0 = xs[3 * xa], lo = xs[3 * xa + 1], hi = xs[3 * xa + 2];
-      cpx<T> *o = ob + (size_t)il * nd + d0 - lo;
 #pragma unroll
-      for (int k = 0; k < N; ++k) {
-        const int m = freq_of<N>(k);
-        if (m >= lo && m <= hi) o[m] = b[k];
-      }
+      for (int k = 0; k < N; ++k) src[k * nxa] = b[k];
     }
     __syncthreads();
     for (int e = tid; e < nb * nd; e += nth) {
       const int il = e / nd, d = e - il * nd;
       const size_t item = (size_t)col * no + (ilist ? ilist[i0 + il] : i0 + il);
-      tbuf[(item * N + z) * nd + d] = ob[(size_t)il * nd + d];
+      tbuf[(item * N + z) * nd + d] = wk[(size_t)il * N * nxa + ytab[d]];
     }
+    __syncthreads();
   }
 }
 

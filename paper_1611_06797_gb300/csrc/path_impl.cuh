@@ -24,8 +24,8 @@ template <typename T> static int plane_ib_default(const Plan &p, int kernel) {
   } else if (kernel == 2) {
     // four planes per block: small blocks, many resident per SM (best on the 24^3 workload
     // in both precisions among 2..16)
-    const size_t per = ((size_t)n * nxa + p.n_daux) * sizeof(cpx<T>);
-    ib = (int)((100 * 1024 - plane - 3 * sizeof(int) * nxa - 64) / per);
+    const size_t per = (size_t)n * nxa * sizeof(cpx<T>);
+    ib = (int)((100 * 1024 - plane - sizeof(int) * p.n_daux - 64) / per);
     if (ib > 4) ib = 4;
   } else {
     const size_t per = plane + (size_t)p.n_daux * sizeof(cpx<T>);
@@ -42,8 +42,7 @@ template <typename T> static size_t plane_smem(const Plan &p, int kernel, int ib
   const size_t plane = (size_t)n * (n + 1) * sizeof(cpx<T>);
   const int nxa = p.mxhi_aux - p.mxlo_aux + 1;
   if (kernel == 0) return plane * (1 + ib);
-  if (kernel == 2)
-    return plane + (size_t)ib * ((size_t)n * nxa + p.n_daux) * sizeof(cpx<T>) + 3 * sizeof(int) * nxa;
+  if (kernel == 2) return plane + (size_t)ib * n * nxa * sizeof(cpx<T>) + sizeof(int) * p.n_daux;
   return plane * (1 + ib) + (size_t)ib * p.n_daux * sizeof(cpx<T>) + 3 * sizeof(int) * nxa;
 }
 

@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(kThreads) k_fma_chains(int iters, T b, T c, T 
   T x[kChains];
 #pragma unroll
   for (int k = 0; k < kChains; ++k) x[k] = (T)(threadIdx.x + k) * (T)1e-3;
+#pragma unroll 4
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
     for (int k = 0; k < kChains; ++k) x[k] = fma(x[k], b, c);
@@ -44,7 +45,7 @@ template <typename T> int measure(int iters, double *tflops) {
   if (cudaMalloc(&out, sizeof(T) * (size_t)blocks * kThreads) != cudaSuccess) return LTMP2_ERR_OOM;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) rc = LTMP2_ERR_CUDA;
   float best = 1e30f;
-  for (int rep = 0; rep < 6 && !rc; ++rep) {   // the first launch is a warm-up
+  for (int rep = 0; rep < 6 && !rc; ++rep) {   // the first launch is a warm-up (and lets the clock settle)
     cudaEventRecord(a);
     k_fma_chains<T><<<blocks, kThreads>>>(iters, (T)0.9999999, (T)1e-7, out);
     cudaEventRecord(b);
@@ -67,7 +68,8 @@ template <typename T> int measure(int iters, double *tflops) {
 
 extern "C" int ltmp2_alu_peak(int precision, double *tflops) {
   if (!tflops) return LTMP2_ERR_INVALID_ARG;
-  if (precision == LTMP2_FP64) return measure<double>(2048, tflops);
-  if (precision == LTMP2_FP32) return measure<float>(65536, tflops);
+  // about 0.1 s per launch at the nominal rates
+  if (precision == LTMP2_FP64) return measure<double>(1 << 15, tflops);
+  if (precision == LTMP2_FP32) return measure<float>(1 << 20, tflops);
   return LTMP2_ERR_INVALID_ARG;
 }
