@@ -404,6 +404,54 @@ int ltmp2_energy_noalloc(const ltmp2_system *sys, int n_tau, const double *tau, 
  * frees a small device buffer.  Errors: INVALID_ARG, OOM, CUDA.                      */
 int ltmp2_alu_peak(int precision, double *tflops);
 
+/* ---------------------------------------------------------------- k-point sampling
+ * Sec. II C-D: the MP2 energy per unit cell with the Brillouin zone sampled on a
+ * Gamma-centred n1 x n2 x n3 mesh, k = sum_i (kappa_i / n_i) b_i, kappa_i = 0 .. n_i - 1
+ * (k-point index (kappa_1 n_2 + kappa_2) n_3 + kappa_3).  Bloch orbitals
+ * phi_{nk}(r) = e^{ikr} sum_m c_{nk}(m) e^{iG_m r} / sqrt(N_k Omega_0) over one plane-wave
+ * set shared by every k; the two-electron integrals (Eq. 2eIPLWV) conserve crystal
+ * momentum, k1 + k2 = k3 + k4 + G, and carry the shifted Coulomb kernel
+ * 4 pi / |G + k3 - k1|^2.  With the outer loop over the momentum transfers
+ * Q' = G' + q' of the Born-von Karman supercell, every transformed state
+ * w_{j k}^{(Q' tau)} = e^{(e_{jk}-mu) tau} P_v^{k - q'}(tau) e^{-iQ'r} |j k> (Eqs. StateDec,
+ * DecompCoeff) uses the Green's function of its own k - q', and the exchange and direct
+ * contractions (Eqs. xLTMP2, dLTMP2Compact) run over every occupied pair (i k1, j k2): the
+ * N_k^3 loop over (k1, k2, q).  The energies equal the Gamma-point energies of the
+ * supercell divided by N_k.  General complex orbitals (no time-reversal shortcut).
+ *
+ *   lattice, grid       unit cell and its FFT grid, as in ltmp2_system
+ *   mesh [3]            n1, n2, n3 >= 1, N_k = n1 n2 n3 <= 64
+ *   n_pw, miller        the plane-wave set of every k ([n_pw][3]; each |m_i| < n_i/2, every
+ *                       (m1, m2) column one contiguous m3 range; no inversion symmetry needed)
+ *   n_orb, n_occ        orbitals and doubly occupied orbitals per k (1 <= n_occ < n_orb <= n_pw)
+ *   coeff               [N_k][n_orb][n_pw] complex128 (re, im), orthonormal rows per k
+ *   eps                 [N_k][n_orb] Hartree, non-decreasing per k; the indirect gap
+ *                       min_k e_{n_occ, k} - max_k e_{n_occ - 1, k} must be >= 1e-6 Ha
+ *   ecut_aux            E_aux (Ha) of the momentum transfers |Q|^2 / 2; <= 0: 2/3 of the
+ *                       largest |G_m|^2 / 2
+ *   precision           LTMP2_FP64 or LTMP2_FP32 (CUDA-core products in both); flags 0.
+ * The context works with ltmp2_energy, ltmp2_energy_partial (ranges of the primary Q'),
+ * ltmp2_num_primary_gprime, ltmp2_set_slab_size, ltmp2_set_stream, profiling and
+ * ltmp2_destroy; energies are per unit cell, and pair energies and ltmp2_sizes' n_occ
+ * index the N_k n_occ composite occupied orbitals k n_occ + i.  The route, extrapolation,
+ * pair-mask, batching, autotuning, descriptor and spin-unrestricted calls return
+ * UNSUPPORTED.  Errors: as ltmp2_setup.                                            */
+typedef struct {
+  double lattice[9];
+  int grid[3];
+  int mesh[3];
+  int n_pw;
+  const int *miller;
+  int n_orb;
+  int n_occ;
+  const double *coeff;
+  const double *eps;
+  double ecut_aux;
+  int precision;
+  int flags;
+} ltmp2_kpoint_system;
+int ltmp2_setup_kpoints(const ltmp2_kpoint_system *sys, ltmp2_ctx **out);
+
 /* Free all device memory of ctx.  NULL is ignored.                              */
 void ltmp2_destroy(ltmp2_ctx *ctx);
 

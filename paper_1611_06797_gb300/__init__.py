@@ -11,6 +11,7 @@ from .ltmp2 import (Context, Ltmp2Error, LIB_PATH, load_library, ltmp2_setup, lt
                     ltmp2_set_route, ROUTE_GREEN, ROUTE_OVERLAP, ltmp2_energy_uhf, ltmp2_selftest_wait,
                     ltmp2_autotune, ltmp2_get_tuning, ltmp2_set_tuning, ltmp2_batch_create,
                     ltmp2_set_pair_mask, ltmp2_pair_descriptors, Mlp, NUM_DESC, ltmp2_energy_batch, Batch, ltmp2_strerror, setup_from_solid,
+                    ltmp2_setup_kpoints, setup_from_kpoint_solid,
                     STAGE_NAMES, FP64, FP32, FLAG_REAL_ORBITALS, FLAG_SIMT_GEMM, HARTREE_TO_MEV)
 
 __all__ = ["Context", "Ltmp2Error", "LIB_PATH", "load_library", "ltmp2_setup", "ltmp2_set_stream",
@@ -21,4 +22,5 @@ __all__ = ["Context", "Ltmp2Error", "LIB_PATH", "load_library", "ltmp2_setup", "
            "ltmp2_set_route", "ROUTE_GREEN", "ROUTE_OVERLAP", "ltmp2_energy_uhf", "ltmp2_selftest_wait",
            "ltmp2_autotune", "ltmp2_get_tuning", "ltmp2_set_tuning", "ltmp2_batch_create",
            "ltmp2_set_pair_mask", "ltmp2_pair_descriptors", "Mlp", "NUM_DESC", "ltmp2_energy_batch", "Batch", "ltmp2_strerror", "setup_from_solid",
+           "ltmp2_setup_kpoints", "setup_from_kpoint_solid",
            "STAGE_NAMES", "FP64", "FP32", "FLAG_REAL_ORBITALS", "FLAG_SIMT_GEMM", "HARTREE_TO_MEV"]

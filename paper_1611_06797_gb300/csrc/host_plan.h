@@ -29,6 +29,20 @@ struct HostPlan {
   uint64_t fingerprint = 0;             // hash of every input that determines the energies
 };
 
+// k-point extras (ltmp2_kpoint_system): mesh, primary supercell transfers, class tables
+struct KPointHost {
+  std::vector<int> prim_m;       // [n_prim][3] supercell Miller index of each primary Q'
+  std::vector<double> vprim;     // [n_prim] 4 pi / |Q'|^2
+  std::vector<double> vcls64;    // [n_cls][n_aux] 4 pi / |g + delta/n|^2 inside the sphere, else 0
+  std::vector<float> vcls32;
+  std::vector<int> lut;          // [n^3] position in A of each grid point, -1 if absent
+};
+
+// Validate a k-point system and build the tables: the shared plane-wave columns, the
+// auxiliary ball that holds every momentum-transfer class, the class tables, the lookup
+// table and the primary supercell transfers.  hp.p carries n_occ = N_k n_occ.
+int build_kpoint_host_plan(const ltmp2_kpoint_system *sys, HostPlan &hp, KPointHost &kh) noexcept;
+
 // Validate *sys (flags outside allowed_flags are INVALID_ARG) and build the tables.
 // Checks: pointers and sizes, finite lattice / energies / coefficients, non-decreasing
 // energies, the HOMO-LUMO gap, a cubic supported grid, an inversion-symmetric plane-wave

@@ -14,6 +14,9 @@
 namespace ltmp2 {
 
 template <typename T> __device__ __forceinline__ const T *vtab(const Plan &p);
+template <typename T> __device__ __forceinline__ const T *vtab_k(const Plan &p);
+template <> __device__ __forceinline__ const double *vtab_k<double>(const Plan &p) { return p.vcls64; }
+template <> __device__ __forceinline__ const float *vtab_k<float>(const Plan &p) { return p.vcls32; }
 template <> __device__ __forceinline__ const double *vtab<double>(const Plan &p) { return p.v_aux64; }
 template <> __device__ __forceinline__ const float *vtab<float>(const Plan &p) { return p.v_aux32; }
 
@@ -938,6 +941,226 @@ template <typename T> __global__ void k_pair_overlap(Plan p, double *__restrict_
     S[(size_t)i * p.n_occ + j] = red[0] / (double)n3;
     S[(size_t)j * p.n_occ + i] = red[0] / (double)n3;
   }
+}
+
+// ---------------------------------------------------------------- k-point sampling
+// Sec. II C-D.  Occupied orbitals are composite indices I = k_I n_o + i over the mesh; every
+// u_I on the grid is the cell-periodic part of phi_{i k}.  The outer loop runs over the
+// supercell momentum transfers Q' = g' + kappa'/n (supercell Miller index M = n g' + kappa',
+// kappa' in [0, n)), each primary Q' with its partner -Q' as slots s and s + np.  The
+// transformed state of column (kt, s, j) is w = P_v^{kt} e^{-iQ'r} |j kj>: it has crystal
+// momentum kt = kj - kappa'_s (mod n), and its periodic part has the coefficients of u_j
+// shifted by g'_s + t, t = [kappa_j < kappa'_s] per axis.  A co-density of item (I, column)
+// at FFT index g carries the transfer Q = g + (kt - k_I)/n; its Coulomb kernel comes from
+// the table of that class, v_cls[(kt - kappa_I) + n - 1][g] = 4 pi/|Q|^2 inside the
+// auxiliary sphere and 0 outside.
+
+__device__ __forceinline__ int kp_mod(int a, int n) { const int r = a % n; return r < 0 ? r + n : r; }
+__device__ __forceinline__ int kp_index(const Plan &p, int k0, int k1, int k2) {
+  return (k0 * p.mesh[1] + k1) * p.mesh[2] + k2;
+}
+__device__ __forceinline__ void kp_kappa(const Plan &p, int k, int *kap) {
+  kap[2] = k % p.mesh[2];
+  kap[1] = (k / p.mesh[2]) % p.mesh[1];
+  kap[0] = k / (p.mesh[1] * p.mesh[2]);
+}
+// supercell Miller index of slot s of the slab (primary Q' first, then their negatives)
+__device__ __forceinline__ void kp_slot(const Plan &p, int gp0, int np, int s, int *M) {
+  const int *m = p.prim_m + 3 * (size_t)(gp0 + (s < np ? s : s - np));
+  const int sg = s < np ? 1 : -1;
+  M[0] = sg * m[0]; M[1] = sg * m[1]; M[2] = sg * m[2];
+}
+// class index of an integer shift delta (each component in (-n, n))
+__device__ __forceinline__ int kp_class(const Plan &p, const int *d) {
+  return ((d[0] + p.mesh[0] - 1) * (2 * p.mesh[1] - 1) + (d[1] + p.mesh[1] - 1)) * (2 * p.mesh[2] - 1) +
+         (d[2] + p.mesh[2] - 1);
+}
+// position in the auxiliary set of the integer vector g, or -1
+__device__ __forceinline__ int kp_lut(const Plan &p, int g0, int g1, int g2) {
+  const int n = p.n;
+  if (2 * abs(g0) >= n || 2 * abs(g1) >= n || 2 * abs(g2) >= n) return -1;
+  return p.lut[((size_t)wrapn(g2, n) * n + wrapn(g1, n)) * n + wrapn(g0, n)];
+}
+
+// scale factors per k: virtual a of k at [k][n_orb] offset n_o + a, occupied j at [k][j]
+template <typename T>
+__global__ void k_dscale_k(Plan p, const double *__restrict__ eps, double mu, double tau, T *__restrict__ d) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (a >= p.n_orb) return;
+  const double x = (eps[(size_t)k * p.n_orb + a] - mu) * tau;
+  d[(size_t)k * p.n_orb + a] = (T)exp(a < p.no_k ? x : -x);
+}
+
+// S^T row of column c = (kt nslots + s) n_o + j: the scaled, shifted coefficients of u_{j kj}
+template <typename T>
+__global__ void k_gather_k(Plan p, int gp0, int np, cpx<T> *__restrict__ st) {
+  const int c = blockIdx.y;
+  const int no = p.no_k, nslots = 2 * np;
+  const int j = c % no, s = (c / no) % nslots, kt = c / (no * nslots);
+  int M[3], kt3[3], kj3[3], sh[3];
+  kp_slot(p, gp0, np, s, M);
+  kp_kappa(p, kt, kt3);
+  for (int a = 0; a < 3; ++a) {
+    const int ks = kp_mod(M[a], p.mesh[a]);
+    kj3[a] = kp_mod(kt3[a] + ks, p.mesh[a]);
+    sh[a] = (M[a] - ks) / p.mesh[a] + (kj3[a] < ks ? 1 : 0);
+  }
+  const int kj = kp_index(p, kj3[0], kj3[1], kj3[2]);
+  const T dj = ((const T *)p.dscale)[(size_t)kj * p.n_orb + j];
+  const int n = p.n;
+  const cpx<T> *cg = (const cpx<T> *)p.cgrid + (size_t)(kj * no + j) * n * n * n;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < p.n_pw; q += gridDim.x * blockDim.x) {
+    const int wx = wrapn(p.pw_m[3 * q] + sh[0], n), wy = wrapn(p.pw_m[3 * q + 1] + sh[1], n),
+              wz = wrapn(p.pw_m[3 * q + 2] + sh[2], n);
+    st[(size_t)c * p.n_pw + q] = cscale(cg[((size_t)wz * n + wy) * n + wx], dj);
+  }
+}
+
+// Exchange per (primary slot, I, J): item A = (I, w_J^{Q'}), item B = (J, w_I^{-Q'});
+// X_IJ = sum_Q v(Q) M_A(Q) M_B(-Q), the partner of A's index g_A at B's index -g_A + Delta.
+// Diagonal blocks also store M_II at its canonical index g + [kappa_I < kappa_slot], where
+// every item of a slot has Q = g_c - kappa_slot / n (the direct term pairs g_c with -g_c + e).
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_zcol_k(Plan p, int gp0, int np, const cpx<T> *__restrict__ tbuf,
+                                                cpx<T> *__restrict__ mdiag, double2 *__restrict__ sx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T> *MA = reinterpret_cast<cpx<T> *>(smem_raw);
+  const int NO = p.n_occ, no = p.no_k, nslots = 2 * np;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int gpl = blockIdx.x / (NO * NO);
+  const int r = blockIdx.x % (NO * NO);
+  const int I = r / NO, J = r % NO;
+  const int i = I % no, j = J % no, ki = I / no, kj = J / no;
+  int M[3], kI[3], kJ[3], kA[3], kB[3], ktA[3], ktB[3], dA[3], del[3], cA[3], cB[3];
+  kp_slot(p, gp0, np, gpl, M);
+  kp_kappa(p, ki, kI);
+  kp_kappa(p, kj, kJ);
+  for (int a = 0; a < 3; ++a) {
+    const int n = p.mesh[a];
+    kA[a] = kp_mod(M[a], n);
+    kB[a] = kp_mod(-M[a], n);
+    ktA[a] = kp_mod(kJ[a] - kA[a], n);
+    ktB[a] = kp_mod(kI[a] - kB[a], n);
+    dA[a] = ktA[a] - kI[a];
+    del[a] = (kA[a] != 0 ? 1 : 0) - (kJ[a] < kA[a] ? 1 : 0) - (kI[a] < kB[a] ? 1 : 0);
+    cA[a] = kI[a] < kA[a] ? 1 : 0;
+    cB[a] = kI[a] < kB[a] ? 1 : 0;
+  }
+  const size_t colA = ((size_t)kp_index(p, ktA[0], ktA[1], ktA[2]) * nslots + gpl) * no + j;
+  const size_t colB = ((size_t)kp_index(p, ktB[0], ktB[1], ktB[2]) * nslots + gpl + np) * no + i;
+  const size_t itemA = colA * NO + I, itemB = colB * NO + J;
+  const bool diag = (I == J);
+  const T *vA = vtab_k<T>(p) + (size_t)kp_class(p, dA) * p.n_aux;
+  const int nd = p.n_daux;
+  for (int d = tid; d < nd; d += nth) {
+    const int4 c = p.daux[d];
+    const int off = p.daux_off[d];
+    const cpx<T> *src = tbuf + itemA * N * nd + d;
+    cpx<T> a[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) a[k] = src[(size_t)k * nd];
+    LineFFT<T, N, -1>::run(a);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int m = freq_of<N>(k);
+      if (m >= c.z && m <= c.w) {
+        const int g = off + m - c.z;
+        MA[g] = a[k];
+        if (diag) {
+          const int q = kp_lut(p, c.x + cA[0], c.y + cA[1], m + cA[2]);
+          if (q >= 0) mdiag[((size_t)gpl * p.n_aux + q) * NO + I] = a[k];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  T accx = T(0), accy = T(0);
+  for (int d = tid; d < nd; d += nth) {
+    const int4 c = p.daux[d];
+    const int off = p.daux_off[d];
+    const cpx<T> *src = tbuf + itemB * N * nd + d;
+    cpx<T> a[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) a[k] = src[(size_t)k * nd];
+    LineFFT<T, N, -1>::run(a);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int m = freq_of<N>(k);
+      if (m >= c.z && m <= c.w) {
+        if (diag) {
+          const int q = kp_lut(p, c.x + cB[0], c.y + cB[1], m + cB[2]);
+          if (q >= 0) mdiag[((size_t)(gpl + np) * p.n_aux + q) * NO + I] = a[k];
+        }
+        const int qa = kp_lut(p, -c.x + del[0], -c.y + del[1], -m + del[2]);
+        if (qa >= 0) {
+          const T v = vA[qa];
+          const cpx<T> prod = cmul(MA[qa], a[k]);
+          accx += v * prod.x;
+          accy += v * prod.y;
+        }
+      }
+    }
+  }
+  block_reduce_store<T>((double)accx, (double)accy, sx + ((size_t)gpl * NO + I) * NO + J, nullptr);
+}
+
+// Direct term per (primary slot, I): Y_IJ = sum_{g_c} v(g_c - kappa'/n) M_II(g_c; Q') M_JJ(-g_c + e; -Q'),
+// e = [kappa' != 0] per axis, from the canonically stored diagonal co-densities
+template <typename T>
+__global__ void k_direct_k(Plan p, int np, int gp0, const cpx<T> *__restrict__ mdiag, double2 *__restrict__ yd) {
+  const int gpl = blockIdx.x, I = blockIdx.y;
+  const int NO = p.n_occ;
+  int M[3], e[3], dd[3];
+  kp_slot(p, gp0, np, gpl, M);
+  for (int a = 0; a < 3; ++a) {
+    const int ks = kp_mod(M[a], p.mesh[a]);
+    e[a] = ks != 0 ? 1 : 0;
+    dd[a] = -ks;
+  }
+  const T *v = vtab_k<T>(p) + (size_t)kp_class(p, dd) * p.n_aux;
+  const cpx<T> *MA = mdiag + (size_t)gpl * p.n_aux * NO;
+  const cpx<T> *MB = mdiag + (size_t)(gpl + np) * p.n_aux * NO;
+  for (int J = threadIdx.x; J < NO; J += blockDim.x) {
+    double ax = 0, ay = 0;
+    T cx = T(0), cy = T(0);
+    int cnt = 0;
+    for (int g = 0; g < p.n_aux; ++g) {
+      const T vg = v[g];
+      if (vg == T(0)) continue;
+      const int qb = kp_lut(p, e[0] - p.aux_m[3 * g], e[1] - p.aux_m[3 * g + 1], e[2] - p.aux_m[3 * g + 2]);
+      if (qb < 0) continue;
+      const cpx<T> prod = cmul(MA[(size_t)g * NO + I], MB[(size_t)qb * NO + J]);
+      cx += vg * prod.x;
+      cy += vg * prod.y;
+      if ((++cnt & 31) == 0) { ax += (double)cx; ay += (double)cy; cx = cy = T(0); }
+    }
+    ax += (double)cx; ay += (double)cy;
+    yd[((size_t)gpl * NO + I) * NO + J] = make_double2(ax, ay);
+  }
+}
+
+// e^x_IJ += coef v(Q') (X_IJ + X_JI),  e^d_IJ += -2 coef v(Q') (Y_IJ + Y_JI)
+static __global__ void k_accum_k(Plan p, int gp0, int np, double coef, const double2 *__restrict__ sx,
+                                 const double2 *__restrict__ yd) {
+  const int no = p.n_occ;
+  const int ij = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ij >= no * no) return;
+  const int i = ij / no, j = ij % no;
+  double ex = 0, exi = 0, ed = 0, edi = 0;
+  for (int gpl = 0; gpl < np; ++gpl) {
+    const double vv = coef * p.vprim[gp0 + gpl];
+    const double2 a = sx[((size_t)gpl * no + i) * no + j], b = sx[((size_t)gpl * no + j) * no + i];
+    const double2 c = yd[((size_t)gpl * no + i) * no + j], d = yd[((size_t)gpl * no + j) * no + i];
+    ex += vv * (a.x + b.x);
+    exi += vv * (a.y + b.y);
+    ed += -2.0 * vv * (c.x + d.x);
+    edi += -2.0 * vv * (c.y + d.y);
+  }
+  p.ex[ij] += ex;
+  p.exi[ij] += exi;
+  p.ed[ij] += ed;
+  p.edi[ij] += edi;
 }
 
 // ---------------------------------------------------------------- accumulation (FP64)

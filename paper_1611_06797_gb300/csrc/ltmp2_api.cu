@@ -107,6 +107,7 @@ struct ltmp2_ctx {
   int *d_selftest_err = nullptr;   // error word of the failure-path self-test
   unsigned long long fingerprint = 0;  // hash of the set-up inputs (ltmp2_fingerprint)
   unsigned long long mask_hash = 0;    // hash of the pair mask, 0 = every pair kept
+  void *k_cocc = nullptr;              // k-point context: occupied coefficients (owned via allocs)
   ~ltmp2_ctx() {
     tc_release(tc);
     for (void *q : allocs) cudaFree(q);
@@ -255,6 +256,67 @@ template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys,
   return cuda_status(e);
 }
 
+// k-point context: per-k virtual coefficients, composite occupied orbitals, per-k Green's
+// functions, slab buffers (two slots per primary Q', N_k n_occ columns per slot)
+template <typename T>
+int setup_precision_k(ltmp2_ctx *c, const ltmp2_kpoint_system *sys, const std::vector<int> &order) {
+  Plan &p = c->p;
+  cudaError_t e = Path<T>::init_device();
+  if (e != cudaSuccess) return cuda_status(e);
+  const size_t cs = sizeof(CT<T>);
+  const size_t n3 = (size_t)p.n * p.n * p.n;
+  const int nk = p.nk, no = p.no_k, npw = p.n_pw, norb = p.n_orb;
+  int rc;
+  {
+    std::vector<CT<T>> hv((size_t)nk * p.n_v * npw), ho((size_t)nk * no * npw);
+    for (int k = 0; k < nk; ++k)
+      for (int r = 0; r < norb; ++r)
+        for (int q = 0; q < npw; ++q) {
+          const double *src = sys->coeff + (((size_t)k * norb + r) * npw + order[q]) * 2;
+          const CT<T> v = {(T)src[0], (T)src[1]};
+          if (r < no) ho[((size_t)k * no + r) * npw + q] = v;
+          else hv[((size_t)k * p.n_v + r - no) * npw + q] = v;
+        }
+    if ((rc = dalloc_bytes(c, &p.cv, hv.size() * cs))) return rc;
+    if ((rc = cuda_status(cudaMemcpy(p.cv, hv.data(), hv.size() * cs, cudaMemcpyHostToDevice)))) return rc;
+    void *cocc = nullptr;
+    if ((rc = dalloc_bytes(c, &cocc, ho.size() * cs))) return rc;
+    if ((rc = cuda_status(cudaMemcpy(cocc, ho.data(), ho.size() * cs, cudaMemcpyHostToDevice)))) return rc;
+    c->k_cocc = cocc;
+  }
+  if ((rc = dalloc_bytes(c, &p.cgrid, cs * n3 * p.n_occ))) return rc;
+  if ((rc = dalloc_bytes(c, &p.u, cs * n3 * p.n_occ))) return rc;
+  if ((rc = dalloc_bytes(c, &p.ut, cs * n3 * p.n_occ))) return rc;
+  if ((rc = dalloc_bytes(c, &p.dscale, sizeof(T) * (size_t)nk * norb))) return rc;
+  if ((rc = dalloc_bytes(c, &p.pt, cs * (size_t)nk * npw * npw))) return rc;
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const size_t cols_pp = 2 * (size_t)p.n_occ;
+  const size_t per_prim = cs * cols_pp * (2 * (size_t)npw + (size_t)p.n * p.n_dorb + (size_t)p.n_occ * p.n * p.n_daux) +
+                          cs * 2 * (size_t)p.n_aux * p.n_occ + 2 * sizeof(double2) * (size_t)p.n_occ * p.n_occ;
+  const size_t budget = std::min<size_t>(free_b / 3, (size_t)16 << 30);
+  long long mp = (long long)(budget / std::max<size_t>(per_prim, 1));
+  mp = std::min<long long>(mp, std::max<long long>(1, 4096 / (long long)cols_pp));
+  mp = std::min<long long>(mp, p.n_prim);
+  if (mp < 1) mp = 1;
+  p.max_prim = (int)mp;
+  c->slab_capacity = p.max_prim;
+  const size_t max_cols = cols_pp * p.max_prim;
+  if ((rc = dalloc_bytes(c, &p.st, cs * max_cols * npw))) return rc;
+  if ((rc = dalloc_bytes(c, &p.wt, cs * max_cols * npw))) return rc;
+  if ((rc = dalloc_bytes(c, &p.z1, cs * std::max(max_cols, (size_t)p.n_occ) * p.n * p.n_dorb))) return rc;
+  if ((rc = dalloc_bytes(c, &p.tbuf, cs * max_cols * p.n_occ * p.n * p.n_daux))) return rc;
+  // positions of the diagonal co-densities outside a slot's sphere are never written: zero them once
+  const size_t mbytes = cs * 2 * (size_t)p.max_prim * p.n_aux * p.n_occ;
+  if ((rc = dalloc_bytes(c, &p.mdiag, mbytes))) return rc;
+  if ((rc = cuda_status(cudaMemset(p.mdiag, 0, mbytes)))) return rc;
+  if ((rc = dalloc(c, &p.sx, (size_t)p.max_prim * p.n_occ * p.n_occ))) return rc;
+  if ((rc = dalloc(c, &p.yd, (size_t)p.max_prim * p.n_occ * p.n_occ))) return rc;
+  e = Path<T>::setup_occupied(p, c->k_cocc, c->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  return cuda_status(cudaStreamSynchronize(c->stream));
+}
+
 // Launch (without waiting) everything one energy evaluation does on `stream`.  Usable
 // inside stream capture: no allocation, copy or synchronisation happens here.
 template <typename T>
@@ -265,16 +327,19 @@ int enqueue_energy(ltmp2_ctx *c, cudaStream_t stream, int n_tau, const double *t
   if (e != cudaSuccess) return cuda_status(e);
   *launches += Path<T>::frame_launches(p);  // zero + final reduction(s)
   const double nfft = (double)p.n * p.n * p.n;
+  // k-point sampling: Omega = N_k Omega_0 (the Born-von Karman supercell), the unit-cell
+  // transforms are 1/N_k of the supercell's, and the energy is per unit cell (one more 1/N_k)
+  const double nk = p.nk > 0 ? (double)p.nk : 1.0;
   for (int k = 0; k < n_tau; ++k) {
-    e = Path<T>::green(p, tau[k], stream, tm);
+    e = p.nk > 0 ? Path<T>::green_k(p, tau[k], stream, tm) : Path<T>::green(p, tau[k], stream, tm);
     if (e != cudaSuccess) return cuda_status(e);
-    *launches += Path<T>::green_launches(p);
-    const double coef = w[k] / (p.omega * p.omega * nfft * nfft);
+    *launches += p.nk > 0 ? Path<T>::green_k_launches(p) : Path<T>::green_launches(p);
+    const double coef = w[k] / (nk * nk * nk * p.omega * p.omega * nfft * nfft);
     for (int g0 = gp_begin; g0 < gp_end; g0 += p.max_prim) {
       const int np = std::min(p.max_prim, gp_end - g0);
-      e = Path<T>::slab(p, g0, np, coef, stream, tm);
+      e = p.nk > 0 ? Path<T>::slab_k(p, g0, np, coef, stream, tm) : Path<T>::slab(p, g0, np, coef, stream, tm);
       if (e != cudaSuccess) return cuda_status(e);
-      *launches += Path<T>::slab_launches(p);
+      *launches += p.nk > 0 ? Path<T>::slab_k_launches(p) : Path<T>::slab_launches(p);
     }
   }
   e = Path<T>::finish(p, stream, tm);
@@ -602,6 +667,76 @@ int ltmp2_setup(const ltmp2_system *sys, ltmp2_ctx **out) {
   }
 }
 
+int ltmp2_setup_kpoints(const ltmp2_kpoint_system *sys, ltmp2_ctx **out) {
+  if (!sys || !out) return LTMP2_ERR_INVALID_ARG;
+  *out = nullptr;
+  try {
+    HostPlan hp;
+    KPointHost kh;
+    int rc = build_kpoint_host_plan(sys, hp, kh);
+    if (rc) return rc;
+    std::unique_ptr<ltmp2_ctx> owner(new (std::nothrow) ltmp2_ctx());
+    ltmp2_ctx *c = owner.get();
+    if (!c) return LTMP2_ERR_OOM;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+      cudaGetLastError();
+      return LTMP2_ERR_CUDA;
+    }
+    Plan &p = c->p;
+    p = hp.p;
+    std::memcpy(c->lattice, sys->lattice, sizeof(c->lattice));
+    c->ecut_aux = hp.ecut_aux;
+    c->fingerprint = hp.fingerprint;
+    auto up = [&](auto **dptr, const auto &vec) -> int {
+      using X = typename std::remove_reference<decltype(vec)>::type::value_type;
+      int r = dalloc(c, dptr, vec.size());
+      if (r) return r;
+      return cuda_status(cudaMemcpy(*dptr, vec.data(), vec.size() * sizeof(X), cudaMemcpyHostToDevice));
+    };
+    std::vector<double> heps(sys->eps, sys->eps + (size_t)p.nk * p.n_orb);
+    int *d_prim = nullptr, *d_lut = nullptr;
+    double *d_vprim = nullptr, *d_vc64 = nullptr, *d_eps = nullptr;
+    float *d_vc32 = nullptr;
+    if (!rc) rc = up(&p.dorb, hp.dorb);
+    if (!rc) rc = up(&p.dorb_off, hp.dorb_off);
+    if (!rc) rc = up(&p.daux, hp.daux);
+    if (!rc) rc = up(&p.daux_off, hp.daux_off);
+    if (!rc) rc = up(&p.pw_m, hp.pw_m);
+    if (!rc) rc = up(&p.aux_m, hp.aux_m);
+    if (!rc) rc = up(&d_prim, kh.prim_m);
+    if (!rc) rc = up(&d_vprim, kh.vprim);
+    if (!rc) rc = up(&d_vc64, kh.vcls64);
+    if (!rc) rc = up(&d_vc32, kh.vcls32);
+    if (!rc) rc = up(&d_lut, kh.lut);
+    if (!rc) rc = up(&d_eps, heps);
+    p.prim_m = d_prim;
+    p.vprim = d_vprim;
+    p.vcls64 = d_vc64;
+    p.vcls32 = d_vc32;
+    p.lut = d_lut;
+    p.eps = d_eps;
+    const size_t no2 = (size_t)p.n_occ * p.n_occ;
+    if (!rc) rc = dalloc(c, &p.ex, no2);
+    if (!rc) rc = dalloc(c, &p.ed, no2);
+    if (!rc) rc = dalloc(c, &p.exi, no2);
+    if (!rc) rc = dalloc(c, &p.edi, no2);
+    if (!rc) rc = dalloc(c, &p.esum, 4);
+    if (!rc)
+      rc = (sys->precision == LTMP2_FP64) ? setup_precision_k<double>(c, sys, hp.order)
+                                          : setup_precision_k<float>(c, sys, hp.order);
+    if (rc) {
+      cudaGetLastError();
+      return rc;
+    }
+    *out = owner.release();
+    return LTMP2_OK;
+  } catch (const std::bad_alloc &) {
+    return LTMP2_ERR_OOM;
+  } catch (...) {
+    return LTMP2_ERR_INVALID_ARG;
+  }
+}
+
 int ltmp2_set_stream(ltmp2_ctx *ctx, void *stream) {
   if (!ctx) return LTMP2_ERR_INVALID_ARG;
   ctx->stream = static_cast<cudaStream_t>(stream);
@@ -730,6 +865,7 @@ void ltmp2_destroy(ltmp2_ctx *ctx) {
 }
 
 int ltmp2_autotune(ltmp2_ctx *ctx, int *slab, int *gemm_variant) {
+  if (ctx && ctx->p.nk > 0) return LTMP2_ERR_UNSUPPORTED;   // no k-point form
   if (!ctx) return LTMP2_ERR_INVALID_ARG;
   DeviceGuard g(ctx->device);
   int sl = 0, var = -1;
@@ -741,6 +877,7 @@ int ltmp2_autotune(ltmp2_ctx *ctx, int *slab, int *gemm_variant) {
 }
 
 int ltmp2_set_pair_mask(ltmp2_ctx *ctx, const unsigned char *keep) {
+  if (ctx && ctx->p.nk > 0) return LTMP2_ERR_UNSUPPORTED;   // no k-point form
   if (!ctx) return LTMP2_ERR_INVALID_ARG;
   Plan &p = ctx->p;
   if (!keep) {
@@ -785,6 +922,7 @@ int ltmp2_set_pair_mask(ltmp2_ctx *ctx, const unsigned char *keep) {
 }
 
 int ltmp2_pair_descriptors(ltmp2_ctx *ctx, double *desc) {
+  if (ctx && ctx->p.nk > 0) return LTMP2_ERR_UNSUPPORTED;   // no k-point form
   if (!ctx || !desc) return LTMP2_ERR_INVALID_ARG;
   Plan &p = ctx->p;
   const int no = p.n_occ;
@@ -857,6 +995,7 @@ int ltmp2_get_tuning(const ltmp2_ctx *ctx, int *values) {
 }
 
 int ltmp2_set_tuning(ltmp2_ctx *ctx, const int *values) {
+  if (ctx && ctx->p.nk > 0) return LTMP2_ERR_UNSUPPORTED;   // no k-point form
   if (!ctx || !values) return LTMP2_ERR_INVALID_ARG;
   Plan &p = ctx->p;
   const int slab = values[0] < 0 ? p.max_prim : values[0];
@@ -876,6 +1015,9 @@ int ltmp2_set_tuning(ltmp2_ctx *ctx, const int *values) {
 
 int ltmp2_batch_create(ltmp2_ctx *const *ctxs, int n, const int *n_tau, const double *const *tau,
                        const double *const *w, ltmp2_batch **out) {
+  if (ctxs && n > 0)
+    for (int k = 0; k < n; ++k)
+      if (ctxs[k] && ctxs[k]->p.nk > 0) return LTMP2_ERR_UNSUPPORTED;   // no k-point form
   if (!ctxs || !n_tau || !tau || !w || !out || n < 1) return LTMP2_ERR_INVALID_ARG;
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
@@ -998,6 +1140,7 @@ int ltmp2_selftest_wait(ltmp2_ctx *ctx, int budget_us) {
 // ---------------------------------------------------------------- spin-unrestricted form
 int ltmp2_energy_uhf(ltmp2_ctx *alpha, ltmp2_ctx *beta, int n_tau, const double *tau, const double *w,
                      double *e_direct, double *e_exchange, double *e_spin) {
+  if ((alpha && alpha->p.nk > 0) || (beta && beta->p.nk > 0)) return LTMP2_ERR_UNSUPPORTED;   // no k-point form
   if (!alpha || !beta || alpha == beta || !e_direct || !e_exchange) return LTMP2_ERR_INVALID_ARG;
   int rc = check_tau(n_tau, tau, w);
   if (rc) return rc;
@@ -1047,6 +1190,7 @@ int ltmp2_energy_uhf(ltmp2_ctx *alpha, ltmp2_ctx *beta, int n_tau, const double 
 
 // ---------------------------------------------------------------- transformed-state route
 int ltmp2_set_route(ltmp2_ctx *ctx, int route) {
+  if (ctx && ctx->p.nk > 0) return LTMP2_ERR_UNSUPPORTED;   // no k-point form
   if (!ctx || (route != LTMP2_ROUTE_GREEN && route != LTMP2_ROUTE_OVERLAP)) return LTMP2_ERR_INVALID_ARG;
   Plan &p = ctx->p;
   if (route == LTMP2_ROUTE_GREEN) {
@@ -1070,6 +1214,7 @@ int ltmp2_set_route(ltmp2_ctx *ctx, int route) {
 // ---------------------------------------------------------------- internal cutoff extrapolation
 static_assert(kMaxLevels == LTMP2_MAX_LEVELS, "level capacity");
 int ltmp2_set_extrapolation(ltmp2_ctx *ctx, int n_c, double alpha) {
+  if (ctx && ctx->p.nk > 0) return LTMP2_ERR_UNSUPPORTED;   // no k-point form
   if (!ctx) return LTMP2_ERR_INVALID_ARG;
   Plan &p = ctx->p;
   ctx->lev_done = false;

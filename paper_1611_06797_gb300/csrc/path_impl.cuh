@@ -112,6 +112,8 @@ template <typename T> cudaError_t Path<T>::init_device() {
   e = cudaFuncSetAttribute(k_planes2<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
   if (e != cudaSuccess) return e;                                                                   \
   e = cudaFuncSetAttribute(k_planes3<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
+  if (e != cudaSuccess) return e;                                                                   \
+  e = cudaFuncSetAttribute(k_zcol_k<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
   if (e != cudaSuccess) return e;
   LTMP2_FOR_EACH_N(LTMP2_SET_SMEM)
 #undef LTMP2_SET_SMEM
@@ -308,6 +310,91 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
       k_accum_lev<<<dim3((no * no + 31) / 32, p.n_lev - 1), 32, 0, st>>>(p, gp0, np, coef);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+  }
+  return cudaSuccess;
+}
+
+template <typename T> cudaError_t Path<T>::green_k(const Plan &p, double tau, cudaStream_t st, StageTimer *tm) {
+  ScopedStage s(tm, kStageGreen);
+  k_dscale_k<T><<<dim3((p.n_orb + 255) / 256, p.nk), 256, 0, st>>>(p, p.eps, p.mu, tau, (T *)p.dscale);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t pw2 = (size_t)p.n_pw * p.n_pw;
+  dim3 grid((p.n_pw + 63) / 64, (p.n_pw + 63) / 64);
+  for (int k = 0; k < p.nk; ++k) {
+    // P^T_k[q][p] = sum_a conj(c_{a k}(q)) e^{-(e_{a k}-mu)tau} c_{a k}(p)
+    const cpx<T> *cv = (const cpx<T> *)p.cv + (size_t)k * p.n_v * p.n_pw;
+    k_cgemm<T, false, true><<<grid, 256, 0, st>>>(p.n_pw, p.n_pw, p.n_v, cv, p.n_pw, cv, p.n_pw,
+                                                  (const T *)p.dscale + (size_t)k * p.n_orb + p.no_k,
+                                                  (cpx<T> *)p.pt + k * pw2, p.n_pw);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t Path<T>::slab_k(const Plan &p, int gp0, int np, double coef, cudaStream_t st, StageTimer *tm) {
+  const int n = p.n, NO = p.n_occ;
+  const int nslots = 2 * np;
+  const int ncols = nslots * NO;          // nk blocks of nslots * n_o columns, one block per kt
+  const int rows_k = nslots * p.no_k;
+  cudaError_t e;
+  {
+    ScopedStage s(tm, kStageGatherZ);
+    k_gather_k<T><<<dim3((p.n_pw + 255) / 256, ncols), 256, 0, st>>>(p, gp0, np, (cpx<T> *)p.st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  {
+    ScopedStage s(tm, kStageWGemm);
+    const size_t pw2 = (size_t)p.n_pw * p.n_pw;
+    dim3 grid((p.n_pw + 63) / 64, (rows_k + 63) / 64);
+    for (int kt = 0; kt < p.nk; ++kt) {
+      const size_t row0 = (size_t)kt * rows_k * p.n_pw;
+      k_cgemm<T, true, false><<<grid, 256, 0, st>>>(rows_k, p.n_pw, p.n_pw, (const cpx<T> *)p.st + row0, p.n_pw,
+                                                    (const cpx<T> *)p.pt + kt * pw2, p.n_pw, nullptr,
+                                                    (cpx<T> *)p.wt + row0, p.n_pw);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
+  const size_t smem_col = (size_t)p.n_aux * sizeof(cpx<T>);
+  const int npairs = np * NO * NO;
+  int col_threads = ((p.n_daux + 31) / 32) * 32;
+  if (col_threads > 256) col_threads = 256;
+  switch (n) {
+#define LTMP2_CASE(NN)                                                                                 \
+  case NN: {                                                                                           \
+    {                                                                                                  \
+      ScopedStage s(tm, kStageGatherZ);                                                                \
+      k_w_zinv<T, NN><<<dim3((p.n_dorb + 127) / 128, ncols), 128, 0, st>>>(p, p.n_pw, (const cpx<T> *)p.wt, \
+                                                                          (cpx<T> *)p.z1);              \
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;                                           \
+    }                                                                                                  \
+    {                                                                                                  \
+      ScopedStage s(tm, kStagePlane);                                                                  \
+      if ((e = launch_planes<T>(p, ncols, p.plane_kernel, p.plane_ib, st)) != cudaSuccess) return e;   \
+    }                                                                                                  \
+    {                                                                                                  \
+      ScopedStage s(tm, kStageColumn);                                                                 \
+      k_zcol_k<T, NN><<<npairs, col_threads, smem_col, st>>>(p, gp0, np, (const cpx<T> *)p.tbuf,       \
+                                                             (cpx<T> *)p.mdiag, p.sx);                 \
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;                                           \
+    }                                                                                                  \
+  } break;
+    LTMP2_FOR_EACH_N(LTMP2_CASE)
+#undef LTMP2_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  {
+    ScopedStage s(tm, kStageDirect);
+    const int th = NO < 128 ? ((NO + 31) / 32) * 32 : 128;
+    k_direct_k<T><<<dim3(np, NO), th, 0, st>>>(p, np, gp0, (const cpx<T> *)p.mdiag, p.yd);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  {
+    ScopedStage s(tm, kStageAccum);
+    k_accum_k<<<(NO * NO + 127) / 128, 128, 0, st>>>(p, gp0, np, coef, p.sx, p.yd);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

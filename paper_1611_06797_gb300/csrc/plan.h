@@ -99,7 +99,19 @@ struct Plan {
   // W = sum_a |a> e^{-(e_a-mu)tau} rho_aj(G') e^{(e_j-mu)tau} (real orbitals only).
   int route = 0;
   void *rt = nullptr;        // route 1: [n_prim * n_occ][n_v] cpx<T>, row (G', j), column a
-  int slots_per_prim() const { return real_orb ? 1 : 2; }
+  // k-point sampling (Sec. II C-D), nk > 0: n_occ counts composite occupied orbitals
+  // k n_o + i over the mesh, n_orb / n_v are per k, cv [nk][n_v][n_pw], pt [nk][n_pw][n_pw],
+  // dscale [nk][n_orb]; the auxiliary set A (daux, aux_m) is the ball that holds every
+  // momentum-transfer class; the outer loop runs over primary supercell transfers Q'.
+  int nk = 0;
+  int mesh[3] = {1, 1, 1};
+  int no_k = 0;                        // occupied per k
+  const int *prim_m = nullptr;         // [n_prim][3] supercell Miller index of each primary Q'
+  const double *vprim = nullptr;       // [n_prim] 4 pi / |Q'|^2
+  const double *vcls64 = nullptr;      // [n_cls][n_aux] 4 pi / |g + delta/n|^2 inside the sphere, else 0
+  const float *vcls32 = nullptr;
+  const int *lut = nullptr;            // [n^3] position in A of the grid point, -1 if absent
+  int slots_per_prim() const { return (real_orb && nk == 0) ? 1 : 2; }
 };
 
 // Per-stage profiler hooks (host).  begin/end bracket one kernel launch.
@@ -144,6 +156,12 @@ template <typename T> struct Path {
   static cudaError_t plane_pass(const Plan &p, int ncols, int kernel, int ib, cudaStream_t st);
   // per-orbital density moments [n_occ][6] and pair density overlaps [n_occ][n_occ] (device)
   static cudaError_t descriptors(const Plan &p, double *moments, double *overlap, cudaStream_t st);
+  // k-point sampling: scale factors and the Green's function of every k for one tau, and
+  // one slab of primary supercell transfers Q' [gp0, gp0 + np)
+  static cudaError_t green_k(const Plan &p, double tau, cudaStream_t st, StageTimer *tm);
+  static cudaError_t slab_k(const Plan &p, int gp0, int np, double coef, cudaStream_t st, StageTimer *tm);
+  static int green_k_launches(const Plan &p) { return 1 + p.nk; }
+  static int slab_k_launches(const Plan &p) { return 6 + p.nk; }
   // opposite-spin direct term of one slab (alpha plan pa, beta plan pb, same slab):
   // y [slab][na][nb] scratch, acc [na][nb] accumulated
   static cudaError_t direct_cross(const Plan &pa, const Plan &pb, int gp0, int np, double coef, double *y,

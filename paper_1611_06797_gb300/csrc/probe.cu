@@ -18,13 +18,19 @@ constexpr int kThreads = 256;
 // nothing is folded away and almost nothing reaches memory.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_fma_chains(int iters, T b, T c, T *out) {
-  T x[kChains];
+  T x[kChains], br[kChains];
+  // both FMA operands in registers (x * 0 is not folded for floating point, so cr is a
+  // run-time value): operands from the constant bank would throttle the FP64 pipe
+  const T cr = c + (T)threadIdx.x * (T)0;
 #pragma unroll
-  for (int k = 0; k < kChains; ++k) x[k] = (T)(threadIdx.x + k) * (T)1e-3;
+  for (int k = 0; k < kChains; ++k) {
+    x[k] = (T)(threadIdx.x + k) * (T)1e-3;
+    br[k] = b - (T)k * (T)1e-9;
+  }
 #pragma unroll 4
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int k = 0; k < kChains; ++k) x[k] = fma(x[k], b, c);
+    for (int k = 0; k < kChains; ++k) x[k] = fma(x[k], br[k], cr);
   }
   T s = 0;
 #pragma unroll

@@ -40,6 +40,14 @@ class _System(ctypes.Structure):
                 ("ecut_aux", ctypes.c_double), ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
+class _KSystem(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_double * 9), ("grid", ctypes.c_int * 3), ("mesh", ctypes.c_int * 3),
+                ("n_pw", ctypes.c_int), ("miller", ctypes.POINTER(ctypes.c_int)), ("n_orb", ctypes.c_int),
+                ("n_occ", ctypes.c_int), ("coeff", ctypes.POINTER(ctypes.c_double)),
+                ("eps", ctypes.POINTER(ctypes.c_double)), ("ecut_aux", ctypes.c_double),
+                ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -56,6 +64,7 @@ def load_library():
     vp = ctypes.c_void_p
     sig = {
         "ltmp2_setup": (ctypes.c_int, [P(_System), P(vp)]),
+        "ltmp2_setup_kpoints": (ctypes.c_int, [P(_KSystem), P(vp)]),
         "ltmp2_set_stream": (ctypes.c_int, [vp, vp]),
         "ltmp2_laplace_grid": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, dp]),
         "ltmp2_energy": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, dp, dp, dp]),
@@ -143,6 +152,45 @@ def ltmp2_setup(lattice, grid, miller, coeff, eps, n_occ: int, ecut_aux: float =
     h = ctypes.c_void_p()
     _check(lib.ltmp2_setup(ctypes.byref(s), ctypes.byref(h)), "ltmp2_setup")
     return Context(h.value, int(n_occ))
+
+
+def ltmp2_setup_kpoints(lattice, grid, mesh, miller, coeff, eps, n_occ: int, ecut_aux: float = 0.0,
+                        precision: int = FP64) -> Context:
+    """k-point context (include/ltmp2.h): coeff [N_k][n_orb][n_pw], eps [N_k][n_orb], one plane-wave
+    set for every k; n_occ per k.  The context's pair energies index N_k n_occ composite orbitals."""
+    lib = load_library()
+    lattice = np.ascontiguousarray(np.asarray(lattice, dtype=np.float64).reshape(9))
+    miller = np.ascontiguousarray(np.asarray(miller, dtype=np.int32).reshape(-1, 3))
+    coeff = np.ascontiguousarray(np.asarray(coeff, dtype=np.complex128))
+    eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+    mesh = [int(x) for x in np.asarray(mesh).reshape(3)]
+    nk = mesh[0] * mesh[1] * mesh[2]
+    if coeff.ndim != 3 or coeff.shape[0] != nk or coeff.shape[2] != miller.shape[0] or eps.shape != coeff.shape[:2]:
+        raise ValueError("coeff must be [N_k][n_orb][n_pw] and eps [N_k][n_orb]")
+    s = _KSystem()
+    s.lattice[:] = lattice.tolist()
+    s.grid[:] = [int(g) for g in np.asarray(grid).reshape(3)]
+    s.mesh[:] = mesh
+    s.n_pw = miller.shape[0]
+    s.miller = miller.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    s.n_orb = coeff.shape[1]
+    s.n_occ = int(n_occ)
+    s.coeff = _dp(coeff.view(np.float64))
+    s.eps = _dp(eps)
+    s.ecut_aux = float(ecut_aux)
+    s.precision = int(precision)
+    s.flags = 0
+    h = ctypes.c_void_p()
+    _check(lib.ltmp2_setup_kpoints(ctypes.byref(s), ctypes.byref(h)), "ltmp2_setup_kpoints")
+    return Context(h.value, int(n_occ) * nk)
+
+
+def setup_from_kpoint_solid(ks, precision: int = FP64, ecut_aux: Optional[float] = None) -> Context:
+    """ltmp2_setup_kpoints for a synth.KPointSolid (E_aux = 2/3 E_cut unless given)."""
+    if ecut_aux is None:
+        ecut_aux = 2.0 * ks.ecut / 3.0
+    return ltmp2_setup_kpoints(ks.lattice, ks.grid, ks.mesh, ks.miller, ks.coeff, ks.eps, ks.n_occ, ecut_aux,
+                               precision)
 
 
 def setup_from_solid(solid, precision: int = FP64, real: Optional[bool] = None,

@@ -214,3 +214,29 @@ def test_noalloc_rejects_bad_systems_with_the_setup_codes():
         L.ltmp2_energy_noalloc(sp.lattice, sp.grid, sp.miller, sp.coeff, sp.eps, sp.n_occ, tau, w,
                                flags=L.FLAG_REAL_ORBITALS)
     assert e.value.name == "NOT_REAL"
+
+
+def test_kpoint_setup_validates_on_the_host():
+    """ltmp2_setup_kpoints rejects bad input before any device work, with ltmp2_setup's codes."""
+    from synth import build_kpoint_solid
+    ks = build_kpoint_solid(5.0, 8, 9, (2, 1, 1), np.array([[1.1, 2.3, 2.0]]), 1, seed=4)
+    base = dict(lattice=ks.lattice, grid=ks.grid, mesh=ks.mesh, miller=ks.miller, coeff=ks.coeff, eps=ks.eps,
+                n_occ=ks.n_occ, ecut_aux=2 * ks.ecut / 3)
+
+    def expect(code, **over):
+        kw = dict(base)
+        kw.update(over)
+        with pytest.raises(L.Ltmp2Error) as e:
+            L.ltmp2_setup_kpoints(**kw)
+        assert e.value.name == code, (code, e.value.name)
+    c = ks.coeff.copy(); c[1, 0] *= 1.01
+    expect("NOT_ORTHONORMAL", coeff=c)
+    c = ks.coeff.copy(); c[0, 3, 2] = complex(np.nan, 0)
+    expect("INVALID_ARG", coeff=c)
+    e = ks.eps.copy(); e[1, 1] = ks.eps[:, 0].max()          # LUMO of k = 1 at the HOMO of the mesh
+    expect("GAP", eps=e)
+    expect("GRID", grid=[8, 8, 10])
+    with pytest.raises(ValueError):                           # the binding checks the array shapes
+        L.ltmp2_setup_kpoints(**dict(base, mesh=[0, 1, 1]))
+    expect("INVALID_ARG", n_occ=0)
+    expect("INVALID_ARG", precision=3)
