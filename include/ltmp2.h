@@ -83,9 +83,10 @@ typedef struct ltmp2_ctx ltmp2_ctx; /* opaque; owns all device memory of one sys
  *   grid      [3]  FFT grid n1, n2, n3.  Must be cubic (n1 = n2 = n3) with
  *                  n in {8,10,12,16,18,20,24,25,27,30,32,36,40}.
  *   n_pw           number of plane waves of the orbital basis (|G|^2/2 <= E_cut).
- *   miller    [n_pw][3] int: G_p = m1 b1 + m2 b2 + m3 b3.  The set must be
- *                  inversion symmetric, each |m_k| < n_k/2, and for every (m1, m2)
- *                  its m3 values must form one contiguous range (true for a sphere).
+ *   miller    [n_pw][3] int: G_p = m1 b1 + m2 b2 + m3 b3.  Each |m_k| < n_k/2, and
+ *                  for every (m1, m2) its m3 values must form one contiguous range (true
+ *                  for a sphere); with LTMP2_FLAG_REAL_ORBITALS the set must also be
+ *                  inversion symmetric.
  *   n_orb, n_occ   orbitals (ascending energy); the first n_occ are doubly occupied,
  *                  all others virtual.  1 <= n_occ < n_orb <= n_pw.
  *   coeff     [n_orb][n_pw] complex128 as interleaved (re, im) doubles, row-major,

@@ -136,10 +136,15 @@ int build(const ltmp2_system *sys, int allowed_flags, HostPlan &hp) {
     if (!where.emplace(m[q], q).second) return LTMP2_ERR_INVALID_ARG;
     g2max = std::max(g2max, g2_of(hp.B, m[q][0], m[q][1], m[q][2]));
   }
-  hp.negpw.assign(npw, 0);
+  // -G of every plane wave: needed by the real-orbital (cos/sin basis) path only
+  const bool real_flag = (sys->flags & LTMP2_FLAG_REAL_ORBITALS) != 0;
+  hp.negpw.assign(npw, -1);
   for (int q = 0; q < npw; ++q) {
     auto it = where.find({-m[q][0], -m[q][1], -m[q][2]});
-    if (it == where.end()) return LTMP2_ERR_GRID;
+    if (it == where.end()) {
+      if (real_flag) return LTMP2_ERR_GRID;
+      continue;
+    }
     hp.negpw[q] = it->second;
   }
   std::vector<Col> ocols;

@@ -45,8 +45,8 @@ int build_kpoint_host_plan(const ltmp2_kpoint_system *sys, HostPlan &hp, KPointH
 
 // Validate *sys (flags outside allowed_flags are INVALID_ARG) and build the tables.
 // Checks: pointers and sizes, finite lattice / energies / coefficients, non-decreasing
-// energies, the HOMO-LUMO gap, a cubic supported grid, an inversion-symmetric plane-wave
-// set with contiguous m3 columns that fits the grid, orthonormality of a deterministic
+// energies, the HOMO-LUMO gap, a cubic supported grid, a plane-wave set with contiguous m3
+// columns that fits the grid (inversion symmetric with LTMP2_FLAG_REAL_ORBITALS), orthonormality of a deterministic
 // sample of orbitals, and c(-G) = conj c(G) when LTMP2_FLAG_REAL_ORBITALS is set.
 // Returns LTMP2_OK or the status of the first failed check.  Never throws.
 int build_host_plan(const ltmp2_system *sys, int allowed_flags, HostPlan &hp) noexcept;

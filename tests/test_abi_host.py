@@ -101,7 +101,7 @@ def test_setup_rejects_bad_input_before_the_device():
     _expect("INVALID_ARG", s, miller=m)           # duplicate plane wave
     keep = np.array([not (r[0] == 3 and r[1] == 0 and r[2] == 0) for r in s.miller.tolist()])
     _expect("GRID", s, miller=s.miller[keep], coeff=np.eye(keep.sum(), dtype=complex)[:s.n_orb - 1],
-            eps=np.sort(s.eps[:s.n_orb - 1]))    # not inversion symmetric
+            eps=np.sort(s.eps[:s.n_orb - 1]), flags=L.FLAG_REAL_ORBITALS)    # not inversion symmetric
 
 
 def test_setup_checks_real_orbital_flag():
