@@ -275,7 +275,8 @@ def main():
     ap.add_argument("--route", default="green", choices=["green", "overlap"],
                     help="transformed states from the per-tau Green's function (default) or from stored "
                          "overlap densities (the paper's steps (i)-(iii))")
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "batch", "learned", "cfg3", "uhf", "fftcmp"],
+    ap.add_argument("--workload", default="cfg2",
+                    choices=["cfg2", "batch", "learned", "cfg3", "uhf", "fftcmp", "kpoints"],
                     help="cfg2: the 16-well 24^3 system; batch: 8 uneven systems in one graph launch; "
                          "learned: surrogate-screened pairs; cfg3: precision form on the 64-well 36^3 system")
     args = ap.parse_args()
@@ -287,7 +288,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "ours" and args.workload in ("batch", "learned", "cfg3", "uhf", "fftcmp"):
+    if args.impl == "ours" and args.workload in ("batch", "learned", "cfg3", "uhf", "fftcmp", "kpoints"):
         import torch
         import paper_1611_06797_gb300 as L
         torch.cuda.set_device(local)
@@ -295,6 +296,8 @@ def main():
             out = form_batch(L, torch, local, args.steps, args.warmup)
         elif args.workload == "cfg3":
             out = form_cfg3(L, torch, local, args.steps, args.warmup)
+        elif args.workload == "kpoints":
+            out = form_kpoints(L, torch, local, args.steps, args.warmup)
         elif args.workload == "learned":
             out = run_learned(args, local)
         elif args.workload == "uhf":
@@ -532,7 +535,7 @@ def main():
         # the metric's forms on their own workloads, fixed repeat counts (steps / warm-up
         # below), so that the default run stays within minutes at any --steps
         out.setdefault("forms", {})
-        for key, fn in (("cfg3_precision", form_cfg3), ("cfg4_batch", form_batch)):
+        for key, fn in (("cfg3_precision", form_cfg3), ("cfg4_batch", form_batch), ("kpoints_2x2x2", form_kpoints)):
             try:
                 out["forms"][key] = fn(L, torch, local, 1, 1, alu=alu)
             except Exception as e:  # reported, never fatal
@@ -811,6 +814,83 @@ def form_cfg3(L, torch, local, steps, warmup, alu=None):
         "cpu_baseline": {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                          "sample": "not run: one occupied pair of this system costs the oracle ~5e11 complex "
                                    "multiply-adds (N_v^2 N_G), beyond a bounded sample"},
+    }
+
+
+def form_kpoints(L, torch, local, steps, warmup, alu=None, mesh=(2, 2, 2)):
+    """k-point sampling (Sec. II C-D): the 2-well 6 bohr cell of the 12^3 workload (515 plane
+    waves, 2 occupied bands per k) on a 2 x 2 x 2 mesh, 6 Laplace points, in both precisions;
+    against the Gamma-point path on the same physics, the 12 bohr supercell with 16 wells
+    (4120 plane waves {k + G}, 24^3 grid, 16 occupied), which the k-point path replaces."""
+    from synth import SPECS, build_kpoint_pair
+    from synth.model_solid import well_positions
+    spec = SPECS["cfg1"]
+    dev = torch.device("cuda", local)
+    t0 = time.time()
+    ks, sc = build_kpoint_pair(spec.a, spec.grid, spec.r2, mesh, well_positions(spec), 2, seed=spec.seed,
+                               device="cuda")
+    t_fix = time.time() - t0
+    n_tau = 6
+    tau, w, qerr = L.ltmp2_laplace_grid(ks.gap, ks.width, n_tau)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    NO = ks.n_k * ks.n_occ
+    units = NO * (NO + 1) // 2 * n_tau
+    per_atom = HARTREE_TO_MEV / ks.n_atoms
+    res = {}
+
+    def timed(ctx, reps):
+        L.ltmp2_set_stream(ctx, stream)
+        for _ in range(warmup):
+            L.ltmp2_energy(ctx, tau, w, pairs=False)
+        torch.cuda.synchronize()
+        L.ltmp2_reset_stage_times(ctx)
+        L.ltmp2_set_profiling(ctx, True)
+        n0 = L.ltmp2_kernel_launches(ctx)
+        evs = []
+        with ClockSampler(local) as clk:
+            for _ in range(reps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                r = L.ltmp2_energy(ctx, tau, w, pairs=False)
+                b.record(stream)
+                evs.append((a, b))
+            torch.cuda.synchronize()
+        L.ltmp2_set_profiling(ctx, False)
+        st = L.ltmp2_stage_times(ctx)
+        out = {"ms": sum(x.elapsed_time(y) for x, y in evs) / reps, "E_d": r[0], "E_x": r[1],
+               "launches": (L.ltmp2_kernel_launches(ctx) - n0) // reps, "clocks": clk.summary(),
+               "stages": {k: {"ms_per_step": v["ms"] / reps} for k, v in st.items()}}
+        L.ltmp2_destroy(ctx)
+        return out
+    for prec, key in ((L.FP64, "fp64"), (L.FP32, "fp32")):
+        res[key] = timed(L.setup_from_kpoint_solid(ks, precision=prec), steps)
+    ctx = L.ltmp2_setup(sc.lattice, sc.grid, sc.miller, sc.coeff, sc.eps, sc.n_occ, 2 * ks.ecut / 3, L.FP64, 0)
+    res["gamma_supercell_fp64"] = timed(ctx, 1)
+    k64, k32, g64 = res["fp64"], res["fp32"], res["gamma_supercell_fp64"]
+    return {
+        "metric": METRIC, "value": units / (k64["ms"] / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+        "warmup": warmup, "ms_per_step": k64["ms"], "s_per_E_MP2": k64["ms"] / 1e3, "higher_is_better": True,
+        "dtype": "f64", "data": "synthetic: seeded Gaussian-well model solid on a k-mesh, dense diagonalisation per k",
+        "config": {"workload": f"k-point form: cfg1 cell (a={spec.a} bohr, 2 wells, {spec.grid}^3 grid, "
+                               f"{ks.n_pw} plane waves shared by every k), {mesh[0]}x{mesh[1]}x{mesh[2]} mesh, "
+                               f"2 occupied bands per k ({NO} composite occupied), {n_tau} tau; pair units over "
+                               f"the composite occupied orbitals", "n_k": ks.n_k, "indirect_gap_Ha": ks.gap,
+                   "laplace_max_rel_err": qerr,
+                   "supercell": f"{sc.n_pw} plane waves, {int(sc.grid[0])}^3 grid, {sc.n_occ} occupied, "
+                                f"{ks.n_atoms * ks.n_k} wells"},
+        "energy_per_cell": {"E_d": k64["E_d"], "E_x": k64["E_x"]},
+        "forms": {"fp32": {"s_per_E_MP2": k32["ms"] / 1e3, "speedup_vs_fp64": k64["ms"] / k32["ms"],
+                           "err_vs_fp64_meV_per_atom": {"E_d": abs(k32["E_d"] - k64["E_d"]) * per_atom,
+                                                        "E_x": abs(k32["E_x"] - k64["E_x"]) * per_atom}}},
+        "gamma_supercell": {"s_per_E_MP2": g64["ms"] / 1e3, "kpoint_speedup": g64["ms"] / k64["ms"],
+                            "abs_diff_per_cell_Ha": {"E_d": abs(g64["E_d"] / ks.n_k - k64["E_d"]),
+                                                     "E_x": abs(g64["E_x"] / ks.n_k - k64["E_x"])},
+                            "stages": g64["stages"]},
+        "stages": k64["stages"], "gpu_launches": k64["launches"], "clocks": k64["clocks"],
+        "setup_s": {"fixtures": t_fix},
     }
 
 

@@ -25,7 +25,7 @@ from typing import Optional, Sequence, Tuple
 
 import numpy as np
 
-from .model_solid import ModelSolid, hamiltonian, sphere_miller
+from .model_solid import ModelSolid, _eigh, hamiltonian, sphere_miller
 
 
 @dataclasses.dataclass
@@ -120,12 +120,12 @@ def build_kpoint_solid(a: float, grid: int, r2: int, mesh: Sequence[int], positi
                        0.5 * (r2 + 1e-6) * b * b, np.asarray(positions, float), depth, width)
 
 
-def supercell_of(ks: KPointSolid) -> ModelSolid:
+def supercell_of(ks: KPointSolid, device: Optional[str] = None) -> ModelSolid:
     """The Gamma-point supercell of the mesh: cell vectors n_i a_i, grid n_i g_i, wells in
     every cell, plane waves {k + G_m} with supercell Miller index n_i m_i + kappa_i, orbitals
     and energies from a dense diagonalisation of the supercell Hamiltonian in that set (the
     Hamiltonian is block diagonal in k; the diagonalisation does not use that), the lowest
-    N_k n_occ states occupied."""
+    N_k n_occ states occupied.  ``device="cuda"``: the eigensolver runs on the GPU."""
     mesh = ks.mesh
     lattice = ks.lattice * mesh[:, None]
     shifts = mesh_kappa(mesh)
@@ -135,17 +135,18 @@ def supercell_of(ks: KPointSolid) -> ModelSolid:
     if np.any(2 * np.abs(Msc) >= grid[None, :]):
         raise ValueError("supercell plane waves do not fit the supercell grid")
     H = hamiltonian(Msc, lattice, pos, ks.well_depth, ks.well_width)
-    w, v = np.linalg.eigh(H)
+    w, v = _eigh(H, device)
     coeff = v.T.copy()
     coeff /= np.linalg.norm(coeff, axis=1)[:, None]
     return ModelSolid(None, lattice, grid, Msc, np.ascontiguousarray(coeff), w, ks.n_k * ks.n_occ, ks.ecut, pos)
 
 
 def build_kpoint_pair(a: float, grid: int, r2: int, mesh: Sequence[int], positions: np.ndarray, n_occ: int,
-                      depth: float = 2.0, width: float = 0.8, random_phases: bool = False, seed: int = 0):
+                      depth: float = 2.0, width: float = 0.8, random_phases: bool = False, seed: int = 0,
+                      device: Optional[str] = None):
     """(k-point solid, its Gamma-point supercell) from the same potential."""
     ks = build_kpoint_solid(a, grid, r2, mesh, positions, n_occ, depth, width, random_phases, seed)
-    return ks, supercell_of(ks)
+    return ks, supercell_of(ks, device)
 
 
 def free_electron_kpoints(a: float, grid: int, r2: int, mesh: Sequence[int]) -> KPointSolid:
