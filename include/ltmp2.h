@@ -180,8 +180,9 @@ int ltmp2_autotune(ltmp2_ctx *ctx, int *slab, int *gemm_variant);
 
 /* Settings in effect for ctx: values[0] slab size, [1] tensor-core GEMM layout (-1 in
  * FP64 or with LTMP2_FLAG_SIMT_GEMM), [2] plane FFT kernel (0 full-plane passes,
- * 1 compacted passes, 2 product in registers with a compact intermediate), [3] occupied
- * planes per plane-kernel block (0 = default).  The autotuner also chooses [2] and [3],
+ * 1 compacted passes, 2 product in registers with a compact intermediate, 3 the same with
+ * every warp on its own occupied planes and no block barriers), [3] occupied planes per
+ * plane-kernel block, for kernel 3 per warp step (0 = default).  The autotuner also chooses [2] and [3],
  * timing the plane kernel alone.                                                      */
 int ltmp2_get_tuning(const ltmp2_ctx *ctx, int *values);
 

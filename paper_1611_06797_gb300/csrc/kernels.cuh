@@ -598,6 +598,75 @@ __global__ void k_planes3(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> 
   }
 }
 
+// Same result as k_planes3 with no block barrier after the w plane is transformed: each of
+// the block's kPlaneWarps warps takes its own occupied i (ib at a time, in its own slice of
+// shared memory) through the x pass, the y pass and the disk gather, synchronising only
+// within the warp.  Warps run out of step, so one warp's FFT arithmetic hides another's
+// shared-memory and L2 latency; ib items per step keep the lanes busy for N < 32.
+constexpr int kPlaneWarps = 4;
+template <typename T, int N>
+__global__ void __launch_bounds__(32 * kPlaneWarps) k_planes4(Plan p, int ib, const cpx<T> *__restrict__ z1,
+                                                              cpx<T> *__restrict__ tbuf) {
+  constexpr int P = N + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T> *xp = reinterpret_cast<cpx<T> *>(smem_raw);
+  const int nxa = p.mxhi_aux - p.mxlo_aux + 1;
+  const int nd = p.n_daux;
+  cpx<T> *wk_all = xp + N * P;                                          // [warps][ib][N][nxa]
+  int *ytab = reinterpret_cast<int *>(wk_all + (size_t)kPlaneWarps * ib * N * nxa);   // [nd]
+  const int z = blockIdx.x, col = blockIdx.y;
+  const int no = p.n_occ;
+  const int mlo = p.mxlo_aux, mhi = p.mxhi_aux;
+  for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+    const int4 c = p.daux[d];
+    ytab[d] = wrapn(c.y, N) * nxa + (c.x - mlo);
+  }
+  plane_inverse<T, N>(p, z1 + ((size_t)col * N + z) * p.n_dorb, xp);   // ends with a barrier
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  cpx<T> *wk = wk_all + (size_t)warp * ib * N * nxa;
+  const cpx<T> *ut = (const cpx<T> *)p.ut;
+  const int jcol = col % no;
+  const int ni = p.keep_count ? p.keep_count[jcol] : no;
+  const int *ilist = p.keep_count ? p.keep_list + (size_t)jcol * no : nullptr;
+  for (int i0 = warp * ib; i0 < ni; i0 += kPlaneWarps * ib) {
+    const int nb = min(ib, ni - i0);
+    for (int t = lane; t < nb * N; t += 32) {
+      const int il = t / N, y = t - il * N;
+      const int iocc = ilist ? ilist[i0 + il] : i0 + il;
+      cpx<T> a[N];
+      const cpx<T> *ur = ut + ((size_t)iocc * N + z) * N * N + y;
+      const cpx<T> *wr = xp + y * P;
+#pragma unroll
+      for (int k = 0; k < N; ++k) a[k] = cmul(cconj(ur[k * N]), wr[k]);
+      LineFFT<T, N, -1>::run(a);
+      cpx<T> *row = wk + (size_t)t * nxa - mlo;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int m = freq_of<N>(k);
+        if (m >= mlo && m <= mhi) row[m] = a[k];
+      }
+    }
+    __syncwarp();
+    for (int t = lane; t < nb * nxa; t += 32) {
+      const int il = t / nxa, xa = t - il * nxa;
+      cpx<T> *src = wk + (size_t)il * N * nxa + xa;
+      cpx<T> b[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) b[k] = src[k * nxa];
+      LineFFT<T, N, -1>::run(b);
+#pragma unroll
+      for (int k = 0; k < N; ++k) src[k * nxa] = b[k];
+    }
+    __syncwarp();
+    for (int e = lane; e < nb * nd; e += 32) {
+      const int il = e / nd, d = e - il * nd;
+      const size_t item = (size_t)col * no + (ilist ? ilist[i0 + il] : i0 + il);
+      tbuf[(item * N + z) * nd + d] = wk[(size_t)il * N * nxa + ytab[d]];
+    }
+    __syncwarp();
+  }
+}
+
 // setup: real-space occupied orbitals u[j][z][y][x] from z1 (cols = occupied orbitals)
 // (and the plane-transposed copy outt[j][z][x][y] that the plane kernel reads row-wise)
 template <typename T, int N>

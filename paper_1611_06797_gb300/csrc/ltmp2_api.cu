@@ -491,8 +491,10 @@ template <typename T> int tune_ctx(ltmp2_ctx *c, int *slab_out, int *var_out) {
   if (!rc) {
     const int ncols = best_slab * p.slots_per_prim() * p.n_occ;
     double best_plane = 1e300;
-    for (int pk = 0; pk < 3 && !rc; ++pk)
-      for (int ib : {2, 4, 8, 16}) {
+    static const int kIbs[2][4] = {{2, 4, 8, 16}, {1, 2, 3, 4}};   // planes per block; kernel 3: per warp step
+    for (int pk = 0; pk < 4 && !rc; ++pk)
+      for (int ibk = 0; ibk < 4; ++ibk) {
+        const int ib = kIbs[pk == 3 ? 1 : 0][ibk];
         if (ib > p.n_occ) continue;
         if (Path<T>::plane_pass(p, ncols, pk, ib, c->stream) != cudaSuccess) {  // infeasible shape
           cudaGetLastError();

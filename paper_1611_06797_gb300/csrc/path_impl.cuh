@@ -11,14 +11,20 @@ namespace ltmp2 {
 #define LTMP2_FOR_EACH_N(X) X(8) X(10) X(12) X(16) X(18) X(20) X(24) X(25) X(27) X(30) X(32) X(36) X(40)
 
 // Plane kernels: 0 = k_planes (full-plane passes), 1 = k_planes2 (compacted passes),
-// 2 = k_planes3 (product in registers, compact intermediate).
-// ib = occupied planes per block; 0 picks the default of each kernel.
+// 2 = k_planes3 (product in registers, compact intermediate), 3 = k_planes4 (as 2, each
+// warp on its own occupied planes without block barriers).
+// ib = occupied planes per block (kernel 3: per warp step); 0 picks the default of each kernel.
 template <typename T> static int plane_ib_default(const Plan &p, int kernel) {
   const int n = p.n;
   const size_t plane = (size_t)n * (n + 1) * sizeof(cpx<T>);
   const int nxa = p.mxhi_aux - p.mxlo_aux + 1;
   int ib;
-  if (kernel == 0) {
+  if (kernel == 3) {
+    // as many planes per warp step as fill the 32 lanes of the x pass, within ~48 KB
+    ib = (32 + n - 1) / n;
+    const size_t per = (size_t)kPlaneWarps * n * nxa * sizeof(cpx<T>);
+    while (ib > 1 && plane + ib * per > 48 * 1024) --ib;
+  } else if (kernel == 0) {
     ib = (int)((96 * 1024) / plane) - 1;   // about 96 KB of shared memory
     if (ib > 8) ib = 8;
   } else if (kernel == 2) {
@@ -43,6 +49,7 @@ template <typename T> static size_t plane_smem(const Plan &p, int kernel, int ib
   const int nxa = p.mxhi_aux - p.mxlo_aux + 1;
   if (kernel == 0) return plane * (1 + ib);
   if (kernel == 2) return plane + (size_t)ib * n * nxa * sizeof(cpx<T>) + sizeof(int) * p.n_daux;
+  if (kernel == 3) return plane + (size_t)kPlaneWarps * ib * n * nxa * sizeof(cpx<T>) + sizeof(int) * p.n_daux;
   return plane * (1 + ib) + (size_t)ib * p.n_daux * sizeof(cpx<T>) + 3 * sizeof(int) * nxa;
 }
 
@@ -50,7 +57,7 @@ template <typename T> static size_t plane_smem(const Plan &p, int kernel, int ib
 template <typename T> static cudaError_t launch_planes(const Plan &p, int ncols, int kernel, int ib, cudaStream_t st) {
   if (ib <= 0) ib = plane_ib_default<T>(p, kernel);
   const size_t smem = plane_smem<T>(p, kernel, ib);
-  int threads = ib * p.n;
+  int threads = kernel == 3 ? 32 * kPlaneWarps : ib * p.n;
   if (threads < 64) threads = 64;
   if (threads > 1024 || smem > 200 * 1024) return cudaErrorInvalidValue;
   switch (p.n) {
@@ -60,8 +67,10 @@ template <typename T> static cudaError_t launch_planes(const Plan &p, int ncols,
       k_planes<T, NN><<<dim3(NN, ncols), threads, smem, st>>>(p, ib, (const cpx<T> *)p.z1, (cpx<T> *)p.tbuf);  \
     else if (kernel == 1)                                                                                  \
       k_planes2<T, NN><<<dim3(NN, ncols), threads, smem, st>>>(p, ib, (const cpx<T> *)p.z1, (cpx<T> *)p.tbuf); \
-    else                                                                                                   \
+    else if (kernel == 2)                                                                                  \
       k_planes3<T, NN><<<dim3(NN, ncols), threads, smem, st>>>(p, ib, (const cpx<T> *)p.z1, (cpx<T> *)p.tbuf); \
+    else                                                                                                   \
+      k_planes4<T, NN><<<dim3(NN, ncols), threads, smem, st>>>(p, ib, (const cpx<T> *)p.z1, (cpx<T> *)p.tbuf); \
     break;
     LTMP2_FOR_EACH_N(LTMP2_CASE)
 #undef LTMP2_CASE
@@ -72,9 +81,9 @@ template <typename T> static cudaError_t launch_planes(const Plan &p, int ncols,
 }
 
 template <typename T> bool Path<T>::plane_feasible(const Plan &p, int kernel, int ib) {
-  if (kernel < 0 || kernel > 2 || ib < 0) return false;
+  if (kernel < 0 || kernel > 3 || ib < 0) return false;
   if (ib == 0) ib = plane_ib_default<T>(p, kernel);
-  const int threads = ib * p.n;
+  const int threads = kernel == 3 ? 32 * kPlaneWarps : ib * p.n;
   return threads <= 1024 && plane_smem<T>(p, kernel, ib) <= 200 * 1024;
 }
 
@@ -112,6 +121,8 @@ template <typename T> cudaError_t Path<T>::init_device() {
   e = cudaFuncSetAttribute(k_planes2<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
   if (e != cudaSuccess) return e;                                                                   \
   e = cudaFuncSetAttribute(k_planes3<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
+  if (e != cudaSuccess) return e;                                                                   \
+  e = cudaFuncSetAttribute(k_planes4<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
   if (e != cudaSuccess) return e;                                                                   \
   e = cudaFuncSetAttribute(k_zcol_k<T, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
   if (e != cudaSuccess) return e;

@@ -146,8 +146,8 @@ def test_cfg2_full_size_sampled_pairs():
 
 @pytest.mark.parametrize("name,real", [("cfg1", True), ("tiny2", False)])
 def test_plane_kernels_and_block_shapes_agree(name, real):
-    """The three plane-FFT kernels (full-plane passes, compacted passes, product in
-    registers) with several occupied-plane blocks, including a ragged last block, give
+    """The four plane-FFT kernels (full-plane passes, compacted passes, product in
+    registers, warp-autonomous) with several occupied-plane blocks, including a ragged last block, give
     the oracle's energies in FP64 and the FP64 energies within the bound in FP32."""
     s = solid(name)
     tau, w = _quad(s, 4)
@@ -155,7 +155,7 @@ def test_plane_kernels_and_block_shapes_agree(name, real):
     base = {}
     for precision in (L.FP64, L.FP32):
         ctx = L.setup_from_solid(s, precision=precision, real=real)
-        for pk in (0, 1, 2):
+        for pk in (0, 1, 2, 3):
             for ib in (0, 1, 3):
                 L.ltmp2_set_tuning(ctx, plane_kernel=pk, plane_ib=ib)
                 assert L.ltmp2_get_tuning(ctx)["plane_kernel"] == pk
@@ -169,7 +169,7 @@ def test_plane_kernels_and_block_shapes_agree(name, real):
                     bound = MEV_PER_ATOM * s.n_atoms
                     assert abs(ed - base["ed"]) < bound and abs(ex - base["ex"]) < bound
         with pytest.raises(L.Ltmp2Error):
-            L.ltmp2_set_tuning(ctx, plane_kernel=3)
+            L.ltmp2_set_tuning(ctx, plane_kernel=4)
         with pytest.raises(L.Ltmp2Error):
             L.ltmp2_set_tuning(ctx, plane_kernel=0, plane_ib=2000)
         L.ltmp2_destroy(ctx)
