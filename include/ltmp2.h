@@ -221,7 +221,8 @@ int ltmp2_energy_batch(ltmp2_ctx *const *ctxs, int n, const int *n_tau, const do
  * Weak occupied pairs are screened: their exchange co-densities (the N_o^2 part of
  * step (iv.b), Sec. III C) are not formed and their exchange energy is estimated by a
  * small pair-energy model instead; the direct term (step (iv.a)) stays exact for all
- * pairs.  The paper has no counterpart.                                              */
+ * pairs.  The paper has no counterpart.  ltmp2_energy_screened runs the whole form:
+ * descriptors, the model's estimates, the screening rule and the combined energy.     */
 
 /* keep: NULL (every pair contracted) or [n_occ][n_occ] bytes, symmetric, keep[i][i] != 0;
  * keep[i][j] == 0 leaves pair (i, j) out of the exchange contraction in later
@@ -249,6 +250,37 @@ int ltmp2_mlp_train(ltmp2_mlp *net, const float *X, const float *y, int n, int e
 /* y[n] = model(X[n][n_in]) in the units of the training targets.                    */
 int ltmp2_mlp_predict(const ltmp2_mlp *net, const float *X, int n, float *y);
 void ltmp2_mlp_destroy(ltmp2_mlp *net);
+
+/* Training set of the pair model from one exact all-pairs evaluation of ctx (Gamma point):
+ *   X [n_occ (n_occ + 1) / 2][LTMP2_NUM_DESC] the descriptors of ltmp2_pair_descriptors,
+ *   y [n_occ (n_occ + 1) / 2] the target ln|e^x_ij| of each unordered pair i <= j, where
+ *     e^x_ij is the exchange energy of the ordered pairs (i, j) and (j, i) together (of
+ *     (i, i) for i = j), from the contraction of every pair (any pair mask is cleared).
+ * Host arrays.  Errors: INVALID_ARG, UNSUPPORTED (k-point contexts), OOM, CUDA.       */
+int ltmp2_learned_training_data(ltmp2_ctx *ctx, int n_tau, const double *tau, const double *w, float *X,
+                                float *y);
+
+/* The screening rule.  est [n_occ (n_occ + 1) / 2]: non-negative estimates of |e^x_ij|
+ * per unordered pair (row order i, then j >= i).  Off-diagonal pairs are screened in
+ * ascending order of est (ties in row order) while the sum of the screened estimates
+ * stays <= budget (Ha); diagonal pairs are never screened.  keep [n_occ][n_occ] receives
+ * the pair mask (symmetric, 0 = screened); n_screened and est_screened (may be NULL) the
+ * number of screened unordered pairs and the sum of their estimates.  Host only.
+ * Errors: INVALID_ARG (sizes, a negative or non-finite estimate or budget), OOM.       */
+int ltmp2_screen_select(int n_occ, const double *est, double budget, unsigned char *keep, int *n_screened,
+                        double *est_screened);
+
+/* Learned-form energy.  The model net (LTMP2_NUM_DESC inputs, trained on the targets of
+ * ltmp2_learned_training_data) estimates |e^x_ij| = exp(prediction) for every unordered
+ * pair from the descriptors; ltmp2_screen_select picks the screened pairs for the budget
+ * (Ha, e.g. 0.1 meV/atom x atoms); their exchange co-densities are not formed, and
+ *   e_direct   = E_d of every pair (exact),
+ *   e_exchange = E_x of the contracted pairs + the screened pairs' estimates.
+ * info (may be NULL) [4]: screened unordered pairs, their estimated exchange (Ha), the
+ * contracted exchange (Ha), unordered pairs.  The pair mask of ctx is cleared afterwards.
+ * Errors: INVALID_ARG, UNSUPPORTED (k-point contexts), OOM, CUDA, TIMEOUT.            */
+int ltmp2_energy_screened(ltmp2_ctx *ctx, const ltmp2_mlp *net, int n_tau, const double *tau, const double *w,
+                          double budget, double *e_direct, double *e_exchange, double *info);
 
 /* ---------------------------------------------------------------- failure-path self-test
  * (no counterpart in the paper)  Every device-side wait of this library (the tcgen05

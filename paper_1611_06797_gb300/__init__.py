@@ -10,7 +10,8 @@ from .ltmp2 import (Context, Ltmp2Error, LIB_PATH, load_library, ltmp2_setup, lt
                     ltmp2_set_extrapolation, ltmp2_level_energies, ltmp2_extrapolate,
                     ltmp2_set_route, ROUTE_GREEN, ROUTE_OVERLAP, ltmp2_energy_uhf, ltmp2_selftest_wait,
                     ltmp2_autotune, ltmp2_get_tuning, ltmp2_set_tuning, ltmp2_batch_create,
-                    ltmp2_set_pair_mask, ltmp2_pair_descriptors, Mlp, NUM_DESC, ltmp2_energy_batch, Batch, ltmp2_strerror, setup_from_solid,
+                    ltmp2_set_pair_mask, ltmp2_pair_descriptors, Mlp, ltmp2_learned_training_data,
+                    ltmp2_screen_select, ltmp2_energy_screened, NUM_DESC, ltmp2_energy_batch, Batch, ltmp2_strerror, setup_from_solid,
                     ltmp2_setup_kpoints, setup_from_kpoint_solid,
                     STAGE_NAMES, FP64, FP32, FLAG_REAL_ORBITALS, FLAG_SIMT_GEMM, HARTREE_TO_MEV)
 
@@ -21,6 +22,7 @@ __all__ = ["Context", "Ltmp2Error", "LIB_PATH", "load_library", "ltmp2_setup", "
            "ltmp2_set_extrapolation", "ltmp2_level_energies", "ltmp2_extrapolate",
            "ltmp2_set_route", "ROUTE_GREEN", "ROUTE_OVERLAP", "ltmp2_energy_uhf", "ltmp2_selftest_wait",
            "ltmp2_autotune", "ltmp2_get_tuning", "ltmp2_set_tuning", "ltmp2_batch_create",
-           "ltmp2_set_pair_mask", "ltmp2_pair_descriptors", "Mlp", "NUM_DESC", "ltmp2_energy_batch", "Batch", "ltmp2_strerror", "setup_from_solid",
+           "ltmp2_set_pair_mask", "ltmp2_pair_descriptors", "Mlp", "ltmp2_learned_training_data",
+           "ltmp2_screen_select", "ltmp2_energy_screened", "NUM_DESC", "ltmp2_energy_batch", "Batch", "ltmp2_strerror", "setup_from_solid",
            "ltmp2_setup_kpoints", "setup_from_kpoint_solid",
            "STAGE_NAMES", "FP64", "FP32", "FLAG_REAL_ORBITALS", "FLAG_SIMT_GEMM", "HARTREE_TO_MEV"]

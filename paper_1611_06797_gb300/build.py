@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libltmp2.so")
 
 SOURCES = ["ltmp2_api.cu", "host_plan.cu", "kernels_f64.cu", "kernels_f32.cu", "gemm_tc.cu", "laplace.cpp",
-           "ltmp2_noalloc.cu", "mlp.cu", "probe.cu"]
+           "ltmp2_noalloc.cu", "mlp.cu", "probe.cu", "learned.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
               "--expt-relaxed-constexpr"]

@@ -550,6 +550,72 @@ struct ltmp2_batch {
 namespace {
 }  // namespace
 
+namespace {
+// descriptors of every unordered occupied pair (see ltmp2_pair_descriptors)
+int pair_descriptors(ltmp2_ctx *ctx, double *desc) {
+  if (!ctx || !desc) return LTMP2_ERR_INVALID_ARG;
+  Plan &p = ctx->p;
+  const int no = p.n_occ;
+  DeviceGuard g(ctx->device);
+  double *dmom = nullptr, *dov = nullptr;
+  if (cudaMalloc(&dmom, sizeof(double) * 6 * no) != cudaSuccess ||
+      cudaMalloc(&dov, sizeof(double) * (size_t)no * no) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(dmom);
+    return LTMP2_ERR_OOM;
+  }
+  cudaError_t e = p.precision == LTMP2_FP64 ? Path<double>::descriptors(p, dmom, dov, ctx->stream)
+                                            : Path<float>::descriptors(p, dmom, dov, ctx->stream);
+  std::vector<double> mom(6 * (size_t)no), ov((size_t)no * no), eps(p.n_orb);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(mom.data(), dmom, sizeof(double) * mom.size(), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(ov.data(), dov, sizeof(double) * ov.size(), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(eps.data(), p.eps, sizeof(double) * eps.size(), cudaMemcpyDeviceToHost);
+  cudaFree(dmom);
+  cudaFree(dov);
+  if (e != cudaSuccess) return cuda_status(e);
+  // periodic centroid (fractional) and spread (bohr) of each occupied density
+  const double tp = 6.283185307179586476925286766559;
+  std::vector<double> frac(3 * (size_t)no), spread(no);
+  for (int i = 0; i < no; ++i) {
+    double s2 = 0;
+    for (int k = 0; k < 3; ++k) {
+      const double re = mom[6 * i + 2 * k], im = mom[6 * i + 2 * k + 1];
+      double f = std::atan2(im, re) / tp;
+      frac[3 * i + k] = f - std::floor(f);
+      const double mag = std::max(std::sqrt(re * re + im * im), 1e-12);
+      const double sig = std::sqrt(-2.0 * std::log(std::min(mag, 1.0))) / tp;   // fractional units
+      const double alen = std::sqrt(ctx->lattice[3 * k] * ctx->lattice[3 * k] + ctx->lattice[3 * k + 1] * ctx->lattice[3 * k + 1] +
+                                    ctx->lattice[3 * k + 2] * ctx->lattice[3 * k + 2]);
+      s2 += (sig * alen) * (sig * alen);
+    }
+    spread[i] = std::sqrt(s2);
+  }
+  size_t row = 0;
+  for (int i = 0; i < no; ++i)
+    for (int j = i; j < no; ++j, ++row) {
+      double r[3] = {0, 0, 0};
+      for (int k = 0; k < 3; ++k) {
+        double df = frac[3 * i + k] - frac[3 * j + k];
+        df -= std::floor(df + 0.5);
+        for (int c = 0; c < 3; ++c) r[c] += df * ctx->lattice[3 * k + c];
+      }
+      const double dist = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+      double *f = desc + row * LTMP2_NUM_DESC;
+      f[0] = eps[i] - p.mu;
+      f[1] = eps[j] - p.mu;
+      f[2] = std::log10(std::max(ov[(size_t)i * no + j], 1e-300) /
+                        std::sqrt(std::max(ov[(size_t)i * no + i] * ov[(size_t)j * no + j], 1e-300)));
+      f[3] = dist;
+      f[4] = spread[i];
+      f[5] = spread[j];
+      f[6] = (i == j) ? 1.0 : 0.0;
+      f[7] = dist / (spread[i] + spread[j] + 1e-3);
+    }
+  return LTMP2_OK;
+}
+}  // namespace
+
 // spin-unrestricted form: both channels on the alpha context's stream
 namespace {
 template <typename T>
@@ -926,65 +992,11 @@ int ltmp2_set_pair_mask(ltmp2_ctx *ctx, const unsigned char *keep) {
 int ltmp2_pair_descriptors(ltmp2_ctx *ctx, double *desc) {
   if (ctx && ctx->p.nk > 0) return LTMP2_ERR_UNSUPPORTED;   // no k-point form
   if (!ctx || !desc) return LTMP2_ERR_INVALID_ARG;
-  Plan &p = ctx->p;
-  const int no = p.n_occ;
-  DeviceGuard g(ctx->device);
-  double *dmom = nullptr, *dov = nullptr;
-  if (cudaMalloc(&dmom, sizeof(double) * 6 * no) != cudaSuccess ||
-      cudaMalloc(&dov, sizeof(double) * (size_t)no * no) != cudaSuccess) {
-    cudaGetLastError();
-    cudaFree(dmom);
+  try {
+    return pair_descriptors(ctx, desc);
+  } catch (const std::bad_alloc &) {
     return LTMP2_ERR_OOM;
   }
-  cudaError_t e = p.precision == LTMP2_FP64 ? Path<double>::descriptors(p, dmom, dov, ctx->stream)
-                                            : Path<float>::descriptors(p, dmom, dov, ctx->stream);
-  std::vector<double> mom(6 * (size_t)no), ov((size_t)no * no), eps(p.n_orb);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  if (e == cudaSuccess) e = cudaMemcpy(mom.data(), dmom, sizeof(double) * mom.size(), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemcpy(ov.data(), dov, sizeof(double) * ov.size(), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemcpy(eps.data(), p.eps, sizeof(double) * eps.size(), cudaMemcpyDeviceToHost);
-  cudaFree(dmom);
-  cudaFree(dov);
-  if (e != cudaSuccess) return cuda_status(e);
-  // periodic centroid (fractional) and spread (bohr) of each occupied density
-  const double tp = 6.283185307179586476925286766559;
-  std::vector<double> frac(3 * (size_t)no), spread(no);
-  for (int i = 0; i < no; ++i) {
-    double s2 = 0;
-    for (int k = 0; k < 3; ++k) {
-      const double re = mom[6 * i + 2 * k], im = mom[6 * i + 2 * k + 1];
-      double f = std::atan2(im, re) / tp;
-      frac[3 * i + k] = f - std::floor(f);
-      const double mag = std::max(std::sqrt(re * re + im * im), 1e-12);
-      const double sig = std::sqrt(-2.0 * std::log(std::min(mag, 1.0))) / tp;   // fractional units
-      const double alen = std::sqrt(ctx->lattice[3 * k] * ctx->lattice[3 * k] + ctx->lattice[3 * k + 1] * ctx->lattice[3 * k + 1] +
-                                    ctx->lattice[3 * k + 2] * ctx->lattice[3 * k + 2]);
-      s2 += (sig * alen) * (sig * alen);
-    }
-    spread[i] = std::sqrt(s2);
-  }
-  size_t row = 0;
-  for (int i = 0; i < no; ++i)
-    for (int j = i; j < no; ++j, ++row) {
-      double r[3] = {0, 0, 0};
-      for (int k = 0; k < 3; ++k) {
-        double df = frac[3 * i + k] - frac[3 * j + k];
-        df -= std::floor(df + 0.5);
-        for (int c = 0; c < 3; ++c) r[c] += df * ctx->lattice[3 * k + c];
-      }
-      const double dist = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-      double *f = desc + row * LTMP2_NUM_DESC;
-      f[0] = eps[i] - p.mu;
-      f[1] = eps[j] - p.mu;
-      f[2] = std::log10(std::max(ov[(size_t)i * no + j], 1e-300) /
-                        std::sqrt(std::max(ov[(size_t)i * no + i] * ov[(size_t)j * no + j], 1e-300)));
-      f[3] = dist;
-      f[4] = spread[i];
-      f[5] = spread[j];
-      f[6] = (i == j) ? 1.0 : 0.0;
-      f[7] = dist / (spread[i] + spread[j] + 1e-3);
-    }
-  return LTMP2_OK;
 }
 
 int ltmp2_get_tuning(const ltmp2_ctx *ctx, int *values) {

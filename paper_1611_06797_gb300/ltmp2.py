@@ -553,7 +553,14 @@ def _learned_sig(lib):
             ("ltmp2_mlp_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, P(vp)]),
             ("ltmp2_mlp_train", ctypes.c_int, [vp, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.c_float, fp]),
             ("ltmp2_mlp_predict", ctypes.c_int, [vp, fp, ctypes.c_int, fp]),
-            ("ltmp2_mlp_destroy", None, [vp])]:
+            ("ltmp2_mlp_destroy", None, [vp]),
+            ("ltmp2_learned_training_data", ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_double),
+                                                           P(ctypes.c_double), fp, fp]),
+            ("ltmp2_screen_select", ctypes.c_int, [ctypes.c_int, P(ctypes.c_double), ctypes.c_double,
+                                                   P(ctypes.c_ubyte), P(ctypes.c_int), P(ctypes.c_double)]),
+            ("ltmp2_energy_screened", ctypes.c_int, [vp, vp, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double),
+                                                     ctypes.c_double, P(ctypes.c_double), P(ctypes.c_double),
+                                                     P(ctypes.c_double)])]:
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
@@ -619,3 +626,43 @@ class Mlp:
             self.destroy()
         except Exception:
             pass
+
+
+def ltmp2_learned_training_data(ctx: Context, tau, w):
+    """(X [pairs][NUM_DESC] float32, y [pairs] float32 = ln|e^x_ij|) of the unordered pairs i <= j."""
+    lib = _learned_sig(load_library())
+    tau = np.ascontiguousarray(np.asarray(tau, dtype=np.float64))
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    npairs = ctx.n_occ * (ctx.n_occ + 1) // 2
+    X = np.zeros((npairs, NUM_DESC), dtype=np.float32)
+    y = np.zeros(npairs, dtype=np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    _check(lib.ltmp2_learned_training_data(ctx.handle, len(tau), _dp(tau), _dp(w), X.ctypes.data_as(fp),
+                                           y.ctypes.data_as(fp)), "ltmp2_learned_training_data")
+    return X, y
+
+
+def ltmp2_screen_select(n_occ: int, est, budget: float):
+    """(keep [n_occ][n_occ] bool, screened unordered pairs, sum of their estimates)."""
+    lib = _learned_sig(load_library())
+    est = np.ascontiguousarray(np.asarray(est, dtype=np.float64))
+    keep = np.zeros((n_occ, n_occ), dtype=np.uint8)
+    n = ctypes.c_int()
+    tot = ctypes.c_double()
+    _check(lib.ltmp2_screen_select(int(n_occ), _dp(est), float(budget),
+                                   keep.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), ctypes.byref(n),
+                                   ctypes.byref(tot)), "ltmp2_screen_select")
+    return keep.astype(bool), int(n.value), float(tot.value)
+
+
+def ltmp2_energy_screened(ctx: Context, net: "Mlp", tau, w, budget: float) -> dict:
+    """Learned-form energy (include/ltmp2.h): E_d exact, E_x of the kept pairs plus the model's
+    estimates of the screened ones."""
+    lib = _learned_sig(load_library())
+    tau = np.ascontiguousarray(np.asarray(tau, dtype=np.float64))
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    ed, ex, info = np.zeros(1), np.zeros(1), np.zeros(4)
+    _check(lib.ltmp2_energy_screened(ctx.handle, net.handle, len(tau), _dp(tau), _dp(w), float(budget), _dp(ed),
+                                     _dp(ex), _dp(info)), "ltmp2_energy_screened")
+    return {"E_d": float(ed[0]), "E_x": float(ex[0]), "screened_pairs": int(info[0]),
+            "E_x_estimated": float(info[1]), "E_x_contracted": float(info[2]), "pairs": int(info[3])}

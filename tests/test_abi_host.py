@@ -240,3 +240,22 @@ def test_kpoint_setup_validates_on_the_host():
         L.ltmp2_setup_kpoints(**dict(base, mesh=[0, 1, 1]))
     expect("INVALID_ARG", n_occ=0)
     expect("INVALID_ARG", precision=3)
+
+
+def test_screen_select_rule():
+    """Off-diagonal pairs in ascending order of the estimate while the screened sum fits the
+    budget; the diagonal is never screened; ties fall in row order; bad estimates rejected."""
+    n = 4
+    i, j = np.triu_indices(n)
+    est = np.where(i == j, 1e-9, 0.0) + np.array([0, 5, 1, 3, 0, 2, 2, 0, 4, 0], float) * 1e-3
+    keep, nscr, tot = L.ltmp2_screen_select(n, est, 5.5e-3)
+    # ascending: (0,2)=1, (1,2)=2, (1,3)=2 (row order), (0,3)=3, ... -> 1 + 2 + 2 = 5 <= 5.5
+    assert nscr == 3 and abs(tot - 5e-3) < 1e-15
+    assert not keep[0, 2] and not keep[2, 0] and not keep[1, 2] and not keep[1, 3] and not keep[3, 1]
+    assert keep[0, 1] and keep[0, 3] and keep[2, 3] and np.all(np.diag(keep))
+    keep0, n0, t0 = L.ltmp2_screen_select(n, est, 0.0)
+    assert n0 == 0 and t0 == 0.0 and keep0.all()
+    for bad in (-1.0, np.nan):
+        e = est.copy(); e[3] = bad
+        with pytest.raises(L.Ltmp2Error):
+            L.ltmp2_screen_select(n, e, 1.0)

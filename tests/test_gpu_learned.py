@@ -5,8 +5,10 @@
 * The descriptors obey their definitions (Cauchy-Schwarz for the density overlaps,
   zero self-distance).
 * The MLP kernels fit a smooth function.
-* Screening with the trained surrogate keeps E within the 0.1 meV/atom budget of the
-  all-pairs contraction on a system it was not trained on.
+* The learned form through the C ABI (ltmp2_energy_screened), with the model trained on
+  the exact labels of smaller systems (ltmp2_learned_training_data), screens pairs of a
+  system it was not trained on and stays within the 0.1 meV/atom budget of the all-pairs
+  contraction, which judges it; with a zero budget it is the all-pairs contraction.
 """
 import numpy as np
 import pytest
@@ -51,7 +53,7 @@ def test_pair_descriptors_follow_their_definitions():
     s = solid("cfg1")
     ctx = L.setup_from_solid(s, real=True)
     d = L.ltmp2_pair_descriptors(ctx)
-    i, j = LF.pair_index(s.n_occ)
+    i, j = np.triu_indices(s.n_occ)
     assert d.shape == (len(i), L.NUM_DESC) and np.all(np.isfinite(d))
     # overlaps against a direct real-space evaluation of (1/N) sum |u_i|^2 |u_j|^2
     n = int(s.grid[0])
@@ -79,23 +81,26 @@ def test_mlp_fits_a_smooth_function():
 
 
 def test_learned_screening_within_budget_on_unseen_system():
-    train = [solid(n) for n in ("tiny2", "cfg1", "batch0", "batch1", "batch2")]
-    Xs, ys = [], []
+    train = [solid(n) for n in ("cfg1", "batch0", "batch1", "batch2", "batch3", "batch4")]
+    sets = []
     for s in train:
         c = L.setup_from_solid(s, precision=L.FP32, real=True)
-        X, r = LF.training_data(c, *_quad(s))
-        Xs.append(X)
-        ys.append(r)
+        sets.append((c, *_quad(s)))
+    X, y = LF.training_set(sets)
+    for c, _, _ in sets:
         L.ltmp2_destroy(c)
-    net = L.Mlp(seed=11)
-    net.train(np.concatenate(Xs), np.concatenate(ys), epochs=3000, lr=3e-3)
-    s = solid("batch3")
+    assert np.all(np.isfinite(y)) and X.shape == (len(y), L.NUM_DESC)
+    net = LF.train(X, y, epochs=3000, seed=11)
+    s = solid("batch5")
     tau, w = _quad(s)
     c = L.setup_from_solid(s, precision=L.FP32, real=True)
-    ed, ex, _ = L.ltmp2_energy(c, tau, w)
+    ed, ex, _ = L.ltmp2_energy(c, tau, w, pairs=False)
     budget = 0.1 * MEV * s.n_atoms
-    r = LF.screened_energy(c, tau, w, net, budget_ha=budget, share=1.0)
+    r = LF.screened_vs_exact(c, net, tau, w, budget, e_all=(ed, ex))
+    assert r["screened_pairs"] > 0 and r["E_x_estimated"] <= budget
     assert abs(r["E_d"] - ed) < 1e-9 * abs(ed)
-    assert abs(r["E_d"] + r["E_x"] - ed - ex) < budget
-    assert r["error_bound_Ha"] <= budget
-    assert r["screened_pairs"] >= 0
+    assert abs(r["E_d"] + r["E_x"] - ed - ex) < budget, (r, ed, ex)
+    # a zero budget screens nothing: the all-pairs contraction itself
+    r0 = LF.screened_vs_exact(c, net, tau, w, 0.0, e_all=(ed, ex))
+    assert r0["screened_pairs"] == 0 and r0["err_E_x"] < 1e-12 * abs(ex) and r0["err_E_d"] < 1e-12 * abs(ed)
+    L.ltmp2_destroy(c)
