@@ -249,6 +249,9 @@ int ltmp2_mlp_train(ltmp2_mlp *net, const float *X, const float *y, int n, int e
                     float *final_loss);
 /* y[n] = model(X[n][n_in]) in the units of the training targets.                    */
 int ltmp2_mlp_predict(const ltmp2_mlp *net, const float *X, int n, float *y);
+/* Root-mean-square residual of the last training run, in the units of the targets (0
+ * before any training).                                                              */
+int ltmp2_mlp_residual(const ltmp2_mlp *net, float *sigma);
 void ltmp2_mlp_destroy(ltmp2_mlp *net);
 
 /* Training set of the pair model from one exact all-pairs evaluation of ctx (Gamma point):
@@ -271,9 +274,12 @@ int ltmp2_screen_select(int n_occ, const double *est, double budget, unsigned ch
                         double *est_screened);
 
 /* Learned-form energy.  The model net (LTMP2_NUM_DESC inputs, trained on the targets of
- * ltmp2_learned_training_data) estimates |e^x_ij| = exp(prediction) for every unordered
- * pair from the descriptors; ltmp2_screen_select picks the screened pairs for the budget
- * (Ha, e.g. 0.1 meV/atom x atoms); their exchange co-densities are not formed, and
+ * ltmp2_learned_training_data) predicts y_ij ~ ln|e^x_ij| for every unordered pair from
+ * the descriptors, with the training residual sigma (ltmp2_mlp_residual).  Selecting the
+ * smallest predictions favours the pairs the model underestimates, so the screening
+ * decision is conservative: ltmp2_screen_select runs on exp(y_ij + 3 sigma) against the
+ * budget (Ha, e.g. 0.1 meV/atom x atoms), and a screened pair contributes the log-normal
+ * mean exp(y_ij + sigma^2 / 2).  The screened pairs' exchange co-densities are not formed:
  *   e_direct   = E_d of every pair (exact),
  *   e_exchange = E_x of the contracted pairs + the screened pairs' estimates.
  * info (may be NULL) [4]: screened unordered pairs, their estimated exchange (Ha), the

@@ -4,9 +4,10 @@
 // (step (iv.a)) stays exact for every pair.  The model predicts ln|e^x_ij| of an unordered
 // pair (both orders, i < j) from the cheap descriptors of ltmp2_pair_descriptors; it is
 // trained on labels that the exact contraction produces (ltmp2_learned_training_data).
-// Pairs are screened in ascending order of the estimate while the estimated screened
-// exchange stays within the caller's budget; the all-pairs contraction remains the judge
-// of the realised error.  Everything here runs through this library's own C entry points.
+// Pairs are screened in ascending order of a conservative estimate (three training
+// residuals above the prediction) while the screened sum stays within the caller's
+// budget; the all-pairs contraction remains the judge of the realised error.  Everything
+// here runs through this library's own C entry points.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,6 +19,8 @@
 #include "../../include/ltmp2.h"
 
 namespace {
+
+constexpr double kScreenZ = 3.0;   // residual standard deviations added to the screening decision
 
 int sizes_of(ltmp2_ctx *ctx, int *no, int *npairs) {
   int n_aux = 0, n_pw = 0, grid = 0;
@@ -64,12 +67,22 @@ int energy_screened(ltmp2_ctx *ctx, const ltmp2_mlp *net, int n_tau, const doubl
   std::vector<float> X, yp(npairs);
   if ((rc = descriptors_f(ctx, npairs, X))) return rc;
   if ((rc = ltmp2_mlp_predict(net, X.data(), npairs, yp.data()))) return rc;
-  std::vector<double> est(npairs);
-  for (int r = 0; r < npairs; ++r) est[r] = std::exp((double)yp[r]);
+  float sigma = 0.f;
+  if ((rc = ltmp2_mlp_residual(net, &sigma))) return rc;
+  const double sg = std::max(0.0, (double)sigma);
+  std::vector<double> sel(npairs), est(npairs);
+  for (int r = 0; r < npairs; ++r) {
+    sel[r] = std::exp((double)yp[r] + kScreenZ * sg);     // conservative: the decision
+    est[r] = std::exp((double)yp[r] + 0.5 * sg * sg);     // log-normal mean: the estimate
+  }
   std::vector<unsigned char> keep((size_t)no * no);
   int nscr = 0;
+  if ((rc = ltmp2_screen_select(no, sel.data(), budget, keep.data(), &nscr, nullptr))) return rc;
   double est_scr = 0.0;
-  if ((rc = ltmp2_screen_select(no, est.data(), budget, keep.data(), &nscr, &est_scr))) return rc;
+  size_t row = 0;
+  for (int i = 0; i < no; ++i)
+    for (int j = i; j < no; ++j, ++row)
+      if (!keep[(size_t)i * no + j]) est_scr += est[row];
   if ((rc = ltmp2_set_pair_mask(ctx, nscr > 0 ? keep.data() : nullptr))) return rc;
   double ed = 0, ex = 0;
   rc = ltmp2_energy(ctx, n_tau, tau, w, &ed, &ex, nullptr);

@@ -175,6 +175,7 @@ struct ltmp2_mlp {
   float *params = nullptr, *m = nullptr, *v = nullptr;
   std::vector<float> xmean, xstd;
   float ymean = 0.f, ystd = 1.f;
+  float resid = 0.f;   // root-mean-square training residual, in the units of the targets
   int steps = 0;
   ~ltmp2_mlp() {
     cudaFree(params);
@@ -285,12 +286,14 @@ int ltmp2_mlp_train(ltmp2_mlp *net, const float *X, const float *y, int n, int e
                                                (float)b2t);
   }
   cudaError_t e = cudaDeviceSynchronize();
-  if (e == cudaSuccess && final_loss) {
+  if (e == cudaSuccess) {
     std::vector<float> l(nblocks);
     cudaMemcpy(l.data(), lp, sizeof(float) * nblocks, cudaMemcpyDeviceToHost);
     double t = 0;
     for (float x : l) t += x;
-    *final_loss = (float)(t / n);  // mean squared error of the standardised targets
+    const double mse = t / n;  // mean squared error of the standardised targets
+    if (final_loss) *final_loss = (float)mse;
+    net->resid = (float)(std::sqrt(mse) * net->ystd);
   }
   cleanup();
   return e == cudaSuccess ? LTMP2_OK : LTMP2_ERR_CUDA;
@@ -320,6 +323,12 @@ int ltmp2_mlp_predict(const ltmp2_mlp *net, const float *X, int n, float *y) {
   cudaFree(dm);
   cudaFree(ds);
   return rc;
+}
+
+int ltmp2_mlp_residual(const ltmp2_mlp *net, float *sigma) {
+  if (!net || !sigma) return LTMP2_ERR_INVALID_ARG;
+  *sigma = net->resid;
+  return LTMP2_OK;
 }
 
 void ltmp2_mlp_destroy(ltmp2_mlp *net) { delete net; }

@@ -554,6 +554,7 @@ def _learned_sig(lib):
             ("ltmp2_mlp_train", ctypes.c_int, [vp, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.c_float, fp]),
             ("ltmp2_mlp_predict", ctypes.c_int, [vp, fp, ctypes.c_int, fp]),
             ("ltmp2_mlp_destroy", None, [vp]),
+            ("ltmp2_mlp_residual", ctypes.c_int, [vp, fp]),
             ("ltmp2_learned_training_data", ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_double),
                                                            P(ctypes.c_double), fp, fp]),
             ("ltmp2_screen_select", ctypes.c_int, [ctypes.c_int, P(ctypes.c_double), ctypes.c_double,
@@ -607,6 +608,12 @@ class Mlp:
         _check(load_library().ltmp2_mlp_train(self.handle, X.ctypes.data_as(fp), y.ctypes.data_as(fp), len(y),
                                               int(epochs), ctypes.c_float(lr), ctypes.byref(loss)), "ltmp2_mlp_train")
         return float(loss.value)
+
+    def residual(self) -> float:
+        """Root-mean-square training residual in the units of the targets."""
+        r = ctypes.c_float()
+        _check(_learned_sig(load_library()).ltmp2_mlp_residual(self.handle, ctypes.byref(r)), "ltmp2_mlp_residual")
+        return float(r.value)
 
     def predict(self, X) -> np.ndarray:
         X = np.ascontiguousarray(np.asarray(X, dtype=np.float32))
