@@ -660,11 +660,11 @@ def run_learned(args, local):
         c = L.setup_from_solid(sp, precision=L.FP32, real=True)
         sets.append(L.ltmp2_learned_training_data(c, t, w))
         L.ltmp2_destroy(c)
-    X = np.concatenate([x for x, _ in sets])
     y = np.concatenate([v for _, v in sets])
     t_label = time.time() - t0
     t1 = time.time()
-    net = LF.train(X, y, epochs=4000, seed=5)
+    margin = LF.calibrate_margin(sets, epochs=4000, seed=5)
+    net = LF.train(sets, epochs=4000, seed=5)
     t_train = time.time() - t1
     spec = SPECS[args.target]
     t2 = time.time()
@@ -691,7 +691,7 @@ def run_learned(args, local):
         return r, a.elapsed_time(b)
     with ClockSampler(local) as clk:
         (ed, ex, _), ms_all = timed(lambda: L.ltmp2_energy(c, tau, w, pairs=False))
-        r, ms_scr = timed(lambda: L.ltmp2_energy_screened(c, net, tau, w, budget))
+        r, ms_scr = timed(lambda: L.ltmp2_energy_screened(c, net, tau, w, budget, margin))
     L.ltmp2_destroy(c)
     pairs = s.n_occ * (s.n_occ + 1) // 2
     per_atom = HARTREE_TO_MEV / s.n_atoms
@@ -714,7 +714,9 @@ def run_learned(args, local):
             "E": abs(r["E_d"] + r["E_x"] - ed - ex) * per_atom,
             "E_dropping_screened": abs(r["E_x_contracted"] - ex) * per_atom},
         "within_0.1_meV_per_atom": abs(r["E_d"] + r["E_x"] - ed - ex) * per_atom <= 0.1,
-        "mlp": {"train_loss_std_units": net.loss, "train_s": t_train, "label_s": t_label, "samples": int(len(y))},
+        "mlp": {"train_loss_std_units": net.loss, "train_s": t_train, "label_s": t_label, "samples": int(len(y)),
+                "residual_ln": net.residual(), "screening_margin": margin,
+                "margin_from": "leave-one-system-out over the training systems, lowest 2 % of predictions, x2"},
         "clocks": clk.summary(), "setup_s": {"fixture": t_fix},
     }
 

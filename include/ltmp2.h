@@ -275,18 +275,19 @@ int ltmp2_screen_select(int n_occ, const double *est, double budget, unsigned ch
 
 /* Learned-form energy.  The model net (LTMP2_NUM_DESC inputs, trained on the targets of
  * ltmp2_learned_training_data) predicts y_ij ~ ln|e^x_ij| for every unordered pair from
- * the descriptors, with the training residual sigma (ltmp2_mlp_residual).  Selecting the
- * smallest predictions favours the pairs the model underestimates, so the screening
- * decision is conservative: ltmp2_screen_select runs on exp(y_ij + 3 sigma) against the
- * budget (Ha, e.g. 0.1 meV/atom x atoms), and a screened pair contributes the log-normal
- * mean exp(y_ij + sigma^2 / 2).  The screened pairs' exchange co-densities are not formed:
+ * the descriptors.  Selecting the smallest predictions favours the pairs the model
+ * underestimates, so the screening decision runs on an upper bound: ltmp2_screen_select
+ * takes margin x exp(y_ij) against the budget (Ha, e.g. 0.1 meV/atom x atoms), where
+ * margin >= 1 is the caller's validated bound on |e^x| / exp(y) for the lowest predictions
+ * (from systems held out of training).  A screened pair contributes exp(y_ij).  The
+ * screened pairs' exchange co-densities are not formed:
  *   e_direct   = E_d of every pair (exact),
  *   e_exchange = E_x of the contracted pairs + the screened pairs' estimates.
  * info (may be NULL) [4]: screened unordered pairs, their estimated exchange (Ha), the
  * contracted exchange (Ha), unordered pairs.  The pair mask of ctx is cleared afterwards.
- * Errors: INVALID_ARG, UNSUPPORTED (k-point contexts), OOM, CUDA, TIMEOUT.            */
+ * Errors: INVALID_ARG (also margin < 1), UNSUPPORTED (k-point contexts), OOM, CUDA, TIMEOUT. */
 int ltmp2_energy_screened(ltmp2_ctx *ctx, const ltmp2_mlp *net, int n_tau, const double *tau, const double *w,
-                          double budget, double *e_direct, double *e_exchange, double *info);
+                          double budget, double margin, double *e_direct, double *e_exchange, double *info);
 
 /* ---------------------------------------------------------------- failure-path self-test
  * (no counterpart in the paper)  Every device-side wait of this library (the tcgen05

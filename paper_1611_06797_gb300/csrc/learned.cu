@@ -4,9 +4,9 @@
 // (step (iv.a)) stays exact for every pair.  The model predicts ln|e^x_ij| of an unordered
 // pair (both orders, i < j) from the cheap descriptors of ltmp2_pair_descriptors; it is
 // trained on labels that the exact contraction produces (ltmp2_learned_training_data).
-// Pairs are screened in ascending order of a conservative estimate (three training
-// residuals above the prediction) while the screened sum stays within the caller's
-// budget; the all-pairs contraction remains the judge of the realised error.  Everything
+// Pairs are screened in ascending order of a calibrated upper bound (the estimate times a
+// margin that the caller validates on held-out systems) while the screened sum stays within
+// the caller's budget; the all-pairs contraction remains the judge of the realised error.  Everything
 // here runs through this library's own C entry points.
 #include <cuda_runtime.h>
 
@@ -19,8 +19,6 @@
 #include "../../include/ltmp2.h"
 
 namespace {
-
-constexpr double kScreenZ = 3.0;   // residual standard deviations added to the screening decision
 
 int sizes_of(ltmp2_ctx *ctx, int *no, int *npairs) {
   int n_aux = 0, n_pw = 0, grid = 0;
@@ -61,19 +59,16 @@ int training_data(ltmp2_ctx *ctx, int n_tau, const double *tau, const double *w,
 }
 
 int energy_screened(ltmp2_ctx *ctx, const ltmp2_mlp *net, int n_tau, const double *tau, const double *w,
-                    double budget, double *e_direct, double *e_exchange, double *info) {
+                    double budget, double margin, double *e_direct, double *e_exchange, double *info) {
   int no = 0, npairs = 0, rc;
   if ((rc = sizes_of(ctx, &no, &npairs))) return rc;
   std::vector<float> X, yp(npairs);
   if ((rc = descriptors_f(ctx, npairs, X))) return rc;
   if ((rc = ltmp2_mlp_predict(net, X.data(), npairs, yp.data()))) return rc;
-  float sigma = 0.f;
-  if ((rc = ltmp2_mlp_residual(net, &sigma))) return rc;
-  const double sg = std::max(0.0, (double)sigma);
   std::vector<double> sel(npairs), est(npairs);
   for (int r = 0; r < npairs; ++r) {
-    sel[r] = std::exp((double)yp[r] + kScreenZ * sg);     // conservative: the decision
-    est[r] = std::exp((double)yp[r] + 0.5 * sg * sg);     // log-normal mean: the estimate
+    est[r] = std::exp((double)yp[r]);   // the estimate that replaces the pair's exchange
+    sel[r] = margin * est[r];           // the screening decision: a calibrated upper bound
   }
   std::vector<unsigned char> keep((size_t)no * no);
   int nscr = 0;
@@ -148,12 +143,12 @@ int ltmp2_learned_training_data(ltmp2_ctx *ctx, int n_tau, const double *tau, co
 }
 
 int ltmp2_energy_screened(ltmp2_ctx *ctx, const ltmp2_mlp *net, int n_tau, const double *tau, const double *w,
-                          double budget, double *e_direct, double *e_exchange, double *info) {
+                          double budget, double margin, double *e_direct, double *e_exchange, double *info) {
   if (!ctx || !net || !tau || !w || n_tau < 1 || !e_direct || !e_exchange || !(budget >= 0.0) ||
-      !std::isfinite(budget))
+      !std::isfinite(budget) || !(margin >= 1.0) || !std::isfinite(margin))
     return LTMP2_ERR_INVALID_ARG;
   try {
-    return energy_screened(ctx, net, n_tau, tau, w, budget, e_direct, e_exchange, info);
+    return energy_screened(ctx, net, n_tau, tau, w, budget, margin, e_direct, e_exchange, info);
   } catch (const std::bad_alloc &) {
     return LTMP2_ERR_OOM;
   }

@@ -560,8 +560,8 @@ def _learned_sig(lib):
             ("ltmp2_screen_select", ctypes.c_int, [ctypes.c_int, P(ctypes.c_double), ctypes.c_double,
                                                    P(ctypes.c_ubyte), P(ctypes.c_int), P(ctypes.c_double)]),
             ("ltmp2_energy_screened", ctypes.c_int, [vp, vp, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double),
-                                                     ctypes.c_double, P(ctypes.c_double), P(ctypes.c_double),
-                                                     P(ctypes.c_double)])]:
+                                                     ctypes.c_double, ctypes.c_double, P(ctypes.c_double),
+                                                     P(ctypes.c_double), P(ctypes.c_double)])]:
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
@@ -662,14 +662,14 @@ def ltmp2_screen_select(n_occ: int, est, budget: float):
     return keep.astype(bool), int(n.value), float(tot.value)
 
 
-def ltmp2_energy_screened(ctx: Context, net: "Mlp", tau, w, budget: float) -> dict:
+def ltmp2_energy_screened(ctx: Context, net: "Mlp", tau, w, budget: float, margin: float = 1.0) -> dict:
     """Learned-form energy (include/ltmp2.h): E_d exact, E_x of the kept pairs plus the model's
-    estimates of the screened ones."""
+    estimates of the screened ones; margin: the validated upper-bound factor of the decision."""
     lib = _learned_sig(load_library())
     tau = np.ascontiguousarray(np.asarray(tau, dtype=np.float64))
     w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
     ed, ex, info = np.zeros(1), np.zeros(1), np.zeros(4)
-    _check(lib.ltmp2_energy_screened(ctx.handle, net.handle, len(tau), _dp(tau), _dp(w), float(budget), _dp(ed),
-                                     _dp(ex), _dp(info)), "ltmp2_energy_screened")
+    _check(lib.ltmp2_energy_screened(ctx.handle, net.handle, len(tau), _dp(tau), _dp(w), float(budget),
+                                     float(margin), _dp(ed), _dp(ex), _dp(info)), "ltmp2_energy_screened")
     return {"E_d": float(ed[0]), "E_x": float(ex[0]), "screened_pairs": int(info[0]),
             "E_x_estimated": float(info[1]), "E_x_contracted": float(info[2]), "pairs": int(info[3])}

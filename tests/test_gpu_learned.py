@@ -82,29 +82,28 @@ def test_mlp_fits_a_smooth_function():
 
 def test_learned_screening_within_budget_on_unseen_system():
     train = [solid(n) for n in ("cfg1", "batch0", "batch1", "batch2", "batch3", "batch4")]
-    sets = []
-    for s in train:
-        c = L.setup_from_solid(s, precision=L.FP32, real=True)
-        sets.append((c, *_quad(s)))
-    X, y = LF.training_set(sets)
-    for c, _, _ in sets:
+    ctxs = [(L.setup_from_solid(s, precision=L.FP32, real=True), *_quad(s)) for s in train]
+    sets = LF.training_sets(ctxs)
+    for c, _, _ in ctxs:
         L.ltmp2_destroy(c)
-    assert np.all(np.isfinite(y)) and X.shape == (len(y), L.NUM_DESC)
-    net = LF.train(X, y, epochs=3000, seed=11)
+    for X, y in sets:
+        assert np.all(np.isfinite(y)) and X.shape == (len(y), L.NUM_DESC)
+    margin = LF.calibrate_margin(sets, epochs=3000, seed=11)
+    net = LF.train(sets, epochs=3000, seed=11)
+    assert margin >= 2.0 and net.residual() > 0.0
     s = solid("batch5")
     tau, w = _quad(s)
     c = L.setup_from_solid(s, precision=L.FP32, real=True)
     ed, ex, _ = L.ltmp2_energy(c, tau, w, pairs=False)
     budget = 0.1 * MEV * s.n_atoms
-    assert 0.0 < net.residual() < 1.0                           # ln units
-    # the 0.1 meV/atom budget, and a ten times larger one that certainly screens pairs: in
-    # both the realised error (judged by the all-pairs contraction) stays within the budget
-    for b in (budget, 10 * budget):
-        r = LF.screened_vs_exact(c, net, tau, w, b, e_all=(ed, ex))
+    # the 0.1 meV/atom budget and larger ones: the realised error, judged by the all-pairs
+    # contraction, stays within each budget; the largest certainly screens pairs
+    for b in (budget, 10 * budget, 100 * budget):
+        r = LF.screened_vs_exact(c, net, tau, w, b, margin, e_all=(ed, ex))
         assert abs(r["E_d"] - ed) < 1e-9 * abs(ed)
-        assert abs(r["E_d"] + r["E_x"] - ed - ex) < b, (b, r, ed, ex)
+        assert abs(r["E_d"] + r["E_x"] - ed - ex) < b, (b, margin, r, ed, ex)
     assert r["screened_pairs"] > 0 and r["E_x_contracted"] < ex
     # a zero budget screens nothing: the all-pairs contraction itself
-    r0 = LF.screened_vs_exact(c, net, tau, w, 0.0, e_all=(ed, ex))
+    r0 = LF.screened_vs_exact(c, net, tau, w, 0.0, margin, e_all=(ed, ex))
     assert r0["screened_pairs"] == 0 and r0["err_E_x"] < 1e-12 * abs(ex) and r0["err_E_d"] < 1e-12 * abs(ed)
     L.ltmp2_destroy(c)
