@@ -60,10 +60,11 @@ extern "C" {
 /* ---------------------------------------------------------------- precision */
 /* LTMP2_FP64: complex128 FFTs, FP64 GEMMs, FP64 accumulation (the plain path).   */
 /* LTMP2_FP32: complex64 FFTs; transformed-state GEMM on tcgen05 tensor cores in  */
-/*             3xTF32 split precision (hi*hi + hi*lo + lo*hi), each 32-wide k    */
-/*             block's tensor-memory partial added to FP32 register sums;        */
-/*             Green's function on the CUDA cores in FP32; per-pair, per-tau and */
-/*             final sums in FP64.                                               */
+/*             3xTF32 split precision (hi*hi + hi*lo + lo*hi), each 16-wide k    */
+/*             block's tensor-memory partial added to FP32 register sums; with   */
+/*             real orbitals the Green's function P_r = R_v^T D R_v too (general */
+/*             orbitals: CUDA cores, compensated FP32 sums); per-pair, per-tau   */
+/*             and final sums in FP64.                                           */
 #define LTMP2_FP64 0
 #define LTMP2_FP32 1
 

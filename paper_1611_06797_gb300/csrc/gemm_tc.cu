@@ -100,9 +100,72 @@ cudaError_t tc_init(TcResources &r, void *mem, int rows_cap, int npw, int varian
 void tc_release(TcResources &r) {
   delete static_cast<tc::TcMaps *>(r.maps);
   r.maps = nullptr;
+  delete static_cast<tc::TcMaps *>(r.gmaps);
+  r.gmaps = nullptr;
+}
+
+static int kpad_of(int k) { return ((k + tc::BK - 1) / tc::BK) * tc::BK; }
+
+size_t tc_green_bytes(int npw, int nv) {
+  const size_t kp = (size_t)kpad_of(nv);
+  const size_t arows = 2 * (size_t)rows_pad(((npw + 1) / 2 + 63) / 64 * 64);
+  return sizeof(float) * ((size_t)npw * nv + kp * (2 * arows + 2 * (size_t)npw)) + 1024;
+}
+
+cudaError_t tc_green_init(TcResources &r, void *mem, const float *cv, int nv, cudaStream_t st) {
+  if (!r.real || r.variant != 5) return cudaErrorInvalidValue;
+  const int npw = r.npw;
+  r.nv = nv;
+  r.kpad_v = kpad_of(nv);
+  r.grows = (npw + 1) / 2;
+  const size_t arows = 2 * (size_t)rows_pad((r.grows + 63) / 64 * 64);
+  const size_t kp = (size_t)r.kpad_v;
+  float *f = static_cast<float *>(mem);
+  r.rvt = f;
+  f += ((size_t)npw * nv + 63) / 64 * 64;
+  r.gah = f; f += arows * kp;
+  r.gal = f; f += arows * kp;
+  r.gbh = f; f += (size_t)npw * kp;
+  r.gbl = f;
+  tc::TcMaps *mp = new tc::TcMaps();
+  int bad = 0;
+  bad |= make_map(&mp->a1h, r.gah, (int)arows, r.kpad_v, 128, tc::S_BK, CU_TENSOR_MAP_SWIZZLE_64B);
+  bad |= make_map(&mp->a1l, r.gal, (int)arows, r.kpad_v, 128, tc::S_BK, CU_TENSOR_MAP_SWIZZLE_64B);
+  bad |= make_map(&mp->bh, r.gbh, npw, r.kpad_v, tc::S_BN, tc::S_BK, CU_TENSOR_MAP_SWIZZLE_64B);
+  bad |= make_map(&mp->bl, r.gbl, npw, r.kpad_v, tc::S_BN, tc::S_BK, CU_TENSOR_MAP_SWIZZLE_64B);
+  if (bad) {
+    delete mp;
+    return cudaErrorInvalidValue;
+  }
+  r.gmaps = mp;
+  tc::k_transpose_f<<<dim3((npw + 31) / 32, (nv + 31) / 32), dim3(32, 8), 0, st>>>(nv, npw, cv, r.rvt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  tc::k_pack_rows<<<dim3((r.kpad_v + 255) / 256, npw), 256, 0, st>>>(r.rvt, nv, r.kpad_v, r.gbh, r.gbl);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  r.green = true;
+  return cudaSuccess;
+}
+
+cudaError_t tc_green(const TcResources &r, const float *dv, void *pt, cudaStream_t st) {
+  const tc::TcMaps &m = *static_cast<const tc::TcMaps *>(r.gmaps);
+  const int r64 = (r.grows + 63) / 64 * 64;
+  tc::k_pack_green_a<<<dim3((r.kpad_v + 255) / 256, r64), 256, 0, st>>>(r.rvt, dv, r.npw, r.nv, r.kpad_v, r.gah,
+                                                                        r.gal);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 grid((r.npw + tc::S_BN - 1) / tc::S_BN, r64 / 64);
+  tc::k_tc_cgemm_stacked<<<grid, 160, tc::S_SMEM, st>>>(m.a1h, m.a1l, m.bh, m.bl, r.grows, r.npw,
+                                                        r.kpad_v / tc::S_BK, static_cast<float2 *>(pt), r.npw, r.err);
+  return cudaGetLastError();
 }
 
 cudaError_t tc_pack_b(const TcResources &r, const void *pt, cudaStream_t st) {
+  if (r.green) {   // the pair-interleaved output of tc_green
+    tc::k_pack_b_pairs<<<dim3((r.kpad + 255) / 256, r.npw), 256, 0, st>>>(static_cast<const float2 *>(pt), r.npw,
+                                                                            r.kpad, r.bh, r.bl);
+    return cudaGetLastError();
+  }
   if (r.real) {
     tc::k_pack_b_real<<<dim3((r.kpad + 255) / 256, r.npw), 256, 0, st>>>(static_cast<const float *>(pt), r.npw,
                                                                            r.kpad, r.bh, r.bl);

@@ -451,6 +451,64 @@ __global__ void k_pack_b_real(const float *__restrict__ pr, int npw, int kpad, f
   }
 }
 
+// ---------------------------------------------------------------- Green's function operands
+// Real basis: P_r = R_v^T D R_v (Eq. SCHtransmatrix summed over the virtuals), K = n_v.
+// Two real rows of A = R_v^T D form one complex row of the stacked kernel (row 2m as Re,
+// row 2m + 1 as Im), so its float2 output is P_r with rows 2m and 2m + 1 interleaved per
+// column; B = R_v^T (row n = column n of R_v), split once per context.
+__global__ void k_transpose_f(int rows, int cols, const float *__restrict__ in, float *__restrict__ out) {
+  __shared__ float tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[k][threadIdx.x] = in[(size_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int c = c0 + k, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[(size_t)c * rows + r] = tile[threadIdx.x][k];
+  }
+}
+// A hi/lo, stacked rows: row 128 b + r <- A row 2 (64 b + r), row 128 b + 64 + r <- A row 2 (64 b + r) + 1
+__global__ void k_pack_green_a(const float *__restrict__ rvt, const float *__restrict__ dv, int npw, int nv, int kpad,
+                               float *__restrict__ ah, float *__restrict__ al) {
+  const int m = blockIdx.y;
+  const size_t r1 = (size_t)128 * (m / 64) + (m % 64), r2 = r1 + 64;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < kpad; a += gridDim.x * blockDim.x) {
+    const float d = a < nv ? dv[a] : 0.f;
+    const float re = (2 * m < npw && a < nv) ? rvt[(size_t)(2 * m) * nv + a] * d : 0.f;
+    const float im = (2 * m + 1 < npw && a < nv) ? rvt[(size_t)(2 * m + 1) * nv + a] * d : 0.f;
+    const float hr = tf32_rn(re), hi = tf32_rn(im);
+    ah[r1 * kpad + a] = hr;
+    al[r1 * kpad + a] = tf32_rn(re - hr);
+    ah[r2 * kpad + a] = hi;
+    al[r2 * kpad + a] = tf32_rn(im - hi);
+  }
+}
+// B hi/lo [rows][kpad] from a row-major real matrix with row length ld (zero past ld)
+__global__ void k_pack_rows(const float *__restrict__ x, int ld, int kpad, float *__restrict__ bh, float *__restrict__ bl) {
+  const int n = blockIdx.y;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < kpad; q += gridDim.x * blockDim.x) {
+    const float v = q < ld ? x[(size_t)n * ld + q] : 0.f;
+    const float h = tf32_rn(v);
+    bh[(size_t)n * kpad + q] = h;
+    bl[(size_t)n * kpad + q] = tf32_rn(v - h);
+  }
+}
+// the transformed-state GEMM's B from the pair-interleaved Green's function
+__global__ void k_pack_b_pairs(const float2 *__restrict__ c, int npw, int kpad, float *__restrict__ bh,
+                               float *__restrict__ bl) {
+  const int n = blockIdx.y;
+  const float2 *row = c + (size_t)(n / 2) * npw;
+  const bool odd = n & 1;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < kpad; q += gridDim.x * blockDim.x) {
+    const float v = q < npw ? (odd ? row[q].y : row[q].x) : 0.f;
+    const float h = tf32_rn(v);
+    bh[(size_t)n * kpad + q] = h;
+    bl[(size_t)n * kpad + q] = tf32_rn(v - h);
+  }
+}
+
 __global__ void __launch_bounds__(160, 2)
     k_tc_cgemm_stacked(const __grid_constant__ CUtensorMap tah, const __grid_constant__ CUtensorMap tal,
                        const __grid_constant__ CUtensorMap tbh, const __grid_constant__ CUtensorMap tbl, int M,

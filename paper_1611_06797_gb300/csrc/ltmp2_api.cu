@@ -217,7 +217,9 @@ template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys,
   if ((rc = dalloc_bytes(c, &p.u, cs * n3 * p.n_occ))) return rc;
   if ((rc = dalloc_bytes(c, &p.ut, cs * n3 * p.n_occ))) return rc;
   if ((rc = dalloc_bytes(c, &p.dscale, sizeof(T) * p.n_orb))) return rc;
-  if ((rc = dalloc_bytes(c, &p.pt, (p.real_basis ? sizeof(T) : cs) * (size_t)p.n_pw * p.n_pw))) return rc;
+  // real basis: one extra row, for the pair-interleaved Green's function of the tensor-core build
+  if ((rc = dalloc_bytes(c, &p.pt, (p.real_basis ? sizeof(T) * (size_t)(p.n_pw + 1) : cs * (size_t)p.n_pw) * p.n_pw)))
+    return rc;
   // slab capacity from the free memory
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
@@ -248,6 +250,13 @@ template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys,
     c->tc_mem = tcmem;
     e = tc_init(c->tc, tcmem, (int)max_cols, p.n_pw, 5, p.real_basis);
     if (e != cudaSuccess) return cuda_status(e);
+    if (p.real_basis) {
+      // the Green's function P_r = R_v^T D R_v on the tensor cores as well
+      void *gmem = nullptr;
+      if ((rc = dalloc_bytes(c, &gmem, tc_green_bytes(p.n_pw, p.n_v)))) return rc;
+      e = tc_green_init(c->tc, gmem, (const float *)p.cv, p.n_v, c->stream);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
     p.tc = &c->tc;
   }
   e = Path<T>::setup_occupied(p, cocc, c->stream);

@@ -188,6 +188,14 @@ cudaError_t Path<T>::green(const Plan &p, double tau, cudaStream_t st, StageTime
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (p.route == 1) return cudaSuccess;   // no Green's function on the paper's route
+  if constexpr (std::is_same<T, float>::value) {
+    if (p.tc && p.tc->green) {
+      // precision form, real basis: P_r on the tensor cores (3xTF32), then the split of P_r
+      // into the transformed-state GEMM's operands
+      if ((e = tc_green(*p.tc, (const float *)p.dscale + p.n_occ, p.pt, st)) != cudaSuccess) return e;
+      return tc_pack_b(*p.tc, p.pt, st);
+    }
+  }
   const int M = p.n_pw, N = p.n_pw, K = p.n_v;
   dim3 grid((N + 63) / 64, (M + 63) / 64);
   if (p.real_basis) {

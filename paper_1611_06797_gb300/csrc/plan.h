@@ -14,6 +14,13 @@ struct TcResources {
   float *a1h = nullptr, *a1l = nullptr, *a2h = nullptr, *a2l = nullptr, *bh = nullptr, *bl = nullptr;
   int *err = nullptr;      // device flag: a bounded wait ran out
   void *maps = nullptr;    // host copy of the six TMA tensor maps
+  // Green's function on the tensor cores (real basis): P_r = R_v^T D R_v with K = n_v,
+  // two real rows of R_v^T D per complex row of the stacked kernel
+  bool green = false;
+  int nv = 0, kpad_v = 0, grows = 0;   // virtuals, padded K, complex rows ceil(n_pw / 2)
+  float *rvt = nullptr;                // [n_pw][n_v] R_v^T
+  float *gah = nullptr, *gal = nullptr, *gbh = nullptr, *gbl = nullptr;
+  void *gmaps = nullptr;               // host copy of the four tensor maps
 };
 int tc_kpad(int npw);
 size_t tc_bytes(int rows_cap, int npw);
@@ -21,6 +28,11 @@ cudaError_t tc_init(TcResources &r, void *mem, int rows_cap, int npw, int varian
 int tc_variant_bn(int variant);
 void tc_release(TcResources &r);
 cudaError_t tc_pack_b(const TcResources &r, const void *pt, cudaStream_t st);
+// Green's function on the tensor cores: device bytes, set-up (transpose and split of the
+// virtuals' real coordinates cv [n_v][n_pw], once) and one build into pt (pair-interleaved)
+size_t tc_green_bytes(int npw, int nv);
+cudaError_t tc_green_init(TcResources &r, void *mem, const float *cv, int nv, cudaStream_t st);
+cudaError_t tc_green(const TcResources &r, const float *dv, void *pt, cudaStream_t st);
 cudaError_t tc_wgemm(const TcResources &r, const void *st_in, int rows, void *wt, cudaStream_t st);
 // one bounded wait on an mbarrier that never completes (failure-path self-test)
 cudaError_t tc_wait_selftest(int *err, unsigned long long limit_ns, cudaStream_t st);
@@ -132,7 +144,9 @@ enum Stage {
 template <typename T> struct Path {
   // kernel launches per Green's function build and per slab (the tcgen05 path of the
   // precision form adds one operand-packing launch to each)
-  static int green_launches(const Plan &p) { return p.route == 1 ? 1 : (p.tc ? 3 : 2); }
+  static int green_launches(const Plan &p) {
+    return p.route == 1 ? 1 : (p.tc ? (p.tc->green ? 4 : 3) : 2);
+  }
   static int slab_launches(const Plan &p) {
     if (p.route == 1) return 7 + (p.n_lev > 1 ? 1 : 0);   // no gather, CUDA-core product
     return (p.tc ? 8 : 7) + (p.real_basis ? 1 : 0) + (p.n_lev > 1 ? 1 : 0);
