@@ -168,8 +168,15 @@ int ltmp2_set_slab_size(ltmp2_ctx *ctx, int n);
 /* ---------------------------------------------------------------- batching form
  * Several systems of uneven grids and orbital counts in one launch.  The outer loops
  * of Sec. III A (tau points, then slabs of the G' loop, Sec. III B) of every system are
- * captured into one CUDA graph, one branch per system on its own stream, so a run is a
- * single graph launch in which the systems' kernels overlap on the GPU.               */
+ * captured into one CUDA graph, so a run is a single graph launch.  When every system
+ * allows it (Gamma point, one precision, no cutoff levels, the Green's-function route,
+ * at most 16 systems) the graph runs in rounds: round r takes the r-th (tau, slab) of every
+ * system that still has one; each system's gather, transformed-state GEMM and z transform
+ * run on its own branch, then ONE persistent plane-FFT launch and ONE persistent column
+ * launch serve the co-density items of all those systems (resident thread blocks take
+ * (system, column, plane) and (system, pair) items from a device counter), then each
+ * system's direct term and accumulation.  Otherwise every system is one graph branch.
+ * FP64 energies equal ltmp2_energy's to rounding of the summation order.              */
 
 /* Autotuner: times one slab of the path for each candidate (slab sizes down from the
  * setup capacity; in LTMP2_FP32 also the two tensor-core GEMM layouts) and keeps the
@@ -211,6 +218,9 @@ int ltmp2_batch_run(ltmp2_batch *b, double *e_direct, double *e_exchange);
 
 /* Number of kernel nodes in the batch graph (all systems).                          */
 int ltmp2_batch_kernel_nodes(const ltmp2_batch *b, long long *count);
+
+/* *persistent = 1 when b runs in rounds with the shared persistent FFT stages, else 0. */
+int ltmp2_batch_mode(const ltmp2_batch *b, int *persistent);
 
 void ltmp2_batch_destroy(ltmp2_batch *b);
 

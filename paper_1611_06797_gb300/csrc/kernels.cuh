@@ -536,15 +536,14 @@ __global__ void k_planes2(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> 
 //           columns of one m1 are nxa apart: no bank conflicts) and written coalesced to
 //           tbuf[(col, i)][z][d_aux].
 template <typename T, int N>
-__global__ void k_planes3(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> *__restrict__ tbuf) {
+__device__ __forceinline__ void planes3_body(const Plan &p, int ib, int z, int col, const cpx<T> *__restrict__ z1,
+                                             cpx<T> *__restrict__ tbuf, unsigned char *smem_raw) {
   constexpr int P = N + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T> *xp = reinterpret_cast<cpx<T> *>(smem_raw);
   const int nxa = p.mxhi_aux - p.mxlo_aux + 1;   // odd: the aux sphere is symmetric
   const int nd = p.n_daux;
   cpx<T> *wk = xp + N * P;                    // [ib][N][nxa]
   int *ytab = reinterpret_cast<int *>(wk + (size_t)ib * N * nxa);   // [nd] position of disk column d in a plane of wk
-  const int z = blockIdx.x, col = blockIdx.y;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int no = p.n_occ;
   const int mlo = p.mxlo_aux, mhi = p.mxhi_aux;
@@ -596,6 +595,12 @@ __global__ void k_planes3(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> 
     }
     __syncthreads();
   }
+}
+
+template <typename T, int N>
+__global__ void k_planes3(Plan p, int ib, const cpx<T> *__restrict__ z1, cpx<T> *__restrict__ tbuf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  planes3_body<T, N>(p, ib, blockIdx.x, blockIdx.y, z1, tbuf, smem_raw);
 }
 
 // Same result as k_planes3 with no block barrier after the w plane is transformed: each of
@@ -747,9 +752,9 @@ __device__ __forceinline__ void level_reduce_store(const Plan &p, const cpx<T> *
 }
 
 template <typename T, int N, bool LEV>
-__global__ void __launch_bounds__(256) k_zcol(Plan p, int gp0, int np, const cpx<T> *__restrict__ tbuf, cpx<T> *__restrict__ mdiag,
-                       double2 *__restrict__ sx) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void zcol_body(const Plan &p, int gp0, int np, int pair, const cpx<T> *__restrict__ tbuf,
+                                          cpx<T> *__restrict__ mdiag, double2 *__restrict__ sx,
+                                          unsigned char *smem_raw) {
   cpx<T> *MA = reinterpret_cast<cpx<T> *>(smem_raw);
   cpx<T> *PR = MA + p.n_aux;   // LEV only: v(G) times the product, per G
   const int no = p.n_occ;
@@ -757,14 +762,14 @@ __global__ void __launch_bounds__(256) k_zcol(Plan p, int gp0, int np, const cpx
   int i, j, gpl, slotA, slotB;
   bool self = false;
   if (!p.real_orb) {
-    gpl = blockIdx.x / (no * no);
-    const int r = blockIdx.x % (no * no);
+    gpl = pair / (no * no);
+    const int r = pair % (no * no);
     i = r / no; j = r % no;
     slotA = gpl; slotB = gpl + np;
   } else {
     const int npairs = no * (no + 1) / 2;
-    gpl = blockIdx.x / npairs;
-    int t = blockIdx.x % npairs;
+    gpl = pair / npairs;
+    int t = pair % npairs;
     i = 0;
     while (t >= no - i) { t -= no - i; ++i; }
     j = i + t;
@@ -850,6 +855,13 @@ __global__ void __launch_bounds__(256) k_zcol(Plan p, int gp0, int np, const cpx
   } else {
     block_reduce_store<T>((double)accx, (double)accy, sx + elem, transpose ? sx + elem_t : nullptr);
   }
+}
+
+template <typename T, int N, bool LEV>
+__global__ void __launch_bounds__(256) k_zcol(Plan p, int gp0, int np, const cpx<T> *__restrict__ tbuf,
+                                              cpx<T> *__restrict__ mdiag, double2 *__restrict__ sx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  zcol_body<T, N, LEV>(p, gp0, np, blockIdx.x, tbuf, mdiag, sx, smem_raw);
 }
 
 // ---------------------------------------------------------------- direct term

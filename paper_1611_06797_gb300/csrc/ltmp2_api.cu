@@ -540,6 +540,9 @@ template <typename T> int tune_ctx(ltmp2_ctx *c, int *slab_out, int *var_out) {
 // launch; the graph is replayed by ltmp2_batch_run.
 struct ltmp2_batch {
   int device = 0;
+  bool persistent = false;        // shared persistent FFT stages per round (else one branch per system)
+  void *d_plans = nullptr;        // persistent mode: the systems' plans on the device
+  int *d_counters = nullptr;      // persistent mode: the two work-queue counters
   std::vector<ltmp2_ctx *> ctxs;
   std::vector<long long> launches;
   cudaStream_t origin = nullptr;
@@ -548,6 +551,8 @@ struct ltmp2_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   ~ltmp2_batch() {
+    cudaFree(d_plans);
+    cudaFree(d_counters);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     for (auto e : events) cudaEventDestroy(e);
@@ -622,6 +627,107 @@ int pair_descriptors(ltmp2_ctx *ctx, double *desc) {
       f[7] = dist / (spread[i] + spread[j] + 1e-3);
     }
   return LTMP2_OK;
+}
+}  // namespace
+
+// Batching form, persistent mode: rounds of (tau, slab) across the systems; per round each
+// active system's pre-FFT phase on its own branch, then one persistent plane launch and one
+// persistent column launch over the items of every active system, then each system's direct
+// term and accumulation.  Captured on b->origin.
+namespace {
+template <typename T>
+int capture_rounds(ltmp2_batch *b, ltmp2_ctx *const *ctxs, int n, const int *n_tau, const double *const *tau,
+                   const double *const *w) {
+  std::vector<Plan> plans(n);
+  std::vector<int> ib(n), nslab(n), rounds(n);
+  size_t smem_p = 0, smem_c = 0;
+  int rmax = 0;
+  for (int i = 0; i < n; ++i) {
+    const Plan &p = ctxs[i]->p;
+    plans[i] = p;
+    ib[i] = std::max(1, std::min(kPersistThreads / p.n, p.n_occ));
+    smem_p = std::max(smem_p, Path<T>::plane_smem_for(p, ib[i]));
+    smem_c = std::max(smem_c, (size_t)p.n_aux * sizeof(CT<T>));
+    nslab[i] = (p.n_prim + p.max_prim - 1) / p.max_prim;
+    rounds[i] = n_tau[i] * nslab[i];
+    rmax = std::max(rmax, rounds[i]);
+  }
+  if (smem_p > 200 * 1024 || smem_c > 200 * 1024) return LTMP2_ERR_UNSUPPORTED;
+  if (cudaMalloc(&b->d_plans, sizeof(Plan) * n) != cudaSuccess || cudaMalloc(&b->d_counters, 2 * sizeof(int)) != cudaSuccess)
+    return LTMP2_ERR_OOM;
+  int rc = cuda_status(cudaMemcpy(b->d_plans, plans.data(), sizeof(Plan) * n, cudaMemcpyHostToDevice));
+  if (!rc) rc = cuda_status(Path<T>::persist_attributes(smem_p, smem_c));
+  const int blocks_p = Path<T>::persist_blocks(true, smem_p), blocks_c = Path<T>::persist_blocks(false, smem_c);
+  if (!rc && (blocks_p < 1 || blocks_c < 1)) rc = LTMP2_ERR_CUDA;
+  if (rc) return rc;
+  const Plan *dp = static_cast<const Plan *>(b->d_plans);
+  if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LTMP2_ERR_CUDA;
+  rc = cuda_status(cudaEventRecord(b->events[n], b->origin));
+  for (int i = 0; i < n && !rc; ++i) {
+    rc = cuda_status(cudaStreamWaitEvent(b->streams[i], b->events[n], 0));
+    if (!rc) rc = cuda_status(Path<T>::zero_acc(ctxs[i]->p, b->streams[i]));
+    b->launches[i] += 1;
+  }
+  long long shared = 0;
+  for (int r = 0; r < rmax && !rc; ++r) {
+    BatchRound rp, rcol;
+    std::vector<int> act, gp0(n), np(n);
+    for (int i = 0; i < n; ++i)
+      if (r < rounds[i]) act.push_back(i);
+    for (int i : act) {
+      const Plan &p = ctxs[i]->p;
+      const int k = r / nslab[i], j = r % nslab[i];
+      gp0[i] = j * p.max_prim;
+      np[i] = std::min(p.max_prim, p.n_prim - gp0[i]);
+      if (j == 0) {
+        if ((rc = cuda_status(Path<T>::green(p, tau[i][k], b->streams[i], nullptr)))) break;
+        b->launches[i] += Path<T>::green_launches(p);
+      }
+      if ((rc = cuda_status(Path<T>::slab_pre(p, gp0[i], np[i], b->streams[i], nullptr)))) break;
+      b->launches[i] += Path<T>::slab_launches(p) - 4 - (p.n_lev > 1 ? 1 : 0);   // all but plane, column, direct, accum
+      if ((rc = cuda_status(cudaEventRecord(b->events[i], b->streams[i])))) break;
+      if ((rc = cuda_status(cudaStreamWaitEvent(b->origin, b->events[i], 0)))) break;
+    }
+    if (rc) break;
+    rp.nsys = rcol.nsys = (int)act.size();
+    for (int e = 0; e < rp.nsys; ++e) {
+      const int i = act[e];
+      const Plan &p = ctxs[i]->p;
+      const int ncols = np[i] * p.slots_per_prim() * p.n_occ;
+      const int npairs = p.real_orb ? np[i] * (p.n_occ * (p.n_occ + 1) / 2) : np[i] * p.n_occ * p.n_occ;
+      rp.sys[e] = rcol.sys[e] = i;
+      rp.gp0[e] = rcol.gp0[e] = gp0[i];
+      rp.np[e] = rcol.np[e] = np[i];
+      rp.ib[e] = rcol.ib[e] = ib[i];
+      rp.first[e + 1] = rp.first[e] + p.n * ncols;
+      rcol.first[e + 1] = rcol.first[e] + npairs;
+    }
+    if ((rc = cuda_status(Path<T>::planes_persist(dp, rp, b->d_counters, blocks_p, smem_p, b->origin)))) break;
+    if ((rc = cuda_status(Path<T>::zcol_persist(dp, rcol, b->d_counters + 1, blocks_c, smem_c, b->origin)))) break;
+    shared += 2;
+    if ((rc = cuda_status(cudaEventRecord(b->events[n], b->origin)))) break;
+    for (int i : act) {
+      const Plan &p = ctxs[i]->p;
+      const int k = r / nslab[i];
+      const double nfft = (double)p.n * p.n * p.n;
+      const double coef = w[i][k] / (p.omega * p.omega * nfft * nfft);
+      if ((rc = cuda_status(cudaStreamWaitEvent(b->streams[i], b->events[n], 0)))) break;
+      if ((rc = cuda_status(Path<T>::slab_post(p, gp0[i], np[i], coef, b->streams[i], nullptr)))) break;
+      b->launches[i] += 2;
+      if (r == rounds[i] - 1) {
+        if ((rc = cuda_status(Path<T>::finish(p, b->streams[i], nullptr)))) break;
+        b->launches[i] += 1;
+      }
+    }
+  }
+  for (int i = 0; i < n && !rc; ++i) {
+    rc = cuda_status(cudaEventRecord(b->events[i], b->streams[i]));
+    if (!rc) rc = cuda_status(cudaStreamWaitEvent(b->origin, b->events[i], 0));
+  }
+  b->launches[0] += shared;
+  const cudaError_t ec = cudaStreamEndCapture(b->origin, &b->graph);
+  if (rc) return rc;
+  return cuda_status(ec);
 }
 }  // namespace
 
@@ -1069,6 +1175,22 @@ int ltmp2_batch_create(ltmp2_ctx *const *ctxs, int n, const int *n_tau, const do
     if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess) return fail(LTMP2_ERR_CUDA);
   for (auto &e : b->events)
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(LTMP2_ERR_CUDA);
+  // persistent shared FFT stages when every system allows them (Gamma point, one precision, no
+  // cutoff levels, the Green's-function route), else one graph branch per system
+  bool persist = n <= kBatchMax;
+  for (int i = 0; i < n; ++i) {
+    const Plan &p = ctxs[i]->p;
+    persist = persist && p.nk == 0 && p.n_lev < 2 && p.route == 0 && p.precision == ctxs[0]->p.precision;
+  }
+  if (persist) {
+    b->persistent = true;
+    const int prc = ctxs[0]->p.precision == LTMP2_FP64 ? capture_rounds<double>(b, ctxs, n, n_tau, tau, w)
+                                                      : capture_rounds<float>(b, ctxs, n, n_tau, tau, w);
+    if (prc) return fail(prc);
+    if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) return fail(LTMP2_ERR_CUDA);
+    *out = b;
+    return LTMP2_OK;
+  }
   if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(LTMP2_ERR_CUDA);
   int rc = cuda_status(cudaEventRecord(b->events[n], b->origin));
   for (int i = 0; i < n && !rc; ++i) {
@@ -1119,6 +1241,12 @@ int ltmp2_batch_kernel_nodes(const ltmp2_batch *b, long long *count) {
   long long t = 0;
   for (long long x : b->launches) t += x;
   *count = t;
+  return LTMP2_OK;
+}
+
+int ltmp2_batch_mode(const ltmp2_batch *b, int *persistent) {
+  if (!b || !persistent) return LTMP2_ERR_INVALID_ARG;
+  *persistent = b->persistent ? 1 : 0;
   return LTMP2_OK;
 }
 

@@ -217,7 +217,7 @@ cudaError_t Path<T>::green(const Plan &p, double tau, cudaStream_t st, StageTime
 }
 
 template <typename T>
-cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStream_t st, StageTimer *tm) {
+cudaError_t Path<T>::slab_pre(const Plan &p, int gp0, int np, cudaStream_t st, StageTimer *tm) {
   const int n = p.n, no = p.n_occ;
   const int nslots = np * p.slots_per_prim();
   const int ncols = nslots * no;
@@ -272,6 +272,28 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     w_pw = (const cpx<T> *)p.st;
   }
+  switch (n) {
+#define LTMP2_CASE(NN)                                                                                  \
+  case NN: {                                                                                            \
+    ScopedStage s(tm, kStageGatherZ);                                                                   \
+    k_w_zinv<T, NN><<<dim3((p.n_dorb + 127) / 128, ncols), 128, 0, st>>>(p, p.n_pw, w_pw, (cpx<T> *)p.z1); \
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;                                              \
+  } break;
+    LTMP2_FOR_EACH_N(LTMP2_CASE)
+#undef LTMP2_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStream_t st, StageTimer *tm) {
+  const int n = p.n, no = p.n_occ;
+  const int nslots = np * p.slots_per_prim();
+  const int ncols = nslots * no;
+  cudaError_t e;
+  if ((e = slab_pre(p, gp0, np, st, tm)) != cudaSuccess) return e;
   const bool lev = p.n_lev > 1;
   const size_t smem_col = (lev ? 2 : 1) * (size_t)p.n_aux * sizeof(cpx<T>);
   const int npairs = p.real_orb ? np * (no * (no + 1) / 2) : np * no * no;
@@ -280,12 +302,6 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
   switch (n) {
 #define LTMP2_CASE(NN)                                                                                  \
   case NN: {                                                                                            \
-    {                                                                                                   \
-      ScopedStage s(tm, kStageGatherZ);                                                                 \
-      k_w_zinv<T, NN><<<dim3((p.n_dorb + 127) / 128, ncols), 128, 0, st>>>(p, p.n_pw, w_pw,              \
-                                                                          (cpx<T> *)p.z1);               \
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;                                            \
-    }                                                                                                   \
     {                                                                                                   \
       ScopedStage s(tm, kStagePlane);                                                                   \
       if ((e = launch_planes<T>(p, ncols, p.plane_kernel, p.plane_ib, st)) != cudaSuccess) return e;    \
@@ -306,6 +322,14 @@ cudaError_t Path<T>::slab(const Plan &p, int gp0, int np, double coef, cudaStrea
     default:
       return cudaErrorInvalidValue;
   }
+  return slab_post(p, gp0, np, coef, st, tm);
+}
+
+template <typename T>
+cudaError_t Path<T>::slab_post(const Plan &p, int gp0, int np, double coef, cudaStream_t st, StageTimer *tm) {
+  const int no = p.n_occ;
+  const bool lev = p.n_lev > 1;
+  cudaError_t e;
   {
     ScopedStage s(tm, kStageDirect);
     int th = no < 128 ? ((no + 31) / 32) * 32 : 128;
@@ -416,6 +440,109 @@ cudaError_t Path<T>::slab_k(const Plan &p, int gp0, int np, double coef, cudaStr
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- batching form: persistent stages
+// Thread blocks of kPersistThreads stay resident and take items from a device counter:
+// plane items (system, column, z) and column items (system, pair) of every active system of
+// the round, each run by the same body as the system's own kernel (dispatch on its grid).
+template <typename T>
+__global__ void __launch_bounds__(kPersistThreads) k_planes_persist(const Plan *__restrict__ plans, BatchRound r,
+                                                                     int *__restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  const int total = r.first[r.nsys];
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) return;
+    int e = 0;
+    while (item >= r.first[e + 1]) ++e;
+    const Plan &p = plans[r.sys[e]];
+    const int local = item - r.first[e];
+    const int z = local % p.n, col = local / p.n;
+    switch (p.n) {
+#define LTMP2_CASE(NN)                                                                                        \
+  case NN:                                                                                                    \
+    planes3_body<T, NN>(p, r.ib[e], z, col, (const cpx<T> *)p.z1, (cpx<T> *)p.tbuf, smem_raw);               \
+    break;
+      LTMP2_FOR_EACH_N(LTMP2_CASE)
+#undef LTMP2_CASE
+      default:
+        break;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPersistThreads) k_zcol_persist(const Plan *__restrict__ plans, BatchRound r,
+                                                                   int *__restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  const int total = r.first[r.nsys];
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) return;
+    int e = 0;
+    while (item >= r.first[e + 1]) ++e;
+    const Plan &p = plans[r.sys[e]];
+    const int local = item - r.first[e];
+    switch (p.n) {
+#define LTMP2_CASE(NN)                                                                                        \
+  case NN:                                                                                                    \
+    zcol_body<T, NN, false>(p, r.gp0[e], r.np[e], local, (const cpx<T> *)p.tbuf, (cpx<T> *)p.mdiag, p.sx,     \
+                            smem_raw);                                                                        \
+    break;
+      LTMP2_FOR_EACH_N(LTMP2_CASE)
+#undef LTMP2_CASE
+      default:
+        break;
+    }
+  }
+}
+
+template <typename T> size_t Path<T>::plane_smem_for(const Plan &p, int ib) { return plane_smem<T>(p, 2, ib); }
+
+template <typename T> cudaError_t Path<T>::persist_attributes(size_t plane_smem_b, size_t col_smem_b) {
+  cudaError_t e = cudaFuncSetAttribute(k_planes_persist<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)plane_smem_b);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_zcol_persist<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem_b);
+}
+
+// resident blocks of the persistent kernel: every SM filled to its occupancy
+template <typename T> int Path<T>::persist_blocks(bool planes, size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  const cudaError_t e = planes
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_planes_persist<T>, kPersistThreads, smem)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zcol_persist<T>, kPersistThreads, smem);
+  if (e != cudaSuccess) return 0;
+  return sms * (per > 0 ? per : 1);
+}
+
+template <typename T>
+cudaError_t Path<T>::planes_persist(const Plan *d_plans, const BatchRound &r, int *counter, int blocks, size_t smem,
+                                    cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_planes_persist<T><<<blocks, kPersistThreads, smem, st>>>(d_plans, r, counter);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Path<T>::zcol_persist(const Plan *d_plans, const BatchRound &r, int *counter, int blocks, size_t smem,
+                                  cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_zcol_persist<T><<<blocks, kPersistThreads, smem, st>>>(d_plans, r, counter);
+  return cudaGetLastError();
 }
 
 template <typename T>

@@ -135,6 +135,17 @@ struct StageTimer {
 
 constexpr int kMaxLevels = 16;   // nested cutoffs of the internal extrapolation
 
+// One round of the batching form's persistent stages: the active systems, their item ranges
+// (plane items: N planes x columns; column items: pairs) and their slab.
+constexpr int kBatchMax = 16;
+constexpr int kPersistThreads = 128;
+struct BatchRound {
+  int nsys = 0;
+  int first[kBatchMax + 1] = {0};   // item prefix over the active systems
+  int sys[kBatchMax] = {0};         // index of each active system in the plan array
+  int gp0[kBatchMax] = {0}, np[kBatchMax] = {0}, ib[kBatchMax] = {0};
+};
+
 enum Stage {
   kStageGreen = 0, kStageWGemm = 1, kStageGatherZ = 2, kStagePlane = 3,
   kStageColumn = 4, kStageDirect = 5, kStageAccum = 6
@@ -164,6 +175,19 @@ template <typename T> struct Path {
   // one slab of primary G' [gp0, gp0 + np): everything up to the pair sums, then accumulate
   static cudaError_t slab(const Plan &p, int gp0, int np, double coef, cudaStream_t st,
                           StageTimer *tm);
+  // the slab in phases: up to w in real space (gather, transformed-state GEMM, z transform),
+  // and after the co-density FFTs (direct term, accumulation); the batching form runs the
+  // FFT stages of every system in between as shared persistent launches
+  static cudaError_t slab_pre(const Plan &p, int gp0, int np, cudaStream_t st, StageTimer *tm);
+  static cudaError_t slab_post(const Plan &p, int gp0, int np, double coef, cudaStream_t st, StageTimer *tm);
+  // persistent plane / column kernels over the items of several systems (device plan array)
+  static cudaError_t planes_persist(const Plan *d_plans, const struct BatchRound &r, int *counter, int blocks,
+                                    size_t smem, cudaStream_t st);
+  static cudaError_t zcol_persist(const Plan *d_plans, const struct BatchRound &r, int *counter, int blocks,
+                                  size_t smem, cudaStream_t st);
+  static size_t plane_smem_for(const Plan &p, int ib);
+  static cudaError_t persist_attributes(size_t plane_smem, size_t col_smem);
+  static int persist_blocks(bool planes, size_t smem);
   // plane kernel `kernel` with `ib` occupied planes per block fits the launch limits
   static bool plane_feasible(const Plan &p, int kernel, int ib);
   // the plane kernel alone (for the autotuner): kernel 0/1/2, ib (0 = default)

@@ -441,6 +441,7 @@ def _batch_sig(lib):
             ("ltmp2_batch_create", ctypes.c_int, [P(vp), ctypes.c_int, P(ctypes.c_int), P(dp), P(dp), P(vp)]),
             ("ltmp2_batch_run", ctypes.c_int, [vp, dp, dp]),
             ("ltmp2_batch_kernel_nodes", ctypes.c_int, [vp, P(ctypes.c_longlong)]),
+            ("ltmp2_batch_mode", ctypes.c_int, [vp, P(ctypes.c_int)]),
             ("ltmp2_batch_destroy", None, [vp]),
             ("ltmp2_energy_batch", ctypes.c_int, [P(vp), ctypes.c_int, P(ctypes.c_int), P(dp), P(dp), dp, dp])]:
         f = getattr(lib, name)
@@ -503,6 +504,12 @@ class Batch:
         _check(lib.ltmp2_batch_create(handles, n, nt, tps, wps, ctypes.byref(h)), "ltmp2_batch_create")
         self.handle = h
         self.n = n
+
+    def persistent(self) -> bool:
+        """True when the batch runs in rounds with the shared persistent FFT stages."""
+        v = ctypes.c_int()
+        _check(_batch_sig(load_library()).ltmp2_batch_mode(self.handle, ctypes.byref(v)), "ltmp2_batch_mode")
+        return bool(v.value)
 
     def run(self):
         ed, ex = np.zeros(self.n), np.zeros(self.n)
