@@ -62,7 +62,8 @@ extern "C" {
 /* LTMP2_FP32: complex64 FFTs; transformed-state GEMM on tcgen05 tensor cores in  */
 /*             3xTF32 split precision (hi*hi + hi*lo + lo*hi), each 16-wide k    */
 /*             block's tensor-memory partial added to FP32 register sums; with   */
-/*             real orbitals the Green's function P_r = R_v^T D R_v too (general */
+/*             real orbitals the Green's function P_r = R_v^T D R_v and the      */
+/*             direct-term products sum_G v M_ii conj(M_jj) per G' too (general  */
 /*             orbitals: CUDA cores, compensated FP32 sums); per-pair, per-tau   */
 /*             and final sums in FP64.                                           */
 #define LTMP2_FP64 0

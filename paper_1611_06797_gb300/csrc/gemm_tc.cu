@@ -102,6 +102,8 @@ void tc_release(TcResources &r) {
   r.maps = nullptr;
   delete static_cast<tc::TcMaps *>(r.gmaps);
   r.gmaps = nullptr;
+  delete static_cast<tc::TcMaps *>(r.dmaps);
+  r.dmaps = nullptr;
 }
 
 static int kpad_of(int k) { return ((k + tc::BK - 1) / tc::BK) * tc::BK; }
@@ -157,6 +159,58 @@ cudaError_t tc_green(const TcResources &r, const float *dv, void *pt, cudaStream
   dim3 grid((r.npw + tc::S_BN - 1) / tc::S_BN, r64 / 64);
   tc::k_tc_cgemm_stacked<<<grid, 160, tc::S_SMEM, st>>>(m.a1h, m.a1l, m.bh, m.bl, r.grows, r.npw,
                                                         r.kpad_v / tc::S_BK, static_cast<float2 *>(pt), r.npw, r.err);
+  return cudaGetLastError();
+}
+
+size_t tc_direct_bytes(int no, int naux, int slots) {
+  const size_t kp = (size_t)kpad_of(naux);
+  const size_t r64 = ((size_t)no + 63) / 64 * 64;
+  return sizeof(float) * kp * (2 * 2 * r64 * slots + 2 * 2 * (size_t)no * slots) +
+         sizeof(float2) * (size_t)slots * no * 2 * no + 1024;
+}
+
+cudaError_t tc_direct_init(TcResources &r, void *mem, int no, int naux, int slots) {
+  r.dno = no;
+  r.dnaux = naux;
+  r.dslots = slots;
+  r.dkpad = kpad_of(naux);
+  r.dr64 = (no + 63) / 64 * 64;
+  const size_t kp = (size_t)r.dkpad, arows = 2 * (size_t)r.dr64 * slots, brows = 2 * (size_t)no * slots;
+  float *f = static_cast<float *>(mem);
+  r.dah = f; f += arows * kp;
+  r.dal = f; f += arows * kp;
+  r.dbh = f; f += brows * kp;
+  r.dbl = f; f += brows * kp;
+  r.dc = reinterpret_cast<float2 *>(f);
+  tc::TcMaps *mp = new tc::TcMaps();
+  int bad = 0;
+  bad |= make_map(&mp->a1h, r.dah, (int)arows, r.dkpad, 128, tc::S_BK, CU_TENSOR_MAP_SWIZZLE_64B);
+  bad |= make_map(&mp->a1l, r.dal, (int)arows, r.dkpad, 128, tc::S_BK, CU_TENSOR_MAP_SWIZZLE_64B);
+  bad |= make_map(&mp->bh, r.dbh, (int)brows, r.dkpad, tc::S_BN, tc::S_BK, CU_TENSOR_MAP_SWIZZLE_64B);
+  bad |= make_map(&mp->bl, r.dbl, (int)brows, r.dkpad, tc::S_BN, tc::S_BK, CU_TENSOR_MAP_SWIZZLE_64B);
+  if (bad) {
+    delete mp;
+    return cudaErrorInvalidValue;
+  }
+  r.dmaps = mp;
+  r.direct = true;
+  return cudaSuccess;
+}
+
+cudaError_t tc_direct(const TcResources &r, const void *mdiag, const float *v, int np, double2 *yd, cudaStream_t st) {
+  if (np > r.dslots) return cudaErrorInvalidValue;
+  const tc::TcMaps &m = *static_cast<const tc::TcMaps *>(r.dmaps);
+  tc::k_pack_direct<<<dim3(r.dkpad / 32, r.dr64 / 32, np), dim3(32, 8), 0, st>>>(
+      static_cast<const float2 *>(mdiag), v, r.dnaux, r.dno, r.dkpad, r.dr64, r.dah, r.dal, r.dbh, r.dbl);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int no = r.dno;
+  dim3 grid((2 * no + tc::S_BN - 1) / tc::S_BN, r.dr64 / 64, np);
+  tc::k_tc_cgemm_stacked<<<grid, 160, tc::S_SMEM, st>>>(m.a1h, m.a1l, m.bh, m.bl, no, 2 * no, r.dkpad / tc::S_BK,
+                                                        r.dc, 2 * no, r.err, 2 * r.dr64, 2 * no,
+                                                        (long long)no * 2 * no);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  tc::k_direct_combine<<<dim3((no * no + 255) / 256, np), 256, 0, st>>>(r.dc, no, yd);
   return cudaGetLastError();
 }
 

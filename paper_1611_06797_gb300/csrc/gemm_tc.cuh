@@ -509,10 +509,64 @@ __global__ void k_pack_b_pairs(const float2 *__restrict__ c, int npw, int kpad, 
   }
 }
 
+// blockIdx.z runs over independent products of one launch: product z reads stacked A rows
+// from z * a_zrows and B rows from z * b_zrows (tensor-map coordinates) and writes C + z * c_zstride.
+// ---------------------------------------------------------------- direct-term operands
+// Per primary G' z of the slab, Y_ij = sum_G v(G) M_ii(G) conj(M_jj(G)) (real orbitals) is
+// the stacked product of A (complex rows i: M_ii over K = G) with the real rows B_n = v Re M_n
+// (n < n_o) and B_{n_o + n} = v Im M_n.  mdiag is [slot][G][i]: 32 x 32 tiles through shared
+// memory turn it K-major.  A rows of product z start at z * 2 r64 (r64: n_o rounded to 64).
+__global__ void k_pack_direct(const float2 *__restrict__ mdiag, const float *__restrict__ v, int naux, int no,
+                              int kpad, int r64, float *__restrict__ ah, float *__restrict__ al,
+                              float *__restrict__ bh, float *__restrict__ bl) {
+  __shared__ float2 tile[32][33];
+  const int z = blockIdx.z, g0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+  const float2 *mz = mdiag + (size_t)z * naux * no;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int g = g0 + k, i = i0 + threadIdx.x;
+    tile[k][threadIdx.x] = (g < naux && i < no) ? mz[(size_t)g * no + i] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int i = i0 + k, g = g0 + threadIdx.x;
+    if (i >= r64 || g >= kpad) continue;
+    const float2 m = tile[threadIdx.x][k];
+    const float vg = g < naux ? v[g] : 0.f;
+    const size_t ra = (size_t)z * 2 * r64 + 128 * (i / 64) + (i % 64);
+    float h = tf32_rn(m.x);
+    ah[ra * kpad + g] = h;
+    al[ra * kpad + g] = tf32_rn(m.x - h);
+    h = tf32_rn(m.y);
+    ah[(ra + 64) * kpad + g] = h;
+    al[(ra + 64) * kpad + g] = tf32_rn(m.y - h);
+    if (i < no) {
+      const size_t rb = (size_t)z * 2 * no + i;
+      const float re = vg * m.x, im = vg * m.y;
+      h = tf32_rn(re);
+      bh[rb * kpad + g] = h;
+      bl[rb * kpad + g] = tf32_rn(re - h);
+      h = tf32_rn(im);
+      bh[(rb + no) * kpad + g] = h;
+      bl[(rb + no) * kpad + g] = tf32_rn(im - h);
+    }
+  }
+}
+// Y_ij from the four blocks of product z: C [n_o][2 n_o] per z
+__global__ void k_direct_combine(const float2 *__restrict__ C, int no, double2 *__restrict__ yd) {
+  const int z = blockIdx.y;
+  const float2 *c = C + (size_t)z * no * 2 * no;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < no * no; e += gridDim.x * blockDim.x) {
+    const int i = e / no, j = e % no;
+    const float2 a = c[(size_t)i * 2 * no + j], b = c[(size_t)i * 2 * no + no + j];
+    yd[(size_t)z * no * no + e] = make_double2((double)a.x + (double)b.y, (double)a.y - (double)b.x);
+  }
+}
+
 __global__ void __launch_bounds__(160, 2)
     k_tc_cgemm_stacked(const __grid_constant__ CUtensorMap tah, const __grid_constant__ CUtensorMap tal,
                        const __grid_constant__ CUtensorMap tbh, const __grid_constant__ CUtensorMap tbl, int M,
-                       int N, int kblocks, float2 *__restrict__ C, int ldc, int *__restrict__ err) {
+                       int N, int kblocks, float2 *__restrict__ C, int ldc, int *__restrict__ err, int a_zrows = 0,
+                       int b_zrows = 0, long long c_zstride = 0) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t full_bar[S_STAGES], empty_bar[S_STAGES], accf_bar[2], acce_bar[2], done_bar;
   __shared__ uint32_t tmem_slot;
@@ -520,9 +574,11 @@ __global__ void __launch_bounds__(160, 2)
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int arow0 = blockIdx.y * 128;     // stacked operand rows
+  const int arow0 = blockIdx.z * a_zrows + blockIdx.y * 128;   // stacked operand rows
   const int m0 = blockIdx.y * 64;         // complex rows of W^T
   const int n0 = blockIdx.x * S_BN;
+  const int brow0 = blockIdx.z * b_zrows + n0;
+  C += blockIdx.z * c_zstride;
   const int ndrain = (kblocks + S_DRAIN - 1) / S_DRAIN;
 
   if (warp == 0) tmem_alloc(&tmem_slot, S_TMEM_COLS);
@@ -557,8 +613,8 @@ __global__ void __launch_bounds__(160, 2)
         const int x = kb * S_BK;
         tma_load_2d(st + 0 * S_TILE, &tah, &full_bar[s], x, arow0);
         tma_load_2d(st + 1 * S_TILE, &tal, &full_bar[s], x, arow0);
-        tma_load_2d(st + 2 * S_TILE, &tbh, &full_bar[s], x, n0);
-        tma_load_2d(st + 3 * S_TILE, &tbl, &full_bar[s], x, n0);
+        tma_load_2d(st + 2 * S_TILE, &tbh, &full_bar[s], x, brow0);
+        tma_load_2d(st + 3 * S_TILE, &tbl, &full_bar[s], x, brow0);
       };
       int issued = 0, consumed = 0;
       for (int s = 0; s < S_STAGES && s < kblocks; ++s) issue(s, s), issued = s + 1;

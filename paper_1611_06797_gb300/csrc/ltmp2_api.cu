@@ -256,6 +256,11 @@ template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys,
       if ((rc = dalloc_bytes(c, &gmem, tc_green_bytes(p.n_pw, p.n_v)))) return rc;
       e = tc_green_init(c->tc, gmem, (const float *)p.cv, p.n_v, c->stream);
       if (e != cudaSuccess) return cuda_status(e);
+      // and the direct-term products, one per primary G' of a slab
+      void *dmem = nullptr;
+      if ((rc = dalloc_bytes(c, &dmem, tc_direct_bytes(p.n_occ, p.n_aux, p.max_prim)))) return rc;
+      e = tc_direct_init(c->tc, dmem, p.n_occ, p.n_aux, p.max_prim);
+      if (e != cudaSuccess) return cuda_status(e);
     }
     p.tc = &c->tc;
   }
@@ -684,7 +689,8 @@ int capture_rounds(ltmp2_batch *b, ltmp2_ctx *const *ctxs, int n, const int *n_t
         b->launches[i] += Path<T>::green_launches(p);
       }
       if ((rc = cuda_status(Path<T>::slab_pre(p, gp0[i], np[i], b->streams[i], nullptr)))) break;
-      b->launches[i] += Path<T>::slab_launches(p) - 4 - (p.n_lev > 1 ? 1 : 0);   // all but plane, column, direct, accum
+      const int post = 2 + (p.tc && p.tc->direct ? 2 : 0);                       // direct term(s) + accumulation
+      b->launches[i] += Path<T>::slab_launches(p) - 2 - post;                    // all but plane, column and post
       if ((rc = cuda_status(cudaEventRecord(b->events[i], b->streams[i])))) break;
       if ((rc = cuda_status(cudaStreamWaitEvent(b->origin, b->events[i], 0)))) break;
     }
@@ -713,7 +719,7 @@ int capture_rounds(ltmp2_batch *b, ltmp2_ctx *const *ctxs, int n, const int *n_t
       const double coef = w[i][k] / (p.omega * p.omega * nfft * nfft);
       if ((rc = cuda_status(cudaStreamWaitEvent(b->streams[i], b->events[n], 0)))) break;
       if ((rc = cuda_status(Path<T>::slab_post(p, gp0[i], np[i], coef, b->streams[i], nullptr)))) break;
-      b->launches[i] += 2;
+      b->launches[i] += 2 + (p.tc && p.tc->direct ? 2 : 0);
       if (r == rounds[i] - 1) {
         if ((rc = cuda_status(Path<T>::finish(p, b->streams[i], nullptr)))) break;
         b->launches[i] += 1;

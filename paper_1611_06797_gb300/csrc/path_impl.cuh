@@ -335,7 +335,15 @@ cudaError_t Path<T>::slab_post(const Plan &p, int gp0, int np, double coef, cuda
     int th = no < 128 ? ((no + 31) / 32) * 32 : 128;
     // FP32: the shared-memory tiled kernel (1.6x faster on the 24^3 workload); FP64 is
     // bound by the FP64 pipe either way and the one-warp-per-(G', i) kernel is 12 % faster
-    if (lev) {
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (!lev && p.tc && p.tc->direct) {   // real orbitals: one tensor-core product per G'
+        if ((e = tc_direct(*p.tc, p.mdiag, p.v_aux32, np, p.yd, st)) != cudaSuccess) return e;
+        done = true;
+      }
+    }
+    if (done) {
+    } else if (lev) {
       k_direct<T, true><<<dim3(np, no), th, 0, st>>>(p, np, (const cpx<T> *)p.mdiag, p.yd);
     } else if (std::is_same<T, float>::value) {
       const int t = (no + 31) / 32;

@@ -21,6 +21,12 @@ struct TcResources {
   float *rvt = nullptr;                // [n_pw][n_v] R_v^T
   float *gah = nullptr, *gal = nullptr, *gbh = nullptr, *gbl = nullptr;
   void *gmaps = nullptr;               // host copy of the four tensor maps
+  // direct term on the tensor cores (real basis): one product per primary G' of a slab
+  bool direct = false;
+  int dno = 0, dr64 = 0, dkpad = 0, dnaux = 0, dslots = 0;
+  float *dah = nullptr, *dal = nullptr, *dbh = nullptr, *dbl = nullptr;
+  float2 *dc = nullptr;                // [slots][n_o][2 n_o]
+  void *dmaps = nullptr;
 };
 int tc_kpad(int npw);
 size_t tc_bytes(int rows_cap, int npw);
@@ -33,6 +39,11 @@ cudaError_t tc_pack_b(const TcResources &r, const void *pt, cudaStream_t st);
 size_t tc_green_bytes(int npw, int nv);
 cudaError_t tc_green_init(TcResources &r, void *mem, const float *cv, int nv, cudaStream_t st);
 cudaError_t tc_green(const TcResources &r, const float *dv, void *pt, cudaStream_t st);
+// direct term on the tensor cores: bytes and set-up for up to `slots` primary G' per slab,
+// and the pair sums Y [np][n_o][n_o] of one slab from its diagonal co-densities
+size_t tc_direct_bytes(int no, int naux, int slots);
+cudaError_t tc_direct_init(TcResources &r, void *mem, int no, int naux, int slots);
+cudaError_t tc_direct(const TcResources &r, const void *mdiag, const float *v, int np, double2 *yd, cudaStream_t st);
 cudaError_t tc_wgemm(const TcResources &r, const void *st_in, int rows, void *wt, cudaStream_t st);
 // one bounded wait on an mbarrier that never completes (failure-path self-test)
 cudaError_t tc_wait_selftest(int *err, unsigned long long limit_ns, cudaStream_t st);
@@ -160,7 +171,8 @@ template <typename T> struct Path {
   }
   static int slab_launches(const Plan &p) {
     if (p.route == 1) return 7 + (p.n_lev > 1 ? 1 : 0);   // no gather, CUDA-core product
-    return (p.tc ? 8 : 7) + (p.real_basis ? 1 : 0) + (p.n_lev > 1 ? 1 : 0);
+    return (p.tc ? 8 : 7) + (p.real_basis ? 1 : 0) + (p.n_lev > 1 ? 1 : 0) +
+           (p.tc && p.tc->direct && p.n_lev < 2 ? 2 : 0);   // direct term: pack, product, combine
   }
   // route 1 setup: the overlap densities of every primary G' into rt (uses st and pt as
   // scratch; pt holds the transposed virtual coordinates meanwhile)
