@@ -547,6 +547,7 @@ __device__ __forceinline__ void planes3_body(const Plan &p, int ib, int z, int c
   const int tid = threadIdx.x, nth = blockDim.x;
   const int no = p.n_occ;
   const int mlo = p.mxlo_aux, mhi = p.mxhi_aux;
+  const unsigned inv_nxa = ((1u << 20) + nxa - 1) / nxa;   // ceil(2^20 / nxa)
   for (int d = tid; d < nd; d += nth) {
     const int4 c = p.daux[d];
     ytab[d] = wrapn(c.y, N) * nxa + (c.x - mlo);
@@ -578,7 +579,9 @@ __device__ __forceinline__ void planes3_body(const Plan &p, int ib, int z, int c
     }
     __syncthreads();
     for (int t = tid; t < nb * nxa; t += nth) {
-      const int il = t / nxa, xa = t - il * nxa;
+      // t / nxa by an exact multiply-shift: t < 2^12 and nxa < 2^7 keep the rounding of the
+      // reciprocal below one part in nxa
+      const int il = (int)(((unsigned)t * inv_nxa) >> 20), xa = t - il * nxa;
       cpx<T> *src = wk + (size_t)il * N * nxa + xa;
       cpx<T> b[N];
 #pragma unroll
@@ -588,10 +591,11 @@ __device__ __forceinline__ void planes3_body(const Plan &p, int ib, int z, int c
       for (int k = 0; k < N; ++k) src[k * nxa] = b[k];
     }
     __syncthreads();
-    for (int e = tid; e < nb * nd; e += nth) {
-      const int il = e / nd, d = e - il * nd;
+    for (int il = 0; il < nb; ++il) {
       const size_t item = (size_t)col * no + (ilist ? ilist[i0 + il] : i0 + il);
-      tbuf[(item * N + z) * nd + d] = wk[(size_t)il * N * nxa + ytab[d]];
+      cpx<T> *dst = tbuf + (item * N + z) * nd;
+      const cpx<T> *src = wk + (size_t)il * N * nxa;
+      for (int d = tid; d < nd; d += nth) dst[d] = src[ytab[d]];
     }
     __syncthreads();
   }
@@ -622,6 +626,7 @@ __global__ void __launch_bounds__(32 * kPlaneWarps) k_planes4(Plan p, int ib, co
   const int z = blockIdx.x, col = blockIdx.y;
   const int no = p.n_occ;
   const int mlo = p.mxlo_aux, mhi = p.mxhi_aux;
+  const unsigned inv_nxa = ((1u << 20) + nxa - 1) / nxa;   // ceil(2^20 / nxa)
   for (int d = threadIdx.x; d < nd; d += blockDim.x) {
     const int4 c = p.daux[d];
     ytab[d] = wrapn(c.y, N) * nxa + (c.x - mlo);
@@ -653,7 +658,7 @@ __global__ void __launch_bounds__(32 * kPlaneWarps) k_planes4(Plan p, int ib, co
     }
     __syncwarp();
     for (int t = lane; t < nb * nxa; t += 32) {
-      const int il = t / nxa, xa = t - il * nxa;
+      const int il = (int)(((unsigned)t * inv_nxa) >> 20), xa = t - il * nxa;   // t / nxa, exact for t < 2^12
       cpx<T> *src = wk + (size_t)il * N * nxa + xa;
       cpx<T> b[N];
 #pragma unroll
@@ -663,10 +668,11 @@ __global__ void __launch_bounds__(32 * kPlaneWarps) k_planes4(Plan p, int ib, co
       for (int k = 0; k < N; ++k) src[k * nxa] = b[k];
     }
     __syncwarp();
-    for (int e = lane; e < nb * nd; e += 32) {
-      const int il = e / nd, d = e - il * nd;
+    for (int il = 0; il < nb; ++il) {
       const size_t item = (size_t)col * no + (ilist ? ilist[i0 + il] : i0 + il);
-      tbuf[(item * N + z) * nd + d] = wk[(size_t)il * N * nxa + ytab[d]];
+      cpx<T> *dst = tbuf + (item * N + z) * nd;
+      const cpx<T> *src = wk + (size_t)il * N * nxa;
+      for (int d = lane; d < nd; d += 32) dst[d] = src[ytab[d]];
     }
     __syncwarp();
   }
