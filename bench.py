@@ -201,23 +201,29 @@ def oracle_check(cb, e_pair):
 
 
 # ------------------------------------------------------------------ cost model
-def stage_costs(sizes, n_prim, real, n_tau, n_v, nxa):
-    """Algorithmic work per ltmp2_energy call, by stage (flops).
+def stage_costs(sizes, n_prim, real, reps, nxa, nv_tau, w_virtual, n_v, green_full=False):
+    """Algorithmic work of `reps` ltmp2_energy calls, by stage (flops).
 
     Real orbitals use the real cos/sin basis: the Green's function is a real product
     (2 flops per term) and the transformed states a complex x real one (4 flops per term);
-    general orbitals take complex products (8 flops per term).  The plane FFT pass counts
-    5 n log2 n flops per line of n points: per (column, occupied i) it transforms n rows
-    and nxa columns (the aux m1 range) on each of the n planes."""
+    general orbitals take complex products (8 flops per term).  Per Laplace point the
+    library keeps nv_tau[k] virtuals (ltmp2_tau_virtuals); where w_virtual[k] is set the
+    transformed states take two products over them (S^T R_v'^T, then times R_v') and no
+    Green's function is built, else the Green's function sums over nv_tau[k] virtuals (all
+    n_v on the tensor cores: green_full) and one product with it follows.  The plane FFT
+    pass counts 5 n log2 n flops per line of n points: per (column, occupied i) it
+    transforms n rows and nxa columns (the aux m1 range) on each of the n planes."""
     n_pw, n_occ, n = sizes["n_pw"], sizes["n_occ"], sizes["grid"]
     spp = 1 if real else 2
     ncols = n_prim * spp * n_occ
     fg, fw = (2.0, 4.0) if real else (8.0, 8.0)
     line = 5.0 * n * math.log2(n)
+    green = sum(0.0 if wv else fg * n_pw * n_pw * (n_v if green_full else nv) for nv, wv in zip(nv_tau, w_virtual))
+    wgemm = sum(fw * ncols * n_pw * (2.0 * nv if wv else n_pw) for nv, wv in zip(nv_tau, w_virtual))
     return {
-        "green_gemm": {"flops": n_tau * fg * n_pw * n_pw * n_v},
-        "w_gemm": {"flops": n_tau * fw * ncols * n_pw * n_pw},
-        "plane_fft": {"flops": n_tau * ncols * n_occ * n * (n + nxa) * line},
+        "green_gemm": {"flops": reps * green},
+        "w_gemm": {"flops": reps * wgemm},
+        "plane_fft": {"flops": reps * len(nv_tau) * ncols * n_occ * n * (n + nxa) * line},
     }
 
 
@@ -416,9 +422,12 @@ def main():
         stages = L.ltmp2_stage_times(ctx)
         sizes = L.ltmp2_sizes(ctx)
         n_prim = L.ltmp2_num_primary_gprime(ctx)
+        nv_tau, w_virtual = L.ltmp2_tau_virtuals(ctx, tau)
+        green_full = L.ltmp2_get_tuning(ctx)["green_tc"] == 1
         L.ltmp2_destroy(ctx)
         return {"ms_total": ms, "result": res, "launches": launches, "stages": stages, "sizes": sizes,
-                "n_prim": n_prim, "clocks": clk.summary()}
+                "n_prim": n_prim, "clocks": clk.summary(), "nv_tau": [int(x) for x in nv_tau],
+                "w_virtual": [int(x) for x in w_virtual], "green_full": green_full}
 
     def roofline(r, precision, simt):
         n_prim = r["n_prim"]
@@ -426,7 +435,8 @@ def main():
             from paper_1611_06797_gb300.shard import gprime_share
             b0, e0 = gprime_share(n_prim, rank, world)
             n_prim = e0 - b0
-        costs = stage_costs(r["sizes"], n_prim, True, n_tau * args.steps, s.n_orb - s.n_occ, aux_nxa(spec))
+        costs = stage_costs(r["sizes"], n_prim, True, args.steps, aux_nxa(spec), r["nv_tau"], r["w_virtual"],
+                            s.n_orb - s.n_occ, r["green_full"])
         return roofline_of(r["stages"], costs, precision, simt, peaks, peak_kind, alu)
 
     primary = L.FP64 if args.form == "fp64" else L.FP32
@@ -467,6 +477,10 @@ def main():
     }
     out["config"]["route"] = ("overlap densities stored (paper's steps (i)-(iii))" if route == L.ROUTE_OVERLAP
                               else "per-tau Green's function")
+    # virtuals kept per Laplace point (weight >= 2^-64 of the LUMO's) and the points where W
+    # goes through the virtual space instead of the Green's function
+    out["config"]["virtuals_per_tau"] = r["nv_tau"]
+    out["config"]["w_through_virtual_space"] = r["w_virtual"]
     if route_info:
         out["route"] = {("fp64" if k == L.FP64 else "fp32"): v for k, v in route_info.items()}
 
@@ -789,7 +803,9 @@ def form_cfg3(L, torch, local, steps, warmup, alu=None):
     sizes = L.ltmp2_sizes(ctx)
     n_prim = L.ltmp2_num_primary_gprime(ctx)
     tuning = L.ltmp2_get_tuning(ctx)
-    costs = stage_costs(sizes, n_prim, True, n_tau * steps, s.n_orb - s.n_occ, aux_nxa(spec))
+    nv_tau, w_virtual = L.ltmp2_tau_virtuals(ctx, tau)
+    costs = stage_costs(sizes, n_prim, True, steps, aux_nxa(spec), nv_tau, w_virtual, s.n_orb - s.n_occ,
+                        tuning["green_tc"] == 1)
     roof = roofline_of(st, costs, L.FP32, False, peaks, peak_kind, alu)
     # FP32 vs FP64 on the same inputs, over sampled G' ranges
     width = 6

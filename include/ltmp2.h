@@ -191,15 +191,22 @@ int ltmp2_autotune(ltmp2_ctx *ctx, int *slab, int *gemm_variant);
  * FP64 or with LTMP2_FLAG_SIMT_GEMM), [2] plane FFT kernel (0 full-plane passes,
  * 1 compacted passes, 2 product in registers with a compact intermediate, 3 the same with
  * every warp on its own occupied planes and no block barriers), [3] occupied planes per
- * plane-kernel block, for kernel 3 per warp step (0 = default).  The autotuner also chooses [2] and [3],
- * timing the plane kernel alone.                                                      */
+ * plane-kernel block, for kernel 3 per warp step (0 = default), [4] the precision form's
+ * Green's function on the tensor cores (1; 3xTF32, set up at first use) or on the CUDA
+ * cores with compensated sums (0, the default: the tensor-core build's plain FP32 sums
+ * over K = n_v left 4x the error in E_d on the 36^3 workload), [5] its direct-term
+ * contraction on the tensor cores (1, the default) or the CUDA cores (0); [4] and [5] are
+ * -1 where there is no choice (FP64, general orbitals, LTMP2_FLAG_SIMT_GEMM).
+ * The autotuner also chooses [2] and [3], timing the plane kernel alone.  values holds
+ * LTMP2_TUNING_VALUES entries.                                                          */
+#define LTMP2_TUNING_VALUES 6
 int ltmp2_get_tuning(const ltmp2_ctx *ctx, int *values);
 
 /* Apply settings by hand, same layout as ltmp2_get_tuning; a negative entry keeps the
  * current value.  Every choice gives the same energies up to rounding.  INVALID_ARG for
  * a slab outside 1..capacity, a GEMM layout without the tensor-core path (or other than
- * 5 for real orbitals), or a plane-kernel shape over 1024 threads or 200 KB of shared
- * memory.                                                                             */
+ * 5 for real orbitals), a plane-kernel shape over 1024 threads or 200 KB of shared
+ * memory, or a value of [4] / [5] other than -1 where there is no choice.             */
 int ltmp2_set_tuning(ltmp2_ctx *ctx, const int *values);
 
 typedef struct ltmp2_batch ltmp2_batch; /* opaque; a captured, instantiated graph */
@@ -352,6 +359,33 @@ int ltmp2_energy_uhf(ltmp2_ctx *alpha, ltmp2_ctx *beta, int n_tau, const double 
  * LTMP2_FLAG_REAL_ORBITALS (UNSUPPORTED otherwise); its transformed-state product runs on
  * the CUDA cores in both precisions.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.       */
 int ltmp2_set_route(ltmp2_ctx *ctx, int route);
+
+/* ---------------------------------------------------------------- virtuals per Laplace point
+ * The Laplace factor of Eq. SCHLT weights virtual a at point tau by e^{-(e_a-mu)tau}.
+ * Relative to the LUMO's weight, the virtuals with e^{-(e_a - e_LUMO) tau} < 2^-L add
+ * terms below the rounding of an FP64 product over the others (L = 64 by default; the
+ * product's own rounding is about 2^-53 of the sum of its terms' magnitudes), so they are
+ * left out of the Green's function and of step (iii)'s transformation at that tau.
+ * Energies ascend, so the kept virtuals are the first n_v(tau).  When the transformed
+ * states are then cheaper through the virtual space, W = R_v'^T D' (R_v' U S), than
+ * through the Green's function (4 n_pw n_v(tau) against 2 n_pw^2 multiply-adds per
+ * column; real orbitals, CUDA-core GEMMs: the FP64 path and LTMP2_FLAG_SIMT_GEMM), the
+ * library takes that route for that tau and builds no Green's function.
+ *   LTMP2_VIRTUALS_ALL:   every virtual at every tau, W through the Green's function.
+ *   LTMP2_VIRTUALS_AUTO:  the default described above.
+ *   LTMP2_VIRTUALS_SPACE: as AUTO, but W through the virtual space at every tau where
+ *                         the route exists (a test setting: slower at small tau).
+ * k-point contexts keep every virtual (UNSUPPORTED).                                   */
+#define LTMP2_VIRTUALS_ALL 0
+#define LTMP2_VIRTUALS_AUTO 1
+#define LTMP2_VIRTUALS_SPACE 2
+/* mode as above; 53 <= log2_cut <= 1100 is L.  Applies to later ltmp2_energy* calls.
+ * Errors: INVALID_ARG, UNSUPPORTED.                                                      */
+int ltmp2_set_virtual_cut(ltmp2_ctx *ctx, int mode, double log2_cut);
+/* For each of n_tau points tau[k] > 0: n_virt[k] = the virtuals kept at tau[k] and, when
+ * w_virtual is not NULL, w_virtual[k] = 1 if the transformed states go through the virtual
+ * space there (host arithmetic only; no device work).  Errors: INVALID_ARG.              */
+int ltmp2_tau_virtuals(ltmp2_ctx *ctx, int n_tau, const double *tau, int *n_virt, int *w_virtual);
 
 /* ---------------------------------------------------------------- internal cutoff extrapolation
  * Sec. III D, Eq. CutDecay: the MP2 energy converges with the auxiliary cutoff as

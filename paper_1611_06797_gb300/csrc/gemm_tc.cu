@@ -104,6 +104,7 @@ void tc_release(TcResources &r) {
   r.gmaps = nullptr;
   delete static_cast<tc::TcMaps *>(r.dmaps);
   r.dmaps = nullptr;
+  r.green = r.direct = false;   // their tensor maps are gone: set up again before any use
 }
 
 static int kpad_of(int k) { return ((k + tc::BK - 1) / tc::BK) * tc::BK; }
@@ -145,7 +146,7 @@ cudaError_t tc_green_init(TcResources &r, void *mem, const float *cv, int nv, cu
   if (e != cudaSuccess) return e;
   tc::k_pack_rows<<<dim3((r.kpad_v + 255) / 256, npw), 256, 0, st>>>(r.rvt, nv, r.kpad_v, r.gbh, r.gbl);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  r.green = true;
+  r.green = r.use_green = true;
   return cudaSuccess;
 }
 
@@ -193,7 +194,7 @@ cudaError_t tc_direct_init(TcResources &r, void *mem, int no, int naux, int slot
     return cudaErrorInvalidValue;
   }
   r.dmaps = mp;
-  r.direct = true;
+  r.direct = r.use_direct = true;
   return cudaSuccess;
 }
 
@@ -215,7 +216,7 @@ cudaError_t tc_direct(const TcResources &r, const void *mdiag, const float *v, i
 }
 
 cudaError_t tc_pack_b(const TcResources &r, const void *pt, cudaStream_t st) {
-  if (r.green) {   // the pair-interleaved output of tc_green
+  if (r.green_on()) {   // the pair-interleaved output of tc_green
     tc::k_pack_b_pairs<<<dim3((r.kpad + 255) / 256, r.npw), 256, 0, st>>>(static_cast<const float2 *>(pt), r.npw,
                                                                             r.kpad, r.bh, r.bl);
     return cudaGetLastError();

@@ -554,6 +554,7 @@ __device__ __forceinline__ void planes3_body(const Plan &p, int ib, int z, int c
   }
   plane_inverse<T, N>(p, z1 + ((size_t)col * N + z) * p.n_dorb, xp);   // ends with a barrier
   const cpx<T> *ut = (const cpx<T> *)p.ut;
+  const T *utr = (const T *)p.utr;
   const int jcol = col % no;
   const int ni = p.keep_count ? p.keep_count[jcol] : no;
   const int *ilist = p.keep_count ? p.keep_list + (size_t)jcol * no : nullptr;
@@ -564,11 +565,17 @@ __device__ __forceinline__ void planes3_body(const Plan &p, int ib, int z, int c
       const int iocc = ilist ? ilist[i0 + il] : i0 + il;
       cpx<T> a[N];
       // row y of phi_i from the transposed plane: element x at x N + y, so the threads of
-      // a warp (consecutive y) read consecutive addresses
-      const cpx<T> *ur = ut + ((size_t)iocc * N + z) * N * N + y;
+      // a warp (consecutive y) read consecutive addresses.  Real orbitals: phi_i is real,
+      // so conj(phi_i) w is two real products per point and half the bytes are read.
+      const size_t urow = ((size_t)iocc * N + z) * N * N + y;
       const cpx<T> *wr = xp + y * P;
+      if (utr) {
 #pragma unroll
-      for (int k = 0; k < N; ++k) a[k] = cmul(cconj(ur[k * N]), wr[k]);
+        for (int k = 0; k < N; ++k) a[k] = cscale(wr[k], utr[urow + k * N]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k) a[k] = cmul(cconj(ut[urow + k * N]), wr[k]);
+      }
       LineFFT<T, N, -1>::run(a);
       cpx<T> *row = wk + (size_t)t * nxa - mlo;   // row[m] for m in [mlo, mhi]
 #pragma unroll
@@ -635,6 +642,7 @@ __global__ void __launch_bounds__(32 * kPlaneWarps) k_planes4(Plan p, int ib, co
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   cpx<T> *wk = wk_all + (size_t)warp * ib * N * nxa;
   const cpx<T> *ut = (const cpx<T> *)p.ut;
+  const T *utr = (const T *)p.utr;
   const int jcol = col % no;
   const int ni = p.keep_count ? p.keep_count[jcol] : no;
   const int *ilist = p.keep_count ? p.keep_list + (size_t)jcol * no : nullptr;
@@ -644,10 +652,15 @@ __global__ void __launch_bounds__(32 * kPlaneWarps) k_planes4(Plan p, int ib, co
       const int il = t / N, y = t - il * N;
       const int iocc = ilist ? ilist[i0 + il] : i0 + il;
       cpx<T> a[N];
-      const cpx<T> *ur = ut + ((size_t)iocc * N + z) * N * N + y;
+      const size_t urow = ((size_t)iocc * N + z) * N * N + y;
       const cpx<T> *wr = xp + y * P;
+      if (utr) {
 #pragma unroll
-      for (int k = 0; k < N; ++k) a[k] = cmul(cconj(ur[k * N]), wr[k]);
+        for (int k = 0; k < N; ++k) a[k] = cscale(wr[k], utr[urow + k * N]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k) a[k] = cmul(cconj(ut[urow + k * N]), wr[k]);
+      }
       LineFFT<T, N, -1>::run(a);
       cpx<T> *row = wk + (size_t)t * nxa - mlo;
 #pragma unroll
@@ -682,7 +695,7 @@ __global__ void __launch_bounds__(32 * kPlaneWarps) k_planes4(Plan p, int ib, co
 // (and the plane-transposed copy outt[j][z][x][y] that the plane kernel reads row-wise)
 template <typename T, int N>
 __global__ void k_planes_store(Plan p, const cpx<T> *__restrict__ z1, cpx<T> *__restrict__ out,
-                               cpx<T> *__restrict__ outt) {
+                               cpx<T> *__restrict__ outt, T *__restrict__ outr) {
   constexpr int P = N + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T> *xp = reinterpret_cast<cpx<T> *>(smem_raw);
@@ -691,7 +704,9 @@ __global__ void k_planes_store(Plan p, const cpx<T> *__restrict__ z1, cpx<T> *__
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int y = e / N, x = e % N;
     out[((size_t)col * N + z) * N * N + e] = xp[y * P + x];
-    outt[((size_t)col * N + z) * N * N + e] = xp[x * P + y];   // e = x' N + y' with x' = y, y' = x
+    const cpx<T> v = xp[x * P + y];   // e = x' N + y' with x' = y, y' = x
+    outt[((size_t)col * N + z) * N * N + e] = v;
+    if (outr) outr[((size_t)col * N + z) * N * N + e] = v.x;
   }
 }
 

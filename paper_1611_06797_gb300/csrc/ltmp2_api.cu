@@ -108,6 +108,9 @@ struct ltmp2_ctx {
   unsigned long long fingerprint = 0;  // hash of the set-up inputs (ltmp2_fingerprint)
   unsigned long long mask_hash = 0;    // hash of the pair mask, 0 = every pair kept
   void *k_cocc = nullptr;              // k-point context: occupied coefficients (owned via allocs)
+  std::vector<double> eps_host;        // orbital energies, ascending (Gamma-point contexts)
+  int virt_mode = LTMP2_VIRTUALS_AUTO; // ltmp2_set_virtual_cut
+  double virt_log2 = 64.0;
   ~ltmp2_ctx() {
     tc_release(tc);
     for (void *q : allocs) cudaFree(q);
@@ -199,6 +202,28 @@ int upload_real_coeff(ltmp2_ctx *c, const ltmp2_system *sys, int row0, int rows,
   return cuda_status(cudaMemcpy(*dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
 }
 
+// R_v^T [n_pw][n_v] in the real basis, for the transformed states through the virtual space
+template <typename T>
+int upload_real_coeff_t(ltmp2_ctx *c, const ltmp2_system *sys, const std::vector<int> &order, void **dst) {
+  const int n_pw = sys->n_pw, no = sys->n_occ, nv = sys->n_orb - sys->n_occ;
+  const double r2 = 1.4142135623730950488016887242097;
+  std::vector<T> h((size_t)nv * n_pw);
+  for (int q = 0; q < n_pw; ++q) {
+    const int o = order[q];
+    const int *m = sys->miller + 3 * o;
+    const int kind = (m[0] == 0 && m[1] == 0 && m[2] == 0)
+                         ? 0
+                         : ((m[0] != 0 ? m[0] > 0 : (m[1] != 0 ? m[1] > 0 : m[2] > 0)) ? 1 : 2);
+    for (int a = 0; a < nv; ++a) {
+      const double *src = sys->coeff + ((size_t)(no + a) * n_pw + o) * 2;
+      h[(size_t)q * nv + a] = (T)(kind == 0 ? src[0] : (kind == 1 ? r2 * src[0] : r2 * src[1]));
+    }
+  }
+  int rc = dalloc_bytes(c, dst, h.size() * sizeof(T));
+  if (rc) return rc;
+  return cuda_status(cudaMemcpy(*dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
 template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys, const std::vector<int> &order) {
   Plan &p = c->p;
   cudaError_t e = Path<T>::init_device();
@@ -211,11 +236,15 @@ template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys,
   } else {
     if ((rc = upload_coeff<T>(c, sys->coeff, p.n_pw, p.n_occ, p.n_v, order, &p.cv))) return rc;
   }
+  // CUDA-core GEMMs in the real basis: R_v^T as well, for the large-tau transformed states
+  const bool simt = std::is_same<T, double>::value || (sys->flags & LTMP2_FLAG_SIMT_GEMM);
+  if (p.real_basis && simt && p.n_v > 0 && (rc = upload_real_coeff_t<T>(c, sys, order, &p.rvt))) return rc;
   void *cocc = nullptr;
   if ((rc = upload_coeff<T>(c, sys->coeff, p.n_pw, 0, p.n_occ, order, &cocc))) return rc;
   if ((rc = dalloc_bytes(c, &p.cgrid, cs * n3 * p.n_occ))) return rc;
   if ((rc = dalloc_bytes(c, &p.u, cs * n3 * p.n_occ))) return rc;
   if ((rc = dalloc_bytes(c, &p.ut, cs * n3 * p.n_occ))) return rc;
+  if (p.real_basis && (rc = dalloc_bytes(c, &p.utr, sizeof(T) * n3 * p.n_occ))) return rc;
   if ((rc = dalloc_bytes(c, &p.dscale, sizeof(T) * p.n_orb))) return rc;
   // real basis: one extra row, for the pair-interleaved Green's function of the tensor-core build
   if ((rc = dalloc_bytes(c, &p.pt, (p.real_basis ? sizeof(T) * (size_t)(p.n_pw + 1) : cs * (size_t)p.n_pw) * p.n_pw)))
@@ -251,12 +280,8 @@ template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys,
     e = tc_init(c->tc, tcmem, (int)max_cols, p.n_pw, 5, p.real_basis);
     if (e != cudaSuccess) return cuda_status(e);
     if (p.real_basis) {
-      // the Green's function P_r = R_v^T D R_v on the tensor cores as well
-      void *gmem = nullptr;
-      if ((rc = dalloc_bytes(c, &gmem, tc_green_bytes(p.n_pw, p.n_v)))) return rc;
-      e = tc_green_init(c->tc, gmem, (const float *)p.cv, p.n_v, c->stream);
-      if (e != cudaSuccess) return cuda_status(e);
-      // and the direct-term products, one per primary G' of a slab
+      // the direct-term products on the tensor cores, one per primary G' of a slab (the
+      // Green's function stays on the CUDA cores unless ltmp2_set_tuning asks otherwise)
       void *dmem = nullptr;
       if ((rc = dalloc_bytes(c, &dmem, tc_direct_bytes(p.n_occ, p.n_aux, p.max_prim)))) return rc;
       e = tc_direct_init(c->tc, dmem, p.n_occ, p.n_aux, p.max_prim);
@@ -333,10 +358,44 @@ int setup_precision_k(ltmp2_ctx *c, const ltmp2_kpoint_system *sys, const std::v
 
 // Launch (without waiting) everything one energy evaluation does on `stream`.  Usable
 // inside stream capture: no allocation, copy or synchronisation happens here.
+// Per tau (Eq. SCHLT's factor e^{-(e_a-mu)tau}): the virtuals whose weight is at least
+// 2^-L of the LUMO's.  Energies ascend, so they are the first nv; the rest contribute
+// below the rounding of an FP64 product over the kept ones and are left out.  W goes
+// through the virtual space when its two products (4 n_pw nv multiply-adds per column)
+// undercut the product with the Green's function (2 n_pw^2) by 10 %.
+constexpr double kVirtualRouteRatio = 0.9;
+int tau_virtuals(const ltmp2_ctx *c, double tau, bool *w_virtual) {
+  const Plan &p = c->p;
+  *w_virtual = false;
+  if (c->virt_mode == LTMP2_VIRTUALS_ALL || p.nk > 0 || p.n_v < 1 || c->eps_host.size() != (size_t)p.n_orb)
+    return p.n_v;
+  const double *ev = c->eps_host.data() + p.n_occ;
+  const double cut = ev[0] + c->virt_log2 * 0.69314718055994530942 / tau;
+  const int nv = std::max(1, (int)(std::upper_bound(ev, ev + p.n_v, cut) - ev));
+  if (p.rvt && p.route == 0 &&
+      (c->virt_mode == LTMP2_VIRTUALS_SPACE || 2.0 * nv <= kVirtualRouteRatio * p.n_pw))
+    *w_virtual = true;
+  return nv;
+}
+void set_tau_virtuals(const ltmp2_ctx *c, Plan &p, double tau) {
+  bool wv = false;
+  p.nv_tau = tau_virtuals(c, tau, &wv);
+  p.w_virtual = wv;
+}
+// back to every virtual and the Green's function when the tau loop ends
+struct TauVirtualsReset {
+  Plan &p;
+  ~TauVirtualsReset() {
+    p.nv_tau = 0;
+    p.w_virtual = false;
+  }
+};
+
 template <typename T>
 int enqueue_energy(ltmp2_ctx *c, cudaStream_t stream, int n_tau, const double *tau, const double *w, int gp_begin,
                    int gp_end, StageTimer *tm, long long *launches) {
   Plan &p = c->p;
+  TauVirtualsReset reset{p};
   cudaError_t e = Path<T>::zero_acc(p, stream);
   if (e != cudaSuccess) return cuda_status(e);
   *launches += Path<T>::frame_launches(p);  // zero + final reduction(s)
@@ -345,6 +404,7 @@ int enqueue_energy(ltmp2_ctx *c, cudaStream_t stream, int n_tau, const double *t
   // transforms are 1/N_k of the supercell's, and the energy is per unit cell (one more 1/N_k)
   const double nk = p.nk > 0 ? (double)p.nk : 1.0;
   for (int k = 0; k < n_tau; ++k) {
+    if (p.nk == 0) set_tau_virtuals(c, p, tau[k]);
     e = p.nk > 0 ? Path<T>::green_k(p, tau[k], stream, tm) : Path<T>::green(p, tau[k], stream, tm);
     if (e != cudaSuccess) return cuda_status(e);
     *launches += p.nk > 0 ? Path<T>::green_k_launches(p) : Path<T>::green_launches(p);
@@ -719,7 +779,7 @@ int capture_rounds(ltmp2_batch *b, ltmp2_ctx *const *ctxs, int n, const int *n_t
       const double coef = w[i][k] / (p.omega * p.omega * nfft * nfft);
       if ((rc = cuda_status(cudaStreamWaitEvent(b->streams[i], b->events[n], 0)))) break;
       if ((rc = cuda_status(Path<T>::slab_post(p, gp0[i], np[i], coef, b->streams[i], nullptr)))) break;
-      b->launches[i] += 2 + (p.tc && p.tc->direct ? 2 : 0);
+      b->launches[i] += 2 + (p.tc && p.tc->direct_on() ? 2 : 0);
       if (r == rounds[i] - 1) {
         if ((rc = cuda_status(Path<T>::finish(p, b->streams[i], nullptr)))) break;
         b->launches[i] += 1;
@@ -742,6 +802,7 @@ namespace {
 template <typename T>
 int enqueue_uhf(ltmp2_ctx *a, ltmp2_ctx *b, int n_tau, const double *tau, const double *w, long long *launches) {
   Plan &pa = a->p, &pb = b->p;
+  TauVirtualsReset ra{pa}, rb{pb};
   cudaStream_t st = a->stream;
   cudaError_t e;
   if ((e = Path<T>::zero_acc(pa, st)) != cudaSuccess || (e = Path<T>::zero_acc(pb, st)) != cudaSuccess)
@@ -751,6 +812,8 @@ int enqueue_uhf(ltmp2_ctx *a, ltmp2_ctx *b, int n_tau, const double *tau, const 
   *launches += 2;
   const double nfft = (double)pa.n * pa.n * pa.n;
   for (int k = 0; k < n_tau; ++k) {
+    set_tau_virtuals(a, pa, tau[k]);
+    set_tau_virtuals(b, pb, tau[k]);
     if ((e = Path<T>::green(pa, tau[k], st, nullptr)) != cudaSuccess) return cuda_status(e);
     if ((e = Path<T>::green(pb, tau[k], st, nullptr)) != cudaSuccess) return cuda_status(e);
     *launches += Path<T>::green_launches(pa) + Path<T>::green_launches(pb);
@@ -822,6 +885,7 @@ int ltmp2_setup(const ltmp2_system *sys, ltmp2_ctx **out) {
     return cuda_status(cudaMemcpy(*dptr, vec.data(), vec.size() * sizeof(X), cudaMemcpyHostToDevice));
   };
   std::vector<double> heps(sys->eps, sys->eps + sys->n_orb);
+  c->eps_host = heps;
   if (!rc) rc = up(&p.dorb, hp.dorb);
   if (!rc) rc = up(&p.dorb_off, hp.dorb_off);
   if (!rc) rc = up(&p.daux, hp.daux);
@@ -1126,6 +1190,8 @@ int ltmp2_get_tuning(const ltmp2_ctx *ctx, int *values) {
   values[1] = ctx->p.tc ? ctx->tc.variant : -1;
   values[2] = ctx->p.plane_kernel;
   values[3] = ctx->p.plane_ib;
+  values[4] = ctx->p.tc && ctx->tc.real ? (ctx->tc.green_on() ? 1 : 0) : -1;
+  values[5] = ctx->p.tc && ctx->tc.direct ? (ctx->tc.use_direct ? 1 : 0) : -1;
   return LTMP2_OK;
 }
 
@@ -1141,11 +1207,26 @@ int ltmp2_set_tuning(ltmp2_ctx *ctx, const int *values) {
   if (variant >= 0) {
     if (!p.tc || (variant != 4 && variant != 5) || (ctx->tc.real && variant != 5)) return LTMP2_ERR_INVALID_ARG;
   }
+  if (values[4] > 1 || values[5] > 1) return LTMP2_ERR_INVALID_ARG;
+  if ((values[4] >= 0 && !(p.tc && ctx->tc.real)) || (values[5] >= 0 && !(p.tc && ctx->tc.direct)))
+    return LTMP2_ERR_INVALID_ARG;
   const bool ok = p.precision == LTMP2_FP64 ? Path<double>::plane_feasible(p, pk, ib)
                                              : Path<float>::plane_feasible(p, pk, ib);
   if (!ok) return LTMP2_ERR_INVALID_ARG;
   DeviceGuard g(ctx->device);
-  return apply_tuning(ctx, slab, variant, pk, ib);
+  int rc = apply_tuning(ctx, slab, variant, pk, ib);
+  if (rc) return rc;
+  if (values[4] == 1 && !ctx->tc.green) {
+    // first use: R_v^T and its split, once (the Green's function on the tensor cores)
+    void *gmem = nullptr;
+    if ((rc = dalloc_bytes(ctx, &gmem, tc_green_bytes(p.n_pw, p.n_v)))) return rc;
+    cudaError_t e = tc_green_init(ctx->tc, gmem, (const float *)p.cv, p.n_v, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  if (values[4] >= 0) ctx->tc.use_green = values[4] == 1;
+  if (values[5] >= 0) ctx->tc.use_direct = values[5] == 1;
+  return LTMP2_OK;
 }
 
 int ltmp2_batch_create(ltmp2_ctx *const *ctxs, int n, const int *n_tau, const double *const *tau,
@@ -1365,6 +1446,29 @@ int ltmp2_set_route(ltmp2_ctx *ctx, int route) {
   if (e != cudaSuccess) return cuda_status(e);
   ctx->kernel_launches += 1 + 2 * ((p.n_prim + p.max_prim - 1) / p.max_prim);
   p.route = 1;
+  return LTMP2_OK;
+}
+
+// ---------------------------------------------------------------- virtuals per Laplace point
+int ltmp2_set_virtual_cut(ltmp2_ctx *ctx, int mode, double log2_cut) {
+  if (ctx && ctx->p.nk > 0) return LTMP2_ERR_UNSUPPORTED;   // no k-point form
+  if (!ctx || mode < LTMP2_VIRTUALS_ALL || mode > LTMP2_VIRTUALS_SPACE || !(log2_cut >= 53.0) ||
+      !(log2_cut <= 1100.0))
+    return LTMP2_ERR_INVALID_ARG;
+  ctx->virt_mode = mode;
+  ctx->virt_log2 = log2_cut;
+  return LTMP2_OK;
+}
+
+int ltmp2_tau_virtuals(ltmp2_ctx *ctx, int n_tau, const double *tau, int *n_virt, int *w_virtual) {
+  if (!ctx || !n_virt || !tau || n_tau < 1) return LTMP2_ERR_INVALID_ARG;
+  for (int k = 0; k < n_tau; ++k)
+    if (!(tau[k] > 0.0) || !std::isfinite(tau[k])) return LTMP2_ERR_INVALID_ARG;
+  for (int k = 0; k < n_tau; ++k) {
+    bool wv = false;
+    n_virt[k] = tau_virtuals(ctx, tau[k], &wv);
+    if (w_virtual) w_virtual[k] = wv ? 1 : 0;
+  }
   return LTMP2_OK;
 }
 

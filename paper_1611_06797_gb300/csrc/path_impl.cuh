@@ -149,7 +149,8 @@ cudaError_t Path<T>::setup_occupied(const Plan &p, const void *c_occ_dev, cudaSt
 #define LTMP2_CASE(NN)                                                                            \
   case NN:                                                                                        \
     k_w_zinv<T, NN><<<dim3((p.n_dorb + 127) / 128, p.n_occ), 128, 0, st>>>(p, p.n_pw, c, z1);     \
-    k_planes_store<T, NN><<<dim3(NN, p.n_occ), 128, smem, st>>>(p, z1, (cpx<T> *)p.u, (cpx<T> *)p.ut); \
+    k_planes_store<T, NN><<<dim3(NN, p.n_occ), 128, smem, st>>>(p, z1, (cpx<T> *)p.u, (cpx<T> *)p.ut,       \
+                                                                (T *)p.utr);                                  \
     break;
     LTMP2_FOR_EACH_N(LTMP2_CASE)
 #undef LTMP2_CASE
@@ -187,16 +188,17 @@ cudaError_t Path<T>::green(const Plan &p, double tau, cudaStream_t st, StageTime
   k_dscale<T><<<(p.n_orb + 255) / 256, 256, 0, st>>>(p.n_orb, p.n_occ, p.eps, p.mu, tau, (T *)p.dscale);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (p.route == 1) return cudaSuccess;   // no Green's function on the paper's route
+  // no Green's function on the paper's route, nor when W goes through the virtual space
+  if (p.route == 1 || p.w_virtual) return cudaSuccess;
   if constexpr (std::is_same<T, float>::value) {
-    if (p.tc && p.tc->green) {
+    if (p.tc && p.tc->green_on()) {
       // precision form, real basis: P_r on the tensor cores (3xTF32), then the split of P_r
       // into the transformed-state GEMM's operands
       if ((e = tc_green(*p.tc, (const float *)p.dscale + p.n_occ, p.pt, st)) != cudaSuccess) return e;
       return tc_pack_b(*p.tc, p.pt, st);
     }
   }
-  const int M = p.n_pw, N = p.n_pw, K = p.n_v;
+  const int M = p.n_pw, N = p.n_pw, K = p.nv_tau > 0 ? p.nv_tau : p.n_v;
   dim3 grid((N + 63) / 64, (M + 63) / 64);
   if (p.real_basis) {
     // P_r[q][p] = sum_a r_a(q) e^{-(e_a-mu)tau} r_a(p), r_a the real coordinates of a
@@ -237,10 +239,25 @@ cudaError_t Path<T>::slab_pre(const Plan &p, int gp0, int np, cudaStream_t st, S
       // W (real-basis coordinates, before the e^{(e_j-mu)tau} row factor) =
       // sum_a rho^T[(G', j)][a] e^{-(e_a-mu)tau} r_a: step (iii) with the stored overlap densities
       dim3 grid((p.n_pw + 63) / 64, (ncols + 63) / 64);
-      k_rgemm<T, cpx<T>, true><<<grid, 256, 0, st>>>(ncols, p.n_pw, p.n_v,
+      const int nv = p.nv_tau > 0 ? p.nv_tau : p.n_v;
+      k_rgemm<T, cpx<T>, true><<<grid, 256, 0, st>>>(ncols, p.n_pw, nv,
                                                       (const cpx<T> *)p.rt + (size_t)gp0 * no * p.n_v, p.n_v,
                                                       (const T *)p.cv, p.n_pw, (const T *)p.dscale + p.n_occ,
                                                       (cpx<T> *)p.wt, p.n_pw);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      done = true;
+    } else if (p.w_virtual) {
+      // X^T = (U S)^T R_v'^T [ncols][nv] in the z1 buffer (free until the z transform; it
+      // holds n n_dorb >= n_pw > nv values per column), then W^T = X^T D' R_v'
+      const int nv = p.nv_tau;
+      dim3 gx((nv + 63) / 64, (ncols + 63) / 64);
+      k_rgemm<T, cpx<T>, true><<<gx, 256, 0, st>>>(ncols, nv, p.n_pw, (const cpx<T> *)p.st, p.n_pw,
+                                                    (const T *)p.rvt, p.n_v, nullptr, (cpx<T> *)p.z1, nv);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      dim3 gw((p.n_pw + 63) / 64, (ncols + 63) / 64);
+      k_rgemm<T, cpx<T>, true><<<gw, 256, 0, st>>>(ncols, p.n_pw, nv, (const cpx<T> *)p.z1, nv, (const T *)p.cv,
+                                                    p.n_pw, (const T *)p.dscale + p.n_occ, (cpx<T> *)p.wt,
+                                                    p.n_pw);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       done = true;
     }
@@ -337,7 +354,7 @@ cudaError_t Path<T>::slab_post(const Plan &p, int gp0, int np, double coef, cuda
     // bound by the FP64 pipe either way and the one-warp-per-(G', i) kernel is 12 % faster
     bool done = false;
     if constexpr (std::is_same<T, float>::value) {
-      if (!lev && p.tc && p.tc->direct) {   // real orbitals: one tensor-core product per G'
+      if (!lev && p.tc && p.tc->direct_on()) {   // real orbitals: one tensor-core product per G'
         if ((e = tc_direct(*p.tc, p.mdiag, p.v_aux32, np, p.yd, st)) != cudaSuccess) return e;
         done = true;
       }

@@ -27,6 +27,11 @@ struct TcResources {
   float *dah = nullptr, *dal = nullptr, *dbh = nullptr, *dbl = nullptr;
   float2 *dc = nullptr;                // [slots][n_o][2 n_o]
   void *dmaps = nullptr;
+  // whether the set-up Green's function / direct-term products are used (ltmp2_set_tuning);
+  // otherwise the CUDA-core kernels run
+  bool use_green = false, use_direct = false;
+  bool green_on() const { return green && use_green; }
+  bool direct_on() const { return direct && use_direct; }
 };
 int tc_kpad(int npw);
 size_t tc_bytes(int rows_cap, int npw);
@@ -86,6 +91,8 @@ struct Plan {
   void *cgrid = nullptr;     // [n_occ][n^3] occupied coefficients scattered on the grid
   void *u = nullptr;         // [n_occ][n^3] occupied orbitals in real space, [z][y][x]
   void *ut = nullptr;        // [n_occ][n^3] the same, each z plane transposed: [z][x][y]
+  void *utr = nullptr;       // real orbitals at Gamma: the real part of ut, T [n_occ][z][x][y]
+                             // (the orbitals are real in real space), else null
   void *dscale = nullptr;    // [n_orb] T: virtual e^{-(e_a-mu)tau}, occupied e^{(e_j-mu)tau}
   void *pt = nullptr;        // [n_pw][n_pw] transposed Green's function P^T (real P if real_basis)
   void *st = nullptr;        // [max_cols][n_pw] gathered, scaled e^{-iG'r}|j> (S^T)
@@ -122,6 +129,15 @@ struct Plan {
   // W = sum_a |a> e^{-(e_a-mu)tau} rho_aj(G') e^{(e_j-mu)tau} (real orbitals only).
   int route = 0;
   void *rt = nullptr;        // route 1: [n_prim * n_occ][n_v] cpx<T>, row (G', j), column a
+  // Virtuals that carry weight at the current tau.  Energies ascend, so the virtuals with
+  // e^{-(e_a - e_LUMO) tau} >= 2^-L are the first nv_tau of them; the others are left out
+  // of the Green's function and of the transformed states (0 = all n_v).  With w_virtual
+  // the transformed states go through the virtual space, W^T = ((U S)^T R_v'^T D') R_v'
+  // (real basis, CUDA-core GEMMs; rvt = R_v^T [n_pw][n_v]), which costs 4 n_pw nv_tau
+  // multiply-adds per column against 2 n_pw^2 through P_r, and no Green's function is built.
+  int nv_tau = 0;
+  bool w_virtual = false;
+  void *rvt = nullptr;
   // k-point sampling (Sec. II C-D), nk > 0: n_occ counts composite occupied orbitals
   // k n_o + i over the mesh, n_orb / n_v are per k, cv [nk][n_v][n_pw], pt [nk][n_pw][n_pw],
   // dscale [nk][n_orb]; the auxiliary set A (daux, aux_m) is the ball that holds every
@@ -167,12 +183,12 @@ template <typename T> struct Path {
   // kernel launches per Green's function build and per slab (the tcgen05 path of the
   // precision form adds one operand-packing launch to each)
   static int green_launches(const Plan &p) {
-    return p.route == 1 ? 1 : (p.tc ? (p.tc->green ? 4 : 3) : 2);
+    return (p.route == 1 || p.w_virtual) ? 1 : (p.tc ? (p.tc->green_on() ? 4 : 3) : 2);
   }
   static int slab_launches(const Plan &p) {
     if (p.route == 1) return 7 + (p.n_lev > 1 ? 1 : 0);   // no gather, CUDA-core product
-    return (p.tc ? 8 : 7) + (p.real_basis ? 1 : 0) + (p.n_lev > 1 ? 1 : 0) +
-           (p.tc && p.tc->direct && p.n_lev < 2 ? 2 : 0);   // direct term: pack, product, combine
+    return (p.tc ? 8 : 7) + (p.real_basis ? 1 : 0) + (p.w_virtual ? 1 : 0) + (p.n_lev > 1 ? 1 : 0) +
+           (p.tc && p.tc->direct_on() && p.n_lev < 2 ? 2 : 0);   // direct term: pack, product, combine
   }
   // route 1 setup: the overlap densities of every primary G' into rt (uses st and pt as
   // scratch; pt holds the transposed virtual coordinates meanwhile)

@@ -19,8 +19,10 @@ constexpr int kThreads = 256;
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_fma_chains(int iters, T b, T c, T *out) {
   T x[kChains], br[kChains];
-  // both FMA operands in registers (x * 0 is not folded for floating point, so cr is a
-  // run-time value): operands from the constant bank would throttle the FP64 pipe
+  // FP64: both FMA operands in registers (x * 0 is not folded for floating point, so cr is
+  // a run-time value), since operands from the constant bank throttle the FP64 pipe.
+  // FP32: one register operand and two kernel parameters; three register operands per
+  // FFMA collide in the register banks and halve the measured rate.
   const T cr = c + (T)threadIdx.x * (T)0;
 #pragma unroll
   for (int k = 0; k < kChains; ++k) {
@@ -30,7 +32,12 @@ __global__ void __launch_bounds__(kThreads) k_fma_chains(int iters, T b, T c, T 
 #pragma unroll 4
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int k = 0; k < kChains; ++k) x[k] = fma(x[k], br[k], cr);
+    for (int k = 0; k < kChains; ++k) {
+      if constexpr (sizeof(T) == 8)
+        x[k] = fma(x[k], br[k], cr);
+      else
+        x[k] = fma(x[k], b, c);
+    }
   }
   T s = 0;
 #pragma unroll

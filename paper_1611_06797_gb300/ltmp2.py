@@ -458,22 +458,52 @@ def ltmp2_autotune(ctx: Context):
     return sl.value, var.value
 
 
+TUNING_VALUES = 6
+
+
 def ltmp2_get_tuning(ctx: Context) -> dict:
     lib = _batch_sig(load_library())
-    v = (ctypes.c_int * 4)()
+    v = (ctypes.c_int * TUNING_VALUES)()
     _check(lib.ltmp2_get_tuning(ctx.handle, v), "ltmp2_get_tuning")
-    return {"slab": v[0], "gemm_variant": v[1], "plane_kernel": v[2], "plane_ib": v[3]}
+    return {"slab": v[0], "gemm_variant": v[1], "plane_kernel": v[2], "plane_ib": v[3],
+            "green_tc": v[4], "direct_tc": v[5]}
 
 
 def ltmp2_set_tuning(ctx: Context, slab: int = -1, gemm_variant: int = -1, plane_kernel: int = -1,
-                     plane_ib: int = -1) -> None:
+                     plane_ib: int = -1, green_tc: int = -1, direct_tc: int = -1) -> None:
     """Apply tuning settings by hand (-1 keeps the current value)."""
     lib = load_library()
     f = lib.ltmp2_set_tuning
     f.restype = ctypes.c_int
     f.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
-    v = (ctypes.c_int * 4)(int(slab), int(gemm_variant), int(plane_kernel), int(plane_ib))
+    v = (ctypes.c_int * TUNING_VALUES)(int(slab), int(gemm_variant), int(plane_kernel), int(plane_ib),
+                                       int(green_tc), int(direct_tc))
     _check(f(ctx.handle, v), "ltmp2_set_tuning")
+
+
+VIRTUALS_ALL, VIRTUALS_AUTO, VIRTUALS_SPACE = 0, 1, 2
+
+
+def ltmp2_set_virtual_cut(ctx: Context, mode: int = VIRTUALS_AUTO, log2_cut: float = 64.0) -> None:
+    """Which virtuals each Laplace point keeps and when W goes through the virtual space."""
+    lib = load_library()
+    f = lib.ltmp2_set_virtual_cut
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
+    _check(f(ctx.handle, int(mode), float(log2_cut)), "ltmp2_set_virtual_cut")
+
+
+def ltmp2_tau_virtuals(ctx: Context, tau) -> Tuple[np.ndarray, np.ndarray]:
+    """(virtuals kept, 1 where W goes through the virtual space) for each Laplace point."""
+    lib = load_library()
+    f = lib.ltmp2_tau_virtuals
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    t = np.ascontiguousarray(tau, dtype=np.float64)
+    nv = np.zeros(t.size, dtype=np.int32)
+    wv = np.zeros(t.size, dtype=np.int32)
+    _check(f(ctx.handle, int(t.size), t.ctypes.data, nv.ctypes.data, wv.ctypes.data), "ltmp2_tau_virtuals")
+    return nv, wv
 
 
 def _batch_args(ctxs, taus, ws):

@@ -164,6 +164,8 @@ def test_entry_points_reject_null_contexts():
         "ltmp2_reset_stage_times": lambda f: f(null),
         "ltmp2_set_stream": lambda f: f(null, None),
         "ltmp2_num_primary_gprime": lambda f: f(null),
+        "ltmp2_set_virtual_cut": lambda f: f(null, 1, ctypes.c_double(64.0)),
+        "ltmp2_tau_virtuals": lambda f: f(null, 1, tau, i, i),
     }
     for name, call in calls.items():
         f = getattr(lib, name)

@@ -173,3 +173,33 @@ def test_plane_kernels_and_block_shapes_agree(name, real):
         with pytest.raises(L.Ltmp2Error):
             L.ltmp2_set_tuning(ctx, plane_kernel=0, plane_ib=2000)
         L.ltmp2_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", ["tiny2", "cfg1"])
+def test_precision_form_green_and_direct_choices(name):
+    """The precision form's Green's function (compensated CUDA-core sums by default, or
+    3xTF32 on the tensor cores, set up at first use) and its direct term (tensor cores by
+    default, or CUDA cores): every combination within 0.1 meV/atom of the FP64 path."""
+    s = solid(name)
+    tau, w = _quad(s, s.spec.n_tau)
+    d64, x64, p64, _ = _gpu(s, tau, w, L.FP64, real=True)
+    ctx = L.setup_from_solid(s, precision=L.FP32, real=True)
+    t = L.ltmp2_get_tuning(ctx)
+    assert t["green_tc"] == 0 and t["direct_tc"] == 1
+    bound = MEV_PER_ATOM * s.n_atoms
+    for g, d in ((1, 1), (1, 0), (0, 0), (0, 1)):
+        L.ltmp2_set_tuning(ctx, green_tc=g, direct_tc=d)
+        t = L.ltmp2_get_tuning(ctx)
+        assert (t["green_tc"], t["direct_tc"]) == (g, d)
+        ed, ex, ep = L.ltmp2_energy(ctx, tau, w)
+        assert abs(ed - d64) < bound and abs(ex - x64) < bound and np.abs(ep - p64).max() < bound, (g, d)
+    with pytest.raises(L.Ltmp2Error):
+        L.ltmp2_set_tuning(ctx, green_tc=2)
+    L.ltmp2_destroy(ctx)
+    # no choice in FP64
+    c64 = L.setup_from_solid(s, precision=L.FP64, real=True)
+    t = L.ltmp2_get_tuning(c64)
+    assert t["green_tc"] == -1 and t["direct_tc"] == -1
+    with pytest.raises(L.Ltmp2Error):
+        L.ltmp2_set_tuning(c64, green_tc=1)
+    L.ltmp2_destroy(c64)
