@@ -619,6 +619,7 @@ def form_batch(L, torch, local, steps, warmup, alu=None):
     ms = sum(times) / len(times)
     maxdiff = max(max(abs(ed[k] - ref[k][0]), abs(ex[k] - ref[k][1])) for k in range(len(solids)))
     nodes = batch.kernel_nodes()
+    persistent = batch.persistent()
     batch.destroy()
     # end to end: setup from host arrays + autotune (cached) + one batch evaluation + destroy
     t1 = time.perf_counter()
@@ -640,6 +641,8 @@ def form_batch(L, torch, local, steps, warmup, alu=None):
         "config": {"workload": "batching form: " + ", ".join(
             f"{s.spec.wells} wells {s.spec.grid}^3 {s.n_pw} PW {s.n_occ} occ {s.spec.n_tau} tau" for s in solids),
                    "systems": len(solids), "pair_tau_units": units, "form": "precision, one CUDA graph per step",
+                   "graph_mode": ("rounds with shared persistent FFT stages" if persistent
+                                  else "one graph branch per system (round counts too uneven for lockstep)"),
                    "l2": "flushed (256 MiB write) before every timed step",
                    "autotune": [{"slab": t[0], "gemm_variant": t[1]} for t in tune]},
         "sequential_ms_per_step": sum(seq) / len(seq), "speedup_vs_sequential": (sum(seq) / len(seq)) / ms,

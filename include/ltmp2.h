@@ -171,7 +171,8 @@ int ltmp2_set_slab_size(ltmp2_ctx *ctx, int n);
  * of Sec. III A (tau points, then slabs of the G' loop, Sec. III B) of every system are
  * captured into one CUDA graph, so a run is a single graph launch.  When every system
  * allows it (Gamma point, one precision, no cutoff levels, the Green's-function route,
- * at most 16 systems) the graph runs in rounds: round r takes the r-th (tau, slab) of every
+ * at most 16 systems) and the systems need similar numbers of (tau, slab) rounds (the
+ * most at most twice the fewest), the graph runs in rounds: round r takes the r-th (tau, slab) of every
  * system that still has one; each system's gather, transformed-state GEMM and z transform
  * run on its own branch, then ONE persistent plane-FFT launch and ONE persistent column
  * launch serve the co-density items of all those systems (resident thread blocks take

@@ -476,6 +476,10 @@ __global__ void __launch_bounds__(kPersistThreads) k_planes_persist(const Plan *
                                                                      int *__restrict__ counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
+  // the round's tables in shared memory: indexed by the item's system, which a kernel
+  // parameter array would have to copy to local memory for
+  __shared__ BatchRound sr;
+  if (threadIdx.x == 0) sr = r;
   const int total = r.first[r.nsys];
   for (;;) {
     __syncthreads();
@@ -484,14 +488,14 @@ __global__ void __launch_bounds__(kPersistThreads) k_planes_persist(const Plan *
     const int item = s_item;
     if (item >= total) return;
     int e = 0;
-    while (item >= r.first[e + 1]) ++e;
-    const Plan &p = plans[r.sys[e]];
-    const int local = item - r.first[e];
+    while (item >= sr.first[e + 1]) ++e;
+    const Plan &p = plans[sr.sys[e]];
+    const int local = item - sr.first[e];
     const int z = local % p.n, col = local / p.n;
     switch (p.n) {
 #define LTMP2_CASE(NN)                                                                                        \
   case NN:                                                                                                    \
-    planes3_body<T, NN>(p, r.ib[e], z, col, (const cpx<T> *)p.z1, (cpx<T> *)p.tbuf, smem_raw);               \
+    planes3_body<T, NN>(p, sr.ib[e], z, col, (const cpx<T> *)p.z1, (cpx<T> *)p.tbuf, smem_raw);              \
     break;
       LTMP2_FOR_EACH_N(LTMP2_CASE)
 #undef LTMP2_CASE
@@ -506,6 +510,10 @@ __global__ void __launch_bounds__(kPersistThreads) k_zcol_persist(const Plan *__
                                                                    int *__restrict__ counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
+  // the round's tables in shared memory: indexed by the item's system, which a kernel
+  // parameter array would have to copy to local memory for
+  __shared__ BatchRound sr;
+  if (threadIdx.x == 0) sr = r;
   const int total = r.first[r.nsys];
   for (;;) {
     __syncthreads();
@@ -514,13 +522,13 @@ __global__ void __launch_bounds__(kPersistThreads) k_zcol_persist(const Plan *__
     const int item = s_item;
     if (item >= total) return;
     int e = 0;
-    while (item >= r.first[e + 1]) ++e;
-    const Plan &p = plans[r.sys[e]];
-    const int local = item - r.first[e];
+    while (item >= sr.first[e + 1]) ++e;
+    const Plan &p = plans[sr.sys[e]];
+    const int local = item - sr.first[e];
     switch (p.n) {
 #define LTMP2_CASE(NN)                                                                                        \
   case NN:                                                                                                    \
-    zcol_body<T, NN, false>(p, r.gp0[e], r.np[e], local, (const cpx<T> *)p.tbuf, (cpx<T> *)p.mdiag, p.sx,     \
+    zcol_body<T, NN, false>(p, sr.gp0[e], sr.np[e], local, (const cpx<T> *)p.tbuf, (cpx<T> *)p.mdiag, p.sx,   \
                             smem_raw);                                                                        \
     break;
       LTMP2_FOR_EACH_N(LTMP2_CASE)

@@ -1,5 +1,6 @@
 """Batching form: several systems of uneven grids and orbital counts evaluated by one
-CUDA-graph launch (rounds of per-system GEMMs and shared persistent FFT stages) must give,
+CUDA-graph launch (rounds of per-system GEMMs and shared persistent FFT stages when the
+systems need similar numbers of rounds, else one graph branch per system) must give,
 system by system, the energies of ltmp2_energy (FP64 to 1e-12 relative; FP32 to the rounding
 of a different summation order in the column kernel) and, in FP64, the oracle's within
 1e-8 Ha: on the small systems and on the eight uneven systems of the batching workload."""
@@ -29,6 +30,11 @@ def test_batch_graph_matches_individual_calls(precision):
         slab, var = L.ltmp2_autotune(c)
         assert 1 <= slab <= L.ltmp2_num_primary_gprime(c)
         assert (var == -1) == (precision == L.FP64)
+    # one slab per Laplace point in every system: equal round counts, so the rounds run in
+    # lockstep with the shared persistent FFT stages
+    for c in ctxs:
+        n = L.ltmp2_num_primary_gprime(c)
+        assert L.ltmp2_set_slab_size(c, n) == n
     single = [L.ltmp2_energy(c, t, w)[:2] for c, (t, w) in zip(ctxs, quads)]
     b = L.ltmp2_batch_create(ctxs, [q[0] for q in quads], [q[1] for q in quads])
     assert b.kernel_nodes() > 0 and b.persistent()
@@ -52,7 +58,10 @@ def test_batching_workload_systems():
         ctxs = [L.setup_from_solid(s, precision=precision, real=True) for s in solids[:count]]
         single = [L.ltmp2_energy(c, t, w, pairs=False)[:2] for c, (t, w) in zip(ctxs, quads)]
         b = L.ltmp2_batch_create(ctxs, [q[0] for q in quads[:count]], [q[1] for q in quads[:count]])
-        assert b.persistent()
+        # rounds per system: n_tau x slabs; in lockstep only when the counts are balanced
+        rounds = [len(q[0]) * -(-L.ltmp2_num_primary_gprime(c) // L.ltmp2_get_tuning(c)["slab"])
+                  for c, q in zip(ctxs, quads)]
+        assert b.persistent() == (max(rounds) <= 2 * min(rounds)), rounds
         ed, ex = b.run()
         b.destroy()
         for k, (d, x) in enumerate(single):
