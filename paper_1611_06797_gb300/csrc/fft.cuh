@@ -127,6 +127,21 @@ template <typename T, int NT, int DIR> __host__ __device__ __forceinline__ cpx<T
   return DIR < 0 ? w : cconj(w);
 }
 
+// v * exp(DIR * 2 pi i e / NT).  e is a compile-time constant once the callers' loops are
+// unrolled; multiples of a quarter turn become exact swaps and sign changes (no multiply).
+template <typename T, int NT, int DIR> __host__ __device__ __forceinline__ cpx<T> twiddle_mul(cpx<T> v, int e) {
+  e %= NT;
+  if ((4 * e) % NT == 0) {
+    switch ((4 * e) / NT) {
+      case 0: return v;
+      case 1: return mul_i<DIR>(v);               // exp(DIR i pi / 2) = DIR i
+      case 2: return {-v.x, -v.y};
+      default: return mul_i<-DIR>(v);             // exp(DIR 3 i pi / 2) = -DIR i
+    }
+  }
+  return cmul(v, twiddle<T, NT, DIR>(e));
+}
+
 // ---------------------------------------------------------------- radix kernels
 template <typename T, int R, int DIR> struct Radix;
 
@@ -187,14 +202,67 @@ __host__ __device__ constexpr int pick_radix(int n) {
   return (n % 4 == 0) ? 4 : (n % 3 == 0) ? 3 : (n % 5 == 0) ? 5 : (n % 2 == 0) ? 2 : n;
 }
 
+// Coprime split N = N1 N2 for the prime-factor (Good-Thomas) algorithm, which needs no
+// twiddle factors between its two passes: N1 = the power-of-two part of N, or for odd N
+// the power-of-three part; 0 when N is a prime power (Cooley-Tukey then).
+__host__ __device__ constexpr int pfa_n1(int n) {
+  int p2 = 1, m = n;
+  while (m % 2 == 0) { m /= 2; p2 *= 2; }
+  if (p2 > 1 && p2 < n) return p2;
+  int p3 = 1;
+  m = n;
+  while (m % 3 == 0) { m /= 3; p3 *= 3; }
+  if (p3 > 1 && p3 < n) return p3;
+  return 0;
+}
+// x with a x = 1 (mod m), m >= 2 and gcd(a, m) = 1
+__host__ __device__ constexpr int inv_mod(int a, int m) {
+  int x = 1;
+  while ((a * x) % m != 1) ++x;
+  return x;
+}
+
 // ---------------------------------------------------------------- line FFT
-// In place on a[0..N-1].  N = R * M; n = M n1 + n2, k = k1 + R k2:
+// In place on a[0..N-1].  NT is the length of the full line (for the twiddle table).
+// Coprime N = N1 N2 (prime-factor algorithm): with n = (N2 n1 + N1 n2) mod N and
+// k = (N2 a k1 + N1 b k2) mod N, a = N2^-1 mod N1, b = N1^-1 mod N2, the kernel factors as
+// W_N^{nk} = W_N1^{n1 k1} W_N2^{n2 k2}: length-N1 transforms along n1, then length-N2
+// transforms along n2, with no twiddle factors between them.
+// Otherwise (Cooley-Tukey, decimation in time) N = R * M; n = M n1 + n2, k = k1 + R k2:
 //   X[k1 + R k2] = sum_n2 W_M^{n2 k2} W_N^{n2 k1} sum_n1 x[M n1 + n2] W_R^{n1 k1}
-// NT is the length of the full line (for the twiddle table).
 template <typename T, int N, int DIR, int NT = N> struct LineFFT {
+  static constexpr int P1 = pfa_n1(N);
   static constexpr int R = pick_radix(N);
   static constexpr int M = N / R;
   static __host__ __device__ __forceinline__ void run(cpx<T> (&a)[N]) {
+    if constexpr (P1 > 0) {
+      constexpr int N1 = P1, N2 = N / P1;
+      constexpr int A = inv_mod(N2 % N1, N1), B = inv_mod(N1 % N2, N2);
+      cpx<T> t[N];   // t[k1 N2 + n2]: after the length-N1 transforms
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) {
+        cpx<T> v[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) v[n1] = a[(N2 * n1 + N1 * n2) % N];
+        LineFFT<T, N1, DIR, NT>::run(v);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) t[k1 * N2 + n2] = v[k1];
+      }
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        cpx<T> u[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) u[n2] = t[k1 * N2 + n2];
+        LineFFT<T, N2, DIR, NT>::run(u);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) a[(N2 * A * k1 + N1 * B * k2) % N] = u[k2];
+      }
+      return;
+    } else {
+      run_ct(a);
+    }
+  }
+  static __host__ __device__ __forceinline__ void run_ct(cpx<T> (&a)[N]) {
     static_assert(R == 2 || R == 3 || R == 4 || R == 5, "line length must be 5-smooth");
 #pragma unroll
     for (int n2 = 0; n2 < M; ++n2) {
@@ -205,7 +273,7 @@ template <typename T, int N, int DIR, int NT = N> struct LineFFT {
 #pragma unroll
       for (int k1 = 0; k1 < R; ++k1) {
         // W_N^{n2 k1} = W_NT^{n2 k1 NT / N}
-        if (n2 * k1 != 0) v[k1] = cmul(v[k1], twiddle<T, NT, DIR>((n2 * k1 * (NT / N)) % NT));
+        if (n2 * k1 != 0) v[k1] = twiddle_mul<T, NT, DIR>(v[k1], (n2 * k1 * (NT / N)) % NT);
         a[M * k1 + n2] = v[k1];
       }
     }
