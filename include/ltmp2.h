@@ -361,6 +361,22 @@ int ltmp2_energy_uhf(ltmp2_ctx *alpha, ltmp2_ctx *beta, int n_tau, const double 
  * the CUDA cores in both precisions.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.       */
 int ltmp2_set_route(ltmp2_ctx *ctx, int route);
 
+/* ---------------------------------------------------------------- FP64 products on the tensor cores
+ * The FP64 path's transformed-state GEMM (step (iii) of Sec. III A in the real basis,
+ * W^T = (U S)^T P_r) runs on the tcgen05 tensor cores with FP64 accuracy, unless
+ * LTMP2_FLAG_SIMT_GEMM is set: every row of both operands is scaled by a power of two and
+ * cut into 8 slices of 7 bits (exact in TF32); the 36 slice products with s + t < 8 are
+ * accumulated per order s + t in FP32 tensor memory, where sums of at most 256 k stay
+ * below 2^24 and are therefore exact, and combined in FP64 registers.  The dropped orders
+ * are below 2^-56 of the row products' magnitude; the result differs from an FP64 GEMM by
+ * about its own rounding.
+ * ltmp2_dgemm_nt: C = A B^T with that scheme.  A [m][lda], B [n][ldb], C [m][ldc]: DEVICE
+ * pointers to row-major doubles (first k columns of A and B used), lda, ldb >= k,
+ * ldc >= n.  Allocates and frees its own slice buffers (about 32 (m + n) k bytes) and
+ * synchronises the device.  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT (a bounded wait
+ * inside the kernel ran out; C is then not written).                                     */
+int ltmp2_dgemm_nt(int m, int n, int k, const double *a, int lda, const double *b, int ldb, double *c, int ldc);
+
 /* ---------------------------------------------------------------- virtuals per Laplace point
  * The Laplace factor of Eq. SCHLT weights virtual a at point tau by e^{-(e_a-mu)tau}.
  * Relative to the LUMO's weight, the virtuals with e^{-(e_a - e_LUMO) tau} < 2^-L add

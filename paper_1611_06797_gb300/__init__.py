@@ -12,7 +12,7 @@ from .ltmp2 import (Context, Ltmp2Error, LIB_PATH, load_library, ltmp2_setup, lt
                     ltmp2_autotune, ltmp2_get_tuning, ltmp2_set_tuning, ltmp2_batch_create,
                     ltmp2_set_pair_mask, ltmp2_pair_descriptors, Mlp, ltmp2_learned_training_data,
                     ltmp2_screen_select, ltmp2_energy_screened, NUM_DESC, ltmp2_energy_batch, Batch, ltmp2_strerror, setup_from_solid,
-                    ltmp2_setup_kpoints, setup_from_kpoint_solid, ltmp2_set_virtual_cut, ltmp2_tau_virtuals,
+                    ltmp2_setup_kpoints, setup_from_kpoint_solid, ltmp2_set_virtual_cut, ltmp2_tau_virtuals, ltmp2_dgemm_nt,
                     VIRTUALS_ALL, VIRTUALS_AUTO, VIRTUALS_SPACE,
                     STAGE_NAMES, FP64, FP32, FLAG_REAL_ORBITALS, FLAG_SIMT_GEMM, HARTREE_TO_MEV)
 
@@ -25,6 +25,6 @@ __all__ = ["Context", "Ltmp2Error", "LIB_PATH", "load_library", "ltmp2_setup", "
            "ltmp2_autotune", "ltmp2_get_tuning", "ltmp2_set_tuning", "ltmp2_batch_create",
            "ltmp2_set_pair_mask", "ltmp2_pair_descriptors", "Mlp", "ltmp2_learned_training_data",
            "ltmp2_screen_select", "ltmp2_energy_screened", "NUM_DESC", "ltmp2_energy_batch", "Batch", "ltmp2_strerror", "setup_from_solid",
-           "ltmp2_setup_kpoints", "setup_from_kpoint_solid", "ltmp2_set_virtual_cut", "ltmp2_tau_virtuals",
+           "ltmp2_setup_kpoints", "setup_from_kpoint_solid", "ltmp2_set_virtual_cut", "ltmp2_tau_virtuals", "ltmp2_dgemm_nt",
            "VIRTUALS_ALL", "VIRTUALS_AUTO", "VIRTUALS_SPACE",
            "STAGE_NAMES", "FP64", "FP32", "FLAG_REAL_ORBITALS", "FLAG_SIMT_GEMM", "HARTREE_TO_MEV"]

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libltmp2.so")
 
-SOURCES = ["ltmp2_api.cu", "host_plan.cu", "kernels_f64.cu", "kernels_f32.cu", "gemm_tc.cu", "laplace.cpp",
+SOURCES = ["ltmp2_api.cu", "host_plan.cu", "kernels_f64.cu", "kernels_f32.cu", "gemm_tc.cu", "gemm_f64tc.cu", "laplace.cpp",
            "ltmp2_noalloc.cu", "mlp.cu", "probe.cu", "learned.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",

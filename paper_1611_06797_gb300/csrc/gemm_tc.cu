@@ -40,6 +40,11 @@ int make_map(CUtensorMap *m, float *base, int rows, int kpad, int box_rows, int 
 }
 }  // namespace
 
+// 64-byte-swizzled K-major fp32 operand map (the FP64 tensor-core GEMM's slices use it too)
+int tc_make_map_sw64(CUtensorMap *m, float *base, int rows, int kpad, int box_rows, int box_k) {
+  return make_map(m, base, rows, kpad, box_rows, box_k, CU_TENSOR_MAP_SWIZZLE_64B);
+}
+
 // Layouts the autotuner chooses from: 4 drained (separate Re / Im operands, N 64, two-stage
 // ring), 5 stacked Re / Im rows with a three-stage 64-byte-swizzle ring (the default and
 // the only layout for real orbitals).

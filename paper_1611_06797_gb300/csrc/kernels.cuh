@@ -26,6 +26,14 @@ __device__ __forceinline__ int wrapn(int m, int n) {
 }
 // frequency of storage slot k on an N-point axis (|m| < N/2 for every used slot)
 template <int N> __device__ __forceinline__ constexpr int freq_of(int k) { return k > N / 2 ? k - N : k; }
+// Elements between the occupied planes of the compact [ib][n][nxa] intermediate of the
+// plane kernels: the smallest Q >= n nxa with Q = nxa (mod 16).  Then element
+// (i, k, xa) sits at i Q + k nxa + xa = (i nxa + xa) + k nxa (mod 16), so the y-pass threads
+// (consecutive i nxa + xa) hit distinct banks even where a warp spans two planes.
+__host__ __device__ __forceinline__ int plane_stride(int n, int nxa) {
+  const int base = n * nxa;
+  return base + ((nxa - base) % 16 + 16) % 16;
+}
 
 // position in A of the G' carried by a slot of the current slab
 __device__ __forceinline__ int slot_aux(const Plan &p, int gp0, int np, int slot) {
@@ -542,8 +550,9 @@ __device__ __forceinline__ void planes3_body(const Plan &p, int ib, int z, int c
   cpx<T> *xp = reinterpret_cast<cpx<T> *>(smem_raw);
   const int nxa = p.mxhi_aux - p.mxlo_aux + 1;   // odd: the aux sphere is symmetric
   const int nd = p.n_daux;
-  cpx<T> *wk = xp + N * P;                    // [ib][N][nxa]
-  int *ytab = reinterpret_cast<int *>(wk + (size_t)ib * N * nxa);   // [nd] position of disk column d in a plane of wk
+  const int Q = plane_stride(N, nxa);
+  cpx<T> *wk = xp + N * P;                    // [ib] planes of [N][nxa], Q elements apart
+  int *ytab = reinterpret_cast<int *>(wk + (size_t)ib * Q);   // [nd] position of disk column d in a plane of wk
   const int tid = threadIdx.x, nth = blockDim.x;
   const int no = p.n_occ;
   const int mlo = p.mxlo_aux, mhi = p.mxhi_aux;
@@ -577,7 +586,7 @@ __device__ __forceinline__ void planes3_body(const Plan &p, int ib, int z, int c
         for (int k = 0; k < N; ++k) a[k] = cmul(cconj(ut[urow + k * N]), wr[k]);
       }
       LineFFT<T, N, -1>::run(a);
-      cpx<T> *row = wk + (size_t)t * nxa - mlo;   // row[m] for m in [mlo, mhi]
+      cpx<T> *row = wk + (size_t)il * Q + y * nxa - mlo;   // row[m] for m in [mlo, mhi]
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         const int m = freq_of<N>(k);
@@ -589,7 +598,7 @@ __device__ __forceinline__ void planes3_body(const Plan &p, int ib, int z, int c
       // t / nxa by an exact multiply-shift: t < 2^12 and nxa < 2^7 keep the rounding of the
       // reciprocal below one part in nxa
       const int il = (int)(((unsigned)t * inv_nxa) >> 20), xa = t - il * nxa;
-      cpx<T> *src = wk + (size_t)il * N * nxa + xa;
+      cpx<T> *src = wk + (size_t)il * Q + xa;
       cpx<T> b[N];
 #pragma unroll
       for (int k = 0; k < N; ++k) b[k] = src[k * nxa];
@@ -601,7 +610,7 @@ __device__ __forceinline__ void planes3_body(const Plan &p, int ib, int z, int c
     for (int il = 0; il < nb; ++il) {
       const size_t item = (size_t)col * no + (ilist ? ilist[i0 + il] : i0 + il);
       cpx<T> *dst = tbuf + (item * N + z) * nd;
-      const cpx<T> *src = wk + (size_t)il * N * nxa;
+      const cpx<T> *src = wk + (size_t)il * Q;
       for (int d = tid; d < nd; d += nth) dst[d] = src[ytab[d]];
     }
     __syncthreads();
@@ -628,8 +637,9 @@ __global__ void __launch_bounds__(32 * kPlaneWarps) k_planes4(Plan p, int ib, co
   cpx<T> *xp = reinterpret_cast<cpx<T> *>(smem_raw);
   const int nxa = p.mxhi_aux - p.mxlo_aux + 1;
   const int nd = p.n_daux;
-  cpx<T> *wk_all = xp + N * P;                                          // [warps][ib][N][nxa]
-  int *ytab = reinterpret_cast<int *>(wk_all + (size_t)kPlaneWarps * ib * N * nxa);   // [nd]
+  const int Q = plane_stride(N, nxa);
+  cpx<T> *wk_all = xp + N * P;                                          // [warps][ib] planes, Q apart
+  int *ytab = reinterpret_cast<int *>(wk_all + (size_t)kPlaneWarps * ib * Q);   // [nd]
   const int z = blockIdx.x, col = blockIdx.y;
   const int no = p.n_occ;
   const int mlo = p.mxlo_aux, mhi = p.mxhi_aux;
@@ -640,7 +650,7 @@ __global__ void __launch_bounds__(32 * kPlaneWarps) k_planes4(Plan p, int ib, co
   }
   plane_inverse<T, N>(p, z1 + ((size_t)col * N + z) * p.n_dorb, xp);   // ends with a barrier
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  cpx<T> *wk = wk_all + (size_t)warp * ib * N * nxa;
+  cpx<T> *wk = wk_all + (size_t)warp * ib * Q;
   const cpx<T> *ut = (const cpx<T> *)p.ut;
   const T *utr = (const T *)p.utr;
   const int jcol = col % no;
@@ -662,7 +672,7 @@ __global__ void __launch_bounds__(32 * kPlaneWarps) k_planes4(Plan p, int ib, co
         for (int k = 0; k < N; ++k) a[k] = cmul(cconj(ut[urow + k * N]), wr[k]);
       }
       LineFFT<T, N, -1>::run(a);
-      cpx<T> *row = wk + (size_t)t * nxa - mlo;
+      cpx<T> *row = wk + (size_t)il * Q + y * nxa - mlo;
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         const int m = freq_of<N>(k);
@@ -672,7 +682,7 @@ __global__ void __launch_bounds__(32 * kPlaneWarps) k_planes4(Plan p, int ib, co
     __syncwarp();
     for (int t = lane; t < nb * nxa; t += 32) {
       const int il = (int)(((unsigned)t * inv_nxa) >> 20), xa = t - il * nxa;   // t / nxa, exact for t < 2^12
-      cpx<T> *src = wk + (size_t)il * N * nxa + xa;
+      cpx<T> *src = wk + (size_t)il * Q + xa;
       cpx<T> b[N];
 #pragma unroll
       for (int k = 0; k < N; ++k) b[k] = src[k * nxa];
@@ -684,7 +694,7 @@ __global__ void __launch_bounds__(32 * kPlaneWarps) k_planes4(Plan p, int ib, co
     for (int il = 0; il < nb; ++il) {
       const size_t item = (size_t)col * no + (ilist ? ilist[i0 + il] : i0 + il);
       cpx<T> *dst = tbuf + (item * N + z) * nd;
-      const cpx<T> *src = wk + (size_t)il * N * nxa;
+      const cpx<T> *src = wk + (size_t)il * Q;
       for (int d = lane; d < nd; d += 32) dst[d] = src[ytab[d]];
     }
     __syncwarp();

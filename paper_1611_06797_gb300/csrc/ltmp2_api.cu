@@ -95,6 +95,7 @@ struct ltmp2_ctx {
   int *d_keep_list = nullptr, *d_keep_count = nullptr;
   TcResources tc;
   void *tc_mem = nullptr;   // operand buffers of the tensor-core GEMM (owned via allocs)
+  OzResources oz;           // FP64 path: slices of the tensor-core FP64 GEMM (memory owned via allocs)
   double ecut_aux = 0.0;               // E_aux of A (Hartree)
   std::vector<double> aux_g2;          // |G|^2 of A in internal order
   // internal cutoff extrapolation: level cutoffs, |A_n| (G != 0), device buffers
@@ -113,6 +114,7 @@ struct ltmp2_ctx {
   double virt_log2 = 64.0;
   ~ltmp2_ctx() {
     tc_release(tc);
+    oz_release(oz);
     for (void *q : allocs) cudaFree(q);
   }
 };
@@ -289,6 +291,14 @@ template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys,
     }
     p.tc = &c->tc;
   }
+  if (std::is_same<T, double>::value && p.real_basis && !(sys->flags & LTMP2_FLAG_SIMT_GEMM)) {
+    // the transformed-state GEMM with FP64 accuracy on the tensor cores (exact integer slices)
+    void *omem = nullptr;
+    if ((rc = dalloc_bytes(c, &omem, oz_bytes((int)max_cols, p.n_pw)))) return rc;
+    e = oz_init(c->oz, omem, (int)max_cols, p.n_pw);
+    if (e != cudaSuccess) return cuda_status(e);
+    p.oz = &c->oz;
+  }
   e = Path<T>::setup_occupied(p, cocc, c->stream);
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaStreamSynchronize(c->stream);
@@ -423,6 +433,10 @@ int enqueue_energy(ltmp2_ctx *c, cudaStream_t stream, int n_tau, const double *t
 // After the work is complete: a bounded wait inside the tensor-core GEMM that ran out is
 // reported (and the flag cleared).
 int check_tc_flag(ltmp2_ctx *c) {
+  if (c->p.oz) {
+    const int rc = oz_check(c->oz);
+    if (rc) return rc;
+  }
   if (!c->p.tc) return LTMP2_OK;
   int flag = 0;
   cudaError_t e = cudaMemcpy(&flag, c->p.tc->err, sizeof(int), cudaMemcpyDeviceToHost);

@@ -48,8 +48,9 @@ template <typename T> static size_t plane_smem(const Plan &p, int kernel, int ib
   const size_t plane = (size_t)n * (n + 1) * sizeof(cpx<T>);
   const int nxa = p.mxhi_aux - p.mxlo_aux + 1;
   if (kernel == 0) return plane * (1 + ib);
-  if (kernel == 2) return plane + (size_t)ib * n * nxa * sizeof(cpx<T>) + sizeof(int) * p.n_daux;
-  if (kernel == 3) return plane + (size_t)kPlaneWarps * ib * n * nxa * sizeof(cpx<T>) + sizeof(int) * p.n_daux;
+  const size_t q = (size_t)plane_stride(n, nxa);
+  if (kernel == 2) return plane + (size_t)ib * q * sizeof(cpx<T>) + sizeof(int) * p.n_daux;
+  if (kernel == 3) return plane + (size_t)kPlaneWarps * ib * q * sizeof(cpx<T>) + sizeof(int) * p.n_daux;
   return plane * (1 + ib) + (size_t)ib * p.n_daux * sizeof(cpx<T>) + 3 * sizeof(int) * nxa;
 }
 
@@ -214,6 +215,8 @@ cudaError_t Path<T>::green(const Plan &p, double tau, cudaStream_t st, StageTime
   if (e != cudaSuccess) return e;
   if constexpr (std::is_same<T, float>::value) {
     if (p.tc) return tc_pack_b(*p.tc, p.pt, st);  // split P into TF32 hi/lo operands
+  } else {
+    if (p.oz) return oz_split_b(*p.oz, (const double *)p.pt, st);   // exact integer slices of P_r
   }
   return cudaSuccess;
 }
@@ -264,6 +267,11 @@ cudaError_t Path<T>::slab_pre(const Plan &p, int gp0, int np, cudaStream_t st, S
     if constexpr (std::is_same<T, float>::value) {
       if (p.tc && !done) {
         if ((e = tc_wgemm(*p.tc, p.st, ncols, p.wt, st)) != cudaSuccess) return e;
+        done = true;
+      }
+    } else {
+      if (p.oz && !done) {   // FP64-accurate products on the tensor cores
+        if ((e = oz_wgemm(*p.oz, p.st, ncols, p.wt, st)) != cudaSuccess) return e;
         done = true;
       }
     }

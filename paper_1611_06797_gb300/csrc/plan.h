@@ -7,6 +7,7 @@
 namespace ltmp2 {
 
 // Operands, tensor maps and error flag of the tcgen05 3xTF32 GEMM (precision form).
+struct OzResources;   // FP64 tensor-core GEMM resources (below)
 struct TcResources {
   int rows_cap = 0, npw = 0, kpad = 0;
   int variant = 5;         // 4 drained N=64, 5 stacked Re/Im rows (default; the only one for real orbitals)
@@ -106,6 +107,7 @@ struct Plan {
   double *esum = nullptr;    // [4]: E_d, E_x, imag parts
   int max_prim = 0;          // primary G' per slab (capacity)
   TcResources *tc = nullptr; // precision form: tcgen05 GEMM resources (host pointer), or null
+  OzResources *oz = nullptr; // FP64 path: tensor-core FP64 GEMM resources (host pointer), or null
   int plane_kernel = 2;      // 0: k_planes, 1: k_planes2, 2: k_planes3 (the autotuner may change it)
   // screened exchange pairs (learned form); all null = every pair contracted
   const unsigned char *pair_keep = nullptr;  // [n_occ][n_occ] 1 = contract, symmetric, diagonal kept
@@ -153,6 +155,25 @@ struct Plan {
   int slots_per_prim() const { return (real_orb && nk == 0) ? 1 : 2; }
 };
 
+// FP64 products on the tensor cores by exact integer slices (gemm_f64tc.cuh): the FP64
+// path's transformed-state GEMM in the real basis, W^T = (U S)^T P_r.
+struct OzResources {
+  int rows_cap = 0, npw = 0, kpad = 0, arows = 0;  // complex rows, K = n_pw, padded K, stacked rows
+  float *a = nullptr, *b = nullptr;                // slices [8][arows][kpad], [8][npw][kpad]
+  double *sa = nullptr, *sb = nullptr;             // row scales (powers of two)
+  int *err = nullptr;                              // device flag: a bounded wait ran out
+  void *maps = nullptr;                            // host copy of the two tensor maps
+};
+size_t oz_bytes(int rows_cap, int npw);
+cudaError_t oz_init(OzResources &r, void *mem, int rows_cap, int npw);
+void oz_release(OzResources &r);
+// slices of P_r (real symmetric [npw][npw]) as the B operand, once per tau
+cudaError_t oz_split_b(const OzResources &r, const double *pr, cudaStream_t st);
+// W^T (complex [rows][npw]) = S^T (complex [rows][npw]) P_r
+cudaError_t oz_wgemm(const OzResources &r, const void *st_in, int rows, void *wt, cudaStream_t st);
+// the bounded-wait flag: LTMP2_OK, or LTMP2_ERR_TIMEOUT (flag cleared), or LTMP2_ERR_CUDA
+int oz_check(const OzResources &r);
+
 // Per-stage profiler hooks (host).  begin/end bracket one kernel launch.
 struct StageTimer {
   virtual void begin(int stage) = 0;
@@ -183,11 +204,12 @@ template <typename T> struct Path {
   // kernel launches per Green's function build and per slab (the tcgen05 path of the
   // precision form adds one operand-packing launch to each)
   static int green_launches(const Plan &p) {
-    return (p.route == 1 || p.w_virtual) ? 1 : (p.tc ? (p.tc->green_on() ? 4 : 3) : 2);
+    return (p.route == 1 || p.w_virtual) ? 1 : (p.tc ? (p.tc->green_on() ? 4 : 3) : (p.oz ? 3 : 2));
   }
   static int slab_launches(const Plan &p) {
     if (p.route == 1) return 7 + (p.n_lev > 1 ? 1 : 0);   // no gather, CUDA-core product
-    return (p.tc ? 8 : 7) + (p.real_basis ? 1 : 0) + (p.w_virtual ? 1 : 0) + (p.n_lev > 1 ? 1 : 0) +
+    return (p.tc ? 8 : 7) + (p.real_basis ? 1 : 0) + (p.w_virtual ? 1 : 0) + (p.oz && !p.w_virtual ? 1 : 0) +
+           (p.n_lev > 1 ? 1 : 0) +
            (p.tc && p.tc->direct_on() && p.n_lev < 2 ? 2 : 0);   // direct term: pack, product, combine
   }
   // route 1 setup: the overlap densities of every primary G' into rt (uses st and pt as

@@ -481,6 +481,27 @@ def ltmp2_set_tuning(ctx: Context, slab: int = -1, gemm_variant: int = -1, plane
     _check(f(ctx.handle, v), "ltmp2_set_tuning")
 
 
+def ltmp2_dgemm_nt(a, b, c=None):
+    """C = A B^T in FP64 accuracy on the tensor cores (exact integer slices).  a [m, k],
+    b [n, k]: float64 CUDA tensors, row-major with unit column stride; returns c [m, n]."""
+    import torch
+    if a.dtype != torch.float64 or b.dtype != torch.float64 or not a.is_cuda or not b.is_cuda:
+        raise ValueError("a and b must be float64 CUDA tensors")
+    if a.dim() != 2 or b.dim() != 2 or a.shape[1] != b.shape[1] or a.stride(1) != 1 or b.stride(1) != 1:
+        raise ValueError("a [m, k] and b [n, k] with unit column stride")
+    m, k = a.shape
+    n = b.shape[0]
+    if c is None:
+        c = torch.empty((m, n), dtype=torch.float64, device=a.device)
+    f = load_library().ltmp2_dgemm_nt
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                  ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+    _check(f(m, n, k, a.data_ptr(), a.stride(0), b.data_ptr(), b.stride(0), c.data_ptr(), c.stride(0)),
+           "ltmp2_dgemm_nt")
+    return c
+
+
 VIRTUALS_ALL, VIRTUALS_AUTO, VIRTUALS_SPACE = 0, 1, 2
 
 
