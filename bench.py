@@ -247,9 +247,10 @@ def roofline_of(st, costs, precision, simt, peaks, peak_kind, alu):
                 "traffic": traffic_for(dom, precision)}
     per_launch_ms = st[dom]["ms"] / st[dom]["launches"]
     work = costs[dom]["flops"] / st[dom]["launches"]
-    if dom == "w_gemm" and precision != 0 and not simt:
-        # 3xTF32: three tensor products per real product
-        work *= 3.0
+    if not simt and (dom == "w_gemm" or (dom == "green_gemm" and precision == 0)):
+        # tensor products per real product: 3xTF32 in the precision form; in the FP64 path the
+        # 36 slice products (orders s + t < 8 of 8 x 7-bit slices per operand)
+        work *= 3.0 if precision != 0 else 36.0
         peak = peaks["bf16_tflops"] * TF32_OVER_BF16
         bound, pk = "tensor", f"tf32 = {peak_kind} bf16 {peaks['bf16_tflops']} x nominal 1.1/2.25"
     elif precision == 0:
@@ -462,6 +463,9 @@ def main():
         "config": {"workload": _workload_desc(spec), "n_pw": sizes["n_pw"], "n_aux": sizes["n_aux"],
                    "n_occ": sizes["n_occ"], "grid": sizes["grid"], "n_tau": n_tau, "pairs": pairs,
                    "form": "plain FP64" if primary == L.FP64 else "precision (FP32 FFT, split GEMM)",
+                   "gemm": ("FP64-accurate products on tcgen05: rows scaled by powers of two, 8 exact 7-bit "
+                            "slices per operand, 36 slice products accumulated exactly in FP32 tensor memory, "
+                            "FP64 sums" if primary == L.FP64 else "tcgen05 3xTF32, FP32 sums per k block"),
                    "time_reversal": True, "l2": "flushed (256 MiB write) before every timed step",
                    "laplace_max_rel_err": qerr,
                    "parallelism": (f"outer G' loop split over {world} GPUs (contiguous balanced shares), one "

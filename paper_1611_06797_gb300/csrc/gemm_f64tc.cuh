@@ -65,38 +65,41 @@ __device__ __forceinline__ double block_max(double v, double *red) {
   return m;
 }
 
-// Slices of the rows of a real matrix X [nrows][ld] (first k columns): plane s row r at
-// planes[(s * prows + r) * kpad], zero past k; scale[r] = 2^e_r.  One block per row.
-__global__ void k_oz_split_rows(const double *__restrict__ x, int nrows, int k, int ld, int kpad, int prows,
-                                float *__restrict__ planes, double *__restrict__ scale) {
+// Slices of the rows of a real matrix X [nrows][ld], columns q < k, each times cscale[q]
+// when cscale is not null: plane s row r at planes[(s * prows + r) * pitch + q] for
+// q < kfill (zero past k); scale[r] = 2^e_r.  One block per row r < prows.
+__global__ void k_oz_split_rows(const double *__restrict__ x, int nrows, int k, int ld, const double *__restrict__ cscale,
+                                int kfill, int pitch, int prows, float *__restrict__ planes, double *__restrict__ scale) {
   __shared__ double red[32];
   const int r = blockIdx.x;
   double m = 0.0;
   if (r < nrows)
-    for (int q = threadIdx.x; q < k; q += blockDim.x) m = fmax(m, fabs(x[(size_t)r * ld + q]));
+    for (int q = threadIdx.x; q < k; q += blockDim.x)
+      m = fmax(m, fabs(x[(size_t)r * ld + q] * (cscale ? cscale[q] : 1.0)));
   const int e = row_exponent(block_max(m, red));
   if (threadIdx.x == 0) scale[r] = ldexp(1.0, e);
-  for (int q = threadIdx.x; q < kpad; q += blockDim.x) {
-    const double v = (r < nrows && q < k) ? ldexp(x[(size_t)r * ld + q], -e) : 0.0;
+  for (int q = threadIdx.x; q < kfill; q += blockDim.x) {
+    const double v = (r < nrows && q < k) ? ldexp(x[(size_t)r * ld + q] * (cscale ? cscale[q] : 1.0), -e) : 0.0;
     float d[S];
     slice(v, d);
 #pragma unroll
-    for (int s = 0; s < S; ++s) planes[((size_t)s * prows + r) * kpad + q] = d[s];
+    for (int s = 0; s < S; ++s) planes[((size_t)s * prows + r) * pitch + q] = d[s];
   }
 }
 
-// Slices of the stacked rows of S^T (complex [rows][npw]): complex row m gives stacked row
-// 128 (m / 64) + m % 64 (its real part) and that + 64 (its imaginary part), each with its
-// own scale.  One block per complex row m < prows / 2 (rows past `rows` are zero).
-__global__ void k_oz_split_stacked(const double2 *__restrict__ st, int rows, int npw, int kpad, int prows,
-                                   float *__restrict__ planes, double *__restrict__ scale) {
+// Slices of the stacked rows of a complex matrix X [rows][ld] (columns q < k): complex row
+// m gives stacked row 128 (m / 64) + m % 64 (its real part) and that + 64 (its imaginary
+// part), each with its own scale; plane s row r at planes[(s * prows + r) * pitch + q] for
+// q < kfill.  One block per complex row m < prows / 2 (rows past `rows` are zero).
+__global__ void k_oz_split_stacked(const double2 *__restrict__ x, int rows, int k, int ld, int kfill, int pitch,
+                                   int prows, float *__restrict__ planes, double *__restrict__ scale) {
   __shared__ double red[32];
   const int m = blockIdx.x;
   const size_t r1 = (size_t)128 * (m / 64) + (m % 64), r2 = r1 + 64;
   double mr = 0.0, mi = 0.0;
   if (m < rows)
-    for (int q = threadIdx.x; q < npw; q += blockDim.x) {
-      const double2 v = st[(size_t)m * npw + q];
+    for (int q = threadIdx.x; q < k; q += blockDim.x) {
+      const double2 v = x[(size_t)m * ld + q];
       mr = fmax(mr, fabs(v.x));
       mi = fmax(mi, fabs(v.y));
     }
@@ -106,16 +109,16 @@ __global__ void k_oz_split_stacked(const double2 *__restrict__ st, int rows, int
     scale[r1] = ldexp(1.0, er);
     scale[r2] = ldexp(1.0, ei);
   }
-  for (int q = threadIdx.x; q < kpad; q += blockDim.x) {
+  for (int q = threadIdx.x; q < kfill; q += blockDim.x) {
     double2 v = make_double2(0.0, 0.0);
-    if (m < rows && q < npw) v = st[(size_t)m * npw + q];
+    if (m < rows && q < k) v = x[(size_t)m * ld + q];
     float dr[S], di[S];
     slice(ldexp(v.x, -er), dr);
     slice(ldexp(v.y, -ei), di);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      planes[((size_t)s * prows + r1) * kpad + q] = dr[s];
-      planes[((size_t)s * prows + r2) * kpad + q] = di[s];
+      planes[((size_t)s * prows + r1) * pitch + q] = dr[s];
+      planes[((size_t)s * prows + r2) * pitch + q] = di[s];
     }
   }
 }

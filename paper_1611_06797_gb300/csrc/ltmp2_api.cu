@@ -294,8 +294,9 @@ template <typename T> int setup_precision(ltmp2_ctx *c, const ltmp2_system *sys,
   if (std::is_same<T, double>::value && p.real_basis && !(sys->flags & LTMP2_FLAG_SIMT_GEMM)) {
     // the transformed-state GEMM with FP64 accuracy on the tensor cores (exact integer slices)
     void *omem = nullptr;
-    if ((rc = dalloc_bytes(c, &omem, oz_bytes((int)max_cols, p.n_pw)))) return rc;
-    e = oz_init(c->oz, omem, (int)max_cols, p.n_pw);
+    if ((rc = dalloc_bytes(c, &omem, oz_bytes((int)max_cols, p.n_pw, p.n_v)))) return rc;
+    e = oz_init(c->oz, omem, (int)max_cols, p.n_pw, p.n_v);
+    if (e == cudaSuccess) e = oz_split_cv(c->oz, (const double *)p.cv, c->stream);   // R_v, once
     if (e != cudaSuccess) return cuda_status(e);
     p.oz = &c->oz;
   }

@@ -201,6 +201,15 @@ cudaError_t Path<T>::green(const Plan &p, double tau, cudaStream_t st, StageTime
   }
   const int M = p.n_pw, N = p.n_pw, K = p.nv_tau > 0 ? p.nv_tau : p.n_v;
   dim3 grid((N + 63) / 64, (M + 63) / 64);
+  if constexpr (std::is_same<T, double>::value) {
+    if (p.oz && p.rvt && oz_green_fits(*p.oz)) {
+      // FP64 on the tensor cores: P_r = (R_v'^T D') R_v', then its slices for the W product
+      if ((e = oz_green(*p.oz, (const double *)p.rvt, (const double *)p.dscale + p.n_occ, K, (double *)p.pt, st)) !=
+          cudaSuccess)
+        return e;
+      return oz_split_b(*p.oz, (const double *)p.pt, st);
+    }
+  }
   if (p.real_basis) {
     // P_r[q][p] = sum_a r_a(q) e^{-(e_a-mu)tau} r_a(p), r_a the real coordinates of a
     k_rgemm<T, T, false><<<grid, 256, 0, st>>>(M, N, K, (const T *)p.cv, p.n_pw, (const T *)p.cv, p.n_pw,
@@ -252,6 +261,16 @@ cudaError_t Path<T>::slab_pre(const Plan &p, int gp0, int np, cudaStream_t st, S
     } else if (p.w_virtual) {
       // X^T = (U S)^T R_v'^T [ncols][nv] in the z1 buffer (free until the z transform; it
       // holds n n_dorb >= n_pw > nv values per column), then W^T = X^T D' R_v'
+      if constexpr (std::is_same<T, double>::value) {
+        if (p.oz) {
+          if ((e = oz_virtual(*p.oz, p.st, ncols, (const double *)p.rvt, (const double *)p.dscale + p.n_occ, p.nv_tau,
+                              p.z1, p.wt, st)) != cudaSuccess)
+            return e;
+          done = true;
+        }
+      }
+    }
+    if (p.w_virtual && !done) {
       const int nv = p.nv_tau;
       dim3 gx((nv + 63) / 64, (ncols + 63) / 64);
       k_rgemm<T, cpx<T>, true><<<gx, 256, 0, st>>>(ncols, nv, p.n_pw, (const cpx<T> *)p.st, p.n_pw,

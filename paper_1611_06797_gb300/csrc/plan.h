@@ -159,14 +159,26 @@ struct Plan {
 // path's transformed-state GEMM in the real basis, W^T = (U S)^T P_r.
 struct OzResources {
   int rows_cap = 0, npw = 0, kpad = 0, arows = 0;  // complex rows, K = n_pw, padded K, stacked rows
+  int nv = 0;                                      // virtuals (rows of the static slices bv)
   float *a = nullptr, *b = nullptr;                // slices [8][arows][kpad], [8][npw][kpad]
-  double *sa = nullptr, *sb = nullptr;             // row scales (powers of two)
+  float *bv = nullptr;                             // slices of R_v [8][nv][kpad], once per context
+  double *sa = nullptr, *sb = nullptr, *sbv = nullptr;  // row scales (powers of two)
   int *err = nullptr;                              // device flag: a bounded wait ran out
-  void *maps = nullptr;                            // host copy of the two tensor maps
+  void *maps = nullptr;                            // host copy of the three tensor maps
 };
-size_t oz_bytes(int rows_cap, int npw);
-cudaError_t oz_init(OzResources &r, void *mem, int rows_cap, int npw);
+size_t oz_bytes(int rows_cap, int npw, int nv);
+cudaError_t oz_init(OzResources &r, void *mem, int rows_cap, int npw, int nv);
 void oz_release(OzResources &r);
+// slices of the virtuals' real coordinates R_v (cv [nv][npw]), once
+cudaError_t oz_split_cv(const OzResources &r, const double *cv, cudaStream_t st);
+// the Green's function P_r = R_v'^T D' R_v' over the first nv virtuals (dv: their weights)
+// into pr [npw][npw]; needs oz_green_fits (n_pw rows fit the A slices)
+bool oz_green_fits(const OzResources &r);
+cudaError_t oz_green(const OzResources &r, const double *rvt, const double *dv, int nv, double *pr, cudaStream_t st);
+// W^T through the virtual space: X^T = S^T R_v'^T into x (complex [rows][nv]), then
+// W^T = X^T D' R_v' into wt (complex [rows][npw])
+cudaError_t oz_virtual(const OzResources &r, const void *st_in, int rows, const double *rvt, const double *dv, int nv,
+                       void *x, void *wt, cudaStream_t st);
 // slices of P_r (real symmetric [npw][npw]) as the B operand, once per tau
 cudaError_t oz_split_b(const OzResources &r, const double *pr, cudaStream_t st);
 // W^T (complex [rows][npw]) = S^T (complex [rows][npw]) P_r
@@ -204,12 +216,17 @@ template <typename T> struct Path {
   // kernel launches per Green's function build and per slab (the tcgen05 path of the
   // precision form adds one operand-packing launch to each)
   static int green_launches(const Plan &p) {
-    return (p.route == 1 || p.w_virtual) ? 1 : (p.tc ? (p.tc->green_on() ? 4 : 3) : (p.oz ? 3 : 2));
+    if (p.route == 1 || p.w_virtual) return 1;
+    if (p.tc) return p.tc->green_on() ? 4 : 3;
+    if (p.oz) return oz_green_fits(*p.oz) && p.rvt ? 5 : 3;   // dscale, [split, split, product | product], split of P_r
+    return 2;
   }
   static int slab_launches(const Plan &p) {
     if (p.route == 1) return 7 + (p.n_lev > 1 ? 1 : 0);   // no gather, CUDA-core product
-    return (p.tc ? 8 : 7) + (p.real_basis ? 1 : 0) + (p.w_virtual ? 1 : 0) + (p.oz && !p.w_virtual ? 1 : 0) +
-           (p.n_lev > 1 ? 1 : 0) +
+    // W: one product; FP64 on the tensor cores: split + product; through the virtual space:
+    // two products (CUDA cores) or split, product, split, split, product (tensor cores)
+    const int w = p.w_virtual ? (p.oz ? 5 : 2) : (p.oz ? 2 : 1);
+    return (p.tc ? 8 : 7) - 1 + w + (p.real_basis ? 1 : 0) + (p.n_lev > 1 ? 1 : 0) +
            (p.tc && p.tc->direct_on() && p.n_lev < 2 ? 2 : 0);   // direct term: pack, product, combine
   }
   // route 1 setup: the overlap densities of every primary G' into rt (uses st and pt as
