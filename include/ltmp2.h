@@ -362,14 +362,15 @@ int ltmp2_energy_uhf(ltmp2_ctx *alpha, ltmp2_ctx *beta, int n_tau, const double 
 int ltmp2_set_route(ltmp2_ctx *ctx, int route);
 
 /* ---------------------------------------------------------------- FP64 products on the tensor cores
- * The FP64 path's transformed-state GEMM (step (iii) of Sec. III A in the real basis,
- * W^T = (U S)^T P_r) runs on the tcgen05 tensor cores with FP64 accuracy, unless
+ * The FP64 path's products in the real basis (the Green's function P_r, the transformed
+ * states W^T = (U S)^T P_r of step (iii), Sec. III A, and at large tau the two products
+ * through the kept virtuals) run on the tcgen05 tensor cores with FP64 accuracy, unless
  * LTMP2_FLAG_SIMT_GEMM is set: every row of both operands is scaled by a power of two and
  * cut into 8 slices of 7 bits (exact in TF32); the 36 slice products with s + t < 8 are
- * accumulated per order s + t in FP32 tensor memory, where sums of at most 256 k stay
- * below 2^24 and are therefore exact, and combined in FP64 registers.  The dropped orders
- * are below 2^-56 of the row products' magnitude; the result differs from an FP64 GEMM by
- * about its own rounding.
+ * accumulated per order s + t in FP32 tensor memory, where sums of at most 400 k stay
+ * below 2^24 and are therefore exact, and combined in FP64 registers.  A dropped term is
+ * at most 7 x 2^-56 of the product of the two rows' largest magnitudes; the result
+ * differs from an FP64 GEMM by about its own rounding.
  * ltmp2_dgemm_nt: C = A B^T with that scheme.  A [m][lda], B [n][ldb], C [m][ldc]: DEVICE
  * pointers to row-major doubles (first k columns of A and B used), lda, ldb >= k,
  * ldc >= n.  Allocates and frees its own slice buffers (about 32 (m + n) k bytes) and

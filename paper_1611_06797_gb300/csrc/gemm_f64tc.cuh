@@ -6,13 +6,14 @@
 //       a = 2^e_a sum_s d_s 2^{-7(s+1)},  d_s integers, |d_0| <= 128, |d_s| <= 64 (s >= 1),
 //   every slice exactly representable in TF32.  Then
 //       (A B^T)_ij = 2^{e_i + f_j} sum_{d=0}^{S-1} 2^{-7(d+2)} sum_{s+t=d} sum_k a_{s,ik} b_{t,jk}
-//   with the pairs s + t >= S left out (their terms are below 2^{-7S} = 2^{-56} of the
-//   row products' magnitude, under the rounding of an FP64 product).  Each inner sum is a
-//   sum of integer products; over 256 k (16 k blocks) it stays below 2^24 in magnitude
-//   (at most 2.75 x 2^14 per k for one order d), so the tensor core's FP32 accumulation
-//   is exact there, whatever its rounding.  The accumulators of the 8 orders d live in
-//   tensor memory (8 x 64 columns = all 512) and are drained every 16 k blocks into FP64
-//   register sums, scaled by 2^{-7(d+2)}.  The result carries the FP64 rounding of those
+//   with the pairs s + t >= S left out (per term at most 7 x 2^12 x 2^-70 x 2^{e_a + e_b}
+//   <= 7 x 2^-56 max|a| max|b|, at the rounding of an FP64 product).  Each inner sum is a
+//   sum of integer products; over 400 k (25 k blocks) it stays below 2^24 in magnitude (at
+//   most 2 x 128 x 64 + 6 x 64 x 64 = 2.5 x 2^14 per k for one order d), so every partial
+//   sum is an integer that FP32 holds exactly and the tensor core's accumulation is exact,
+//   whatever its rounding.  The accumulators of the 8 orders d live in tensor memory
+//   (8 x 64 columns = all 512) and are drained every 25 k blocks into FP64 register sums,
+//   scaled by 2^{-7(d+2)}.  The result carries the FP64 rounding of those
 //   sums and of the slicing, about the error of an FP64 dot product.
 #pragma once
 #include <cuda.h>
@@ -35,7 +36,7 @@ constexpr int STAGE = S * (A_TILE + B_TILE); // 96 KB
 constexpr int STAGES = 2;
 constexpr int SMEM = STAGES * STAGE + 1024;  // + alignment slack
 constexpr int TMEM_COLS = S * BN;            // one accumulator per slice order d = s + t
-constexpr int DRAIN_KB = 16;                 // k blocks between drains (256 k)
+constexpr int DRAIN_KB = 25;                 // k blocks between drains (400 k: sums below 2^24)
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
@@ -225,20 +226,21 @@ __global__ void __launch_bounds__(160, 1)
 #pragma unroll
       for (int d = 0; d < S; ++d) {
         const double scale = ldexp(1.0, -BITS * (d + 2));
+        // the order's 64 columns in flight together, one wait
+        uint32_t rr[BN];
 #pragma unroll
-        for (int c = 0; c < BN / 16; ++c) {
-          uint32_t rr[16];
+        for (int c = 0; c < BN / 16; ++c)
           asm volatile(
               "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
               "%14, %15}, [%16];"
-              : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
-                "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]),
-                "=r"(rr[14]), "=r"(rr[15])
+              : "=r"(rr[c * 16 + 0]), "=r"(rr[c * 16 + 1]), "=r"(rr[c * 16 + 2]), "=r"(rr[c * 16 + 3]),
+                "=r"(rr[c * 16 + 4]), "=r"(rr[c * 16 + 5]), "=r"(rr[c * 16 + 6]), "=r"(rr[c * 16 + 7]),
+                "=r"(rr[c * 16 + 8]), "=r"(rr[c * 16 + 9]), "=r"(rr[c * 16 + 10]), "=r"(rr[c * 16 + 11]),
+                "=r"(rr[c * 16 + 12]), "=r"(rr[c * 16 + 13]), "=r"(rr[c * 16 + 14]), "=r"(rr[c * 16 + 15])
               : "r"(t_lane + (uint32_t)(d * BN + c * 16)));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int j = 0; j < 16; ++j) sum[c * 16 + j] = fma((double)__uint_as_float(rr[j]), scale, sum[c * 16 + j]);
-        }
+        for (int j = 0; j < BN; ++j) sum[j] = fma((double)__uint_as_float(rr[j]), scale, sum[j]);
       }
       fence_before();
       mbar_arrive(&acce_bar);
