@@ -58,27 +58,37 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def source_sha():
+# Source files that define each stage's kernel, its launch configuration and the data it
+# reads: a stored DRAM measurement holds only while these are unchanged.
+STAGE_SOURCES = {
+    "plane_fft": ["kernels.cuh", "fft.cuh", "plan.h", "path_impl.cuh"],
+    "column_fft_contract": ["kernels.cuh", "fft.cuh", "plan.h", "path_impl.cuh"],
+    "w_gemm": ["kernels.cuh", "plan.h", "path_impl.cuh", "tcgen05.cuh", "gemm_tc.cuh", "gemm_tc.cu",
+               "gemm_f64tc.cuh", "gemm_f64tc.cu"],
+}
+
+
+def source_sha(stage: str) -> str:
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1611_06797_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
-            h.update(os.path.basename(f).encode())
+    for name in sorted(STAGE_SOURCES[stage]):
+        with open(os.path.join(ROOT, "paper_1611_06797_gb300", "csrc", name), "rb") as fh:
+            h.update(name.encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def traffic_for(stage: str, precision: int):
     """DRAM bytes per launch of the stage's kernel from the committed ncu summary, if it was
-    taken from the current kernel sources; else None."""
+    taken from the current sources of that kernel; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or stage not in STAGE_SOURCES:
         return None
     with open(path) as f:
         d = json.load(f)
-    if d.get("source_sha") != source_sha():
-        return None
     e = d.get("fp64" if precision == 0 else "fp32", {}).get(stage)
-    return e.get("dram_bytes_per_launch") if e else None
+    if not e or e.get("source_sha") != source_sha(stage):
+        return None
+    return e.get("dram_bytes_per_launch")
 
 
 # ------------------------------------------------------------------ clocks
