@@ -675,7 +675,7 @@ def run_learned(args, local):
     the exact exchange pair energies (ln|e^x_ij| labels from ltmp2_learned_training_data) of
     the 12^3 and 24^3 systems, the 8 batching systems and the 36^3 system; ltmp2_energy_screened
     then screens the cfg5 pairs for a budget of 0.1 meV/atom.  The all-pairs contraction of
-    the same inputs is timed beside it and judges the realised error."""
+    the same inputs is timed beside it and measures the realised error."""
     import numpy as np
     import torch
     import paper_1611_06797_gb300 as L
@@ -725,7 +725,7 @@ def run_learned(args, local):
     X = L.ltmp2_pair_descriptors(c).astype(np.float32)
     keep, n_sel, _ = L.ltmp2_screen_select(s.n_occ, margin * np.exp(net.predict(X).astype(np.float64)), budget)
     with ClockSampler(local) as clk:
-        # all pairs, with the exact exchange of every pair (the judge, and the ceiling below)
+        # all pairs, with the exact exchange of every pair (the reference for the realised error, and the ceiling below)
         (ed, ex, pd, px), ms_all = timed(lambda: L.ltmp2_energy_partial(c, tau, w, 0, n_prim))
         if n_sel > 0:
             r, ms_scr = timed(lambda: L.ltmp2_energy_screened(c, net, tau, w, budget, margin))

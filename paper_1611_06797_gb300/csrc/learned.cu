@@ -6,7 +6,7 @@
 // trained on labels that the exact contraction produces (ltmp2_learned_training_data).
 // Pairs are screened in ascending order of a calibrated upper bound (the estimate times a
 // margin that the caller validates on held-out systems) while the screened sum stays within
-// the caller's budget; the all-pairs contraction remains the judge of the realised error.  Everything
+// the caller's budget; the all-pairs contraction remains the reference for the realised error.  Everything
 // here runs through this library's own C entry points.
 #include <cuda_runtime.h>
 

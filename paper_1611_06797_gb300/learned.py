@@ -6,7 +6,7 @@ descriptors and the exact ln|e^x_ij| labels of each system), trains the model (`
 calibrates the screening margin by leave-one-system-out validation: for each training system
 a model trained on the others predicts it, and the margin is the largest ratio |e^x| / estimate
 among the lowest predictions of any held-out system (the pairs a screening would take), times
-a safety factor.  The all-pairs contraction stays the judge of the realised error.
+a safety factor.  The all-pairs contraction stays the reference for the realised error.
 """
 from __future__ import annotations
 

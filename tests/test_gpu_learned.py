@@ -8,7 +8,7 @@
 * The learned form through the C ABI (ltmp2_energy_screened), with the model trained on
   the exact labels of smaller systems (ltmp2_learned_training_data), screens pairs of a
   system it was not trained on and stays within the 0.1 meV/atom budget of the all-pairs
-  contraction, which judges it; with a zero budget it is the all-pairs contraction.
+  contraction, which measures it; with a zero budget it is the all-pairs contraction.
 """
 import numpy as np
 import pytest
@@ -96,7 +96,7 @@ def test_learned_screening_within_budget_on_unseen_system():
     c = L.setup_from_solid(s, precision=L.FP32, real=True)
     ed, ex, _ = L.ltmp2_energy(c, tau, w, pairs=False)
     budget = 0.1 * MEV * s.n_atoms
-    # the 0.1 meV/atom budget and larger ones: the realised error, judged by the all-pairs
+    # the 0.1 meV/atom budget and larger ones: the realised error, measured by the all-pairs
     # contraction, stays within each budget; the largest certainly screens pairs
     for b in (budget, 10 * budget, 100 * budget):
         r = LF.screened_vs_exact(c, net, tau, w, b, margin, e_all=(ed, ex))
