@@ -190,17 +190,18 @@ __global__ void __launch_bounds__(160, 1)
         // the accumulators are free once the previous window has been drained
         if (first && win >= 1 && !mbar_wait(&acce_bar, (uint32_t)((win - 1) & 1))) { ok = false; break; }
         fence_after();
-        const uint32_t base = smem_u32(smem + st * STAGE);
-        for (int s = 0; s < S; ++s)
-          for (int t = 0; s + t < S; ++t) {
-            const uint32_t d = tmem + (uint32_t)((s + t) * BN);
+        // one descriptor per stage; a tile's descriptor adds its byte offset / 16 (the stage
+        // lies below 256 KB of shared memory, so the 14-bit address field cannot overflow)
+        const uint64_t d0 = sdesc_sw64(smem_u32(smem + st * STAGE));
 #pragma unroll
-            for (int k8 = 0; k8 < BK / 8; ++k8) {
-              const uint64_t ad = sdesc_sw64(base + s * A_TILE + k8 * 32);
-              const uint64_t bd = sdesc_sw64(base + S * A_TILE + t * B_TILE + k8 * 32);
-              mma_tf32(d, ad, bd, IDESC, (first && s == 0 && k8 == 0) ? 0u : 1u);
-            }
-          }
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+          for (int t = 0; t < S - s; ++t)
+#pragma unroll
+            for (int k8 = 0; k8 < BK / 8; ++k8)
+              mma_tf32(tmem + (uint32_t)((s + t) * BN), d0 + (uint64_t)((s * A_TILE + k8 * 32) >> 4),
+                       d0 + (uint64_t)((S * A_TILE + t * B_TILE + k8 * 32) >> 4), IDESC,
+                       (first && s == 0 && k8 == 0) ? 0u : 1u);
         mma_commit(&empty_bar[st]);
         if (kb % DRAIN_KB == DRAIN_KB - 1 || kb == kblocks - 1) mma_commit(&accf_bar);
         // refill the stage of k block kb - 1 once its MMAs are done (those of kb are queued)
