@@ -191,8 +191,9 @@ int ltmp2_autotune(ltmp2_ctx *ctx, int *slab, int *gemm_variant);
 /* Settings in effect for ctx: values[0] slab size, [1] tensor-core GEMM layout (-1 in
  * FP64 or with LTMP2_FLAG_SIMT_GEMM), [2] plane FFT kernel (0 full-plane passes,
  * 1 compacted passes, 2 product in registers with a compact intermediate, 3 the same with
- * every warp on its own occupied planes and no block barriers), [3] occupied planes per
- * plane-kernel block, for kernel 3 per warp step (0 = default), [4] the precision form's
+ * every warp on its own occupied planes and no block barriers; set-up chooses 3 in
+ * LTMP2_FP32 and 2 in LTMP2_FP64), [3] occupied planes per plane-kernel block, for
+ * kernel 3 per warp step (0 = default), [4] the precision form's
  * Green's function on the tensor cores (1; 3xTF32, set up at first use) or on the CUDA
  * cores with compensated sums (0, the default: the tensor-core build's plain FP32 sums
  * over K = n_v left 4x the error in E_d on the 36^3 workload), [5] its direct-term

@@ -517,7 +517,7 @@ struct TuneVal {
 };
 std::map<TuneKey, TuneVal> g_tune_cache;
 
-int apply_tuning(ltmp2_ctx *c, int slab, int variant, int plane_kernel = 2, int plane_ib = 0) {
+int apply_tuning(ltmp2_ctx *c, int slab, int variant, int plane_kernel, int plane_ib) {
   if (slab < 1 || slab > c->slab_capacity) return LTMP2_ERR_INVALID_ARG;
   c->p.max_prim = slab;
   c->p.plane_kernel = plane_kernel;
@@ -554,7 +554,7 @@ template <typename T> int tune_ctx(ltmp2_ctx *c, int *slab_out, int *var_out) {
   int best_slab = slabs.front(), best_var = variants.front();
   int rc = LTMP2_OK;
   for (int v : variants) {
-    if ((rc = apply_tuning(c, slabs.front(), v))) break;
+    if ((rc = apply_tuning(c, slabs.front(), v, p.plane_kernel, p.plane_ib))) break;
     if (Path<T>::green(p, 1.0, c->stream, nullptr) != cudaSuccess) { rc = LTMP2_ERR_CUDA; break; }
     for (int sl : slabs) {
       p.max_prim = sl;
@@ -575,7 +575,7 @@ template <typename T> int tune_ctx(ltmp2_ctx *c, int *slab_out, int *var_out) {
   }
   // plane kernel and its block size, timed alone on the columns of one warm slab
   int best_pk = 0, best_ib = 0;
-  if (!rc) rc = apply_tuning(c, best_slab, best_var);
+  if (!rc) rc = apply_tuning(c, best_slab, best_var, p.plane_kernel, p.plane_ib);
   if (!rc && Path<T>::slab(p, 0, best_slab, 0.0, c->stream, nullptr) != cudaSuccess) rc = LTMP2_ERR_CUDA;
   if (!rc) {
     const int ncols = best_slab * p.slots_per_prim() * p.n_occ;
@@ -888,6 +888,9 @@ int ltmp2_setup(const ltmp2_system *sys, ltmp2_ctx **out) {
   }
   Plan &p = c->p;
   p = hp.p;
+  // plane kernel: FP32, the warp-autonomous one (fastest on the 24^3 and 36^3 workloads);
+  // FP64, the block-synchronous one (FP64-issue bound either way, and 17 % faster)
+  p.plane_kernel = sys->precision == LTMP2_FP32 ? 3 : 2;
   std::memcpy(c->lattice, sys->lattice, sizeof(c->lattice));
   c->ecut_aux = hp.ecut_aux;
   c->aux_g2 = hp.aux_g2;

@@ -20,10 +20,13 @@ template <typename T> static int plane_ib_default(const Plan &p, int kernel) {
   const int nxa = p.mxhi_aux - p.mxlo_aux + 1;
   int ib;
   if (kernel == 3) {
-    // as many planes per warp step as fill the 32 lanes of the x pass, within ~48 KB
+    // as many planes per warp step as fill the 32 lanes of the x pass, at least 2 (two
+    // planes per warp step were fastest in FP32 on the 24^3 and 36^3 workloads: 20.6 and
+    // 790 ms per plane pass against 23.5 and 905 with one), within ~100 KB
     ib = (32 + n - 1) / n;
-    const size_t per = (size_t)kPlaneWarps * n * nxa * sizeof(cpx<T>);
-    while (ib > 1 && plane + ib * per > 48 * 1024) --ib;
+    if (ib < 2) ib = 2;
+    const size_t per = (size_t)kPlaneWarps * plane_stride(n, nxa) * sizeof(cpx<T>);
+    while (ib > 1 && plane + ib * per > 100 * 1024) --ib;
   } else if (kernel == 0) {
     ib = (int)((96 * 1024) / plane) - 1;   // about 96 KB of shared memory
     if (ib > 8) ib = 8;

@@ -108,7 +108,8 @@ struct Plan {
   int max_prim = 0;          // primary G' per slab (capacity)
   TcResources *tc = nullptr; // precision form: tcgen05 GEMM resources (host pointer), or null
   OzResources *oz = nullptr; // FP64 path: tensor-core FP64 GEMM resources (host pointer), or null
-  int plane_kernel = 2;      // 0: k_planes, 1: k_planes2, 2: k_planes3 (the autotuner may change it)
+  int plane_kernel = 2;      // 0: k_planes, 1: k_planes2, 2: k_planes3, 3: k_planes4 (set-up: 3 in FP32;
+                             // the autotuner may change it)
   // screened exchange pairs (learned form); all null = every pair contracted
   const unsigned char *pair_keep = nullptr;  // [n_occ][n_occ] 1 = contract, symmetric, diagonal kept
   const int *keep_list = nullptr;            // [n_occ][n_occ] kept i for each j (first keep_count[j])
