@@ -261,3 +261,21 @@ def test_screen_select_rule():
         e = est.copy(); e[3] = bad
         with pytest.raises(L.Ltmp2Error):
             L.ltmp2_screen_select(n, e, 1.0)
+
+
+def test_dgemm_rejects_bad_arguments_on_the_host():
+    """ltmp2_dgemm_nt checks sizes, leading dimensions and pointers before any device work."""
+    import ctypes
+    lib = L.load_library()
+    f = lib.ltmp2_dgemm_nt
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                  ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+    p = ctypes.c_void_p(16)     # never dereferenced: every call below fails its argument checks
+    assert f(0, 4, 4, p, 4, p, 4, p, 4) == -1       # m < 1
+    assert f(4, 0, 4, p, 4, p, 4, p, 4) == -1       # n < 1
+    assert f(4, 4, 0, p, 4, p, 4, p, 4) == -1       # k < 1
+    assert f(4, 4, 8, p, 4, p, 8, p, 4) == -1       # lda < k
+    assert f(4, 4, 8, p, 8, p, 4, p, 4) == -1       # ldb < k
+    assert f(4, 4, 8, p, 8, p, 8, p, 3) == -1       # ldc < n
+    assert f(4, 4, 8, None, 8, p, 8, p, 4) == -1    # null pointer
