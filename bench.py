@@ -248,29 +248,51 @@ def measured_alu(L):
             "kind": "measured in this run: independent FMA chains over a full grid, CUDA events, best of 5"}
 
 
+def _stage_bound(stage, st, costs, precision, simt, peaks, peak_kind, alu):
+    """achieved = algorithmic work per launch / mean launch time (CUDA events around each
+    launch on the library's stream), against the rate that bounds the stage."""
+    per_launch_ms = st[stage]["ms"] / st[stage]["launches"]
+    out = {"avg_launch_ms": per_launch_ms}
+    if stage in costs:
+        work = costs[stage]["flops"] / st[stage]["launches"]
+        if not simt and (stage == "w_gemm" or (stage == "green_gemm" and precision == 0)):
+            # tensor products per real product: 3xTF32 in the precision form; in the FP64 path
+            # the 36 slice products (orders s + t < 8 of 8 x 7-bit slices per operand)
+            work *= 3.0 if precision != 0 else 36.0
+            peak = peaks["bf16_tflops"] * TF32_OVER_BF16
+            bound, pk = "tensor", f"tf32 = {peak_kind} bf16 {peaks['bf16_tflops']} x nominal 1.1/2.25"
+        elif precision == 0:
+            peak, bound, pk = alu["fp64"], "alu", "FP64 FMA rate " + alu["kind"]
+        else:
+            peak, bound, pk = alu["fp32"], "alu", "FP32 FMA rate " + alu["kind"]
+        achieved = work / (per_launch_ms / 1e3) / 1e12
+        out.update({"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_kind": pk, "work_per_launch": work})
+    traffic = traffic_for(stage, precision)
+    if traffic:
+        # DRAM bytes of a full launch (the stored capture) over the mean launch time: the
+        # last slab of each tau is smaller, so this slightly overstates the rate
+        gbs = traffic / (per_launch_ms / 1e3) / 1e9
+        out.update({"dram_bytes_per_launch": traffic, "dram_gbs": gbs, "dram_frac": gbs / peaks["hbm_gbs"]})
+    return out
+
+
 def roofline_of(st, costs, precision, simt, peaks, peak_kind, alu):
-    """Dominant stage against its bound: achieved = algorithmic work per launch / mean
-    launch time (CUDA events around each launch on the library's stream)."""
+    """Dominant stage against its bound."""
     dom = max(st, key=lambda k: st[k]["ms"])
     if dom not in costs or st[dom]["launches"] == 0:
         return {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": traffic_for(dom, precision)}
-    per_launch_ms = st[dom]["ms"] / st[dom]["launches"]
-    work = costs[dom]["flops"] / st[dom]["launches"]
-    if not simt and (dom == "w_gemm" or (dom == "green_gemm" and precision == 0)):
-        # tensor products per real product: 3xTF32 in the precision form; in the FP64 path the
-        # 36 slice products (orders s + t < 8 of 8 x 7-bit slices per operand)
-        work *= 3.0 if precision != 0 else 36.0
-        peak = peaks["bf16_tflops"] * TF32_OVER_BF16
-        bound, pk = "tensor", f"tf32 = {peak_kind} bf16 {peaks['bf16_tflops']} x nominal 1.1/2.25"
-    elif precision == 0:
-        peak, bound, pk = alu["fp64"], "alu", "FP64 FMA rate " + alu["kind"]
-    else:
-        peak, bound, pk = alu["fp32"], "alu", "FP32 FMA rate " + alu["kind"]
-    achieved = work / (per_launch_ms / 1e3) / 1e12
-    return {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "peak_kind": pk, "traffic": traffic_for(dom, precision),
-            "work_per_launch": work, "avg_launch_ms": per_launch_ms}
+    r = _stage_bound(dom, st, costs, precision, simt, peaks, peak_kind, alu)
+    return {"kernel": dom, "bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"], "unit": "TFLOP/s",
+            "frac": r["frac"], "peak_kind": r["peak_kind"], "traffic": traffic_for(dom, precision),
+            "work_per_launch": r["work_per_launch"], "avg_launch_ms": r["avg_launch_ms"]}
+
+
+def stage_rooflines(st, costs, precision, simt, peaks, peak_kind, alu):
+    """Every timed stage against its bound, and the DRAM rate where its bytes are stored."""
+    return {k: _stage_bound(k, st, costs, precision, simt, peaks, peak_kind, alu)
+            for k in st if st[k]["launches"] > 0 and st[k]["ms"] > 0}
 
 
 def main():
@@ -448,7 +470,8 @@ def main():
             n_prim = e0 - b0
         costs = stage_costs(r["sizes"], n_prim, True, args.steps, aux_nxa(spec), r["nv_tau"], r["w_virtual"],
                             s.n_orb - s.n_occ, r["green_full"])
-        return roofline_of(r["stages"], costs, precision, simt, peaks, peak_kind, alu)
+        return (roofline_of(r["stages"], costs, precision, simt, peaks, peak_kind, alu),
+                stage_rooflines(r["stages"], costs, precision, simt, peaks, peak_kind, alu))
 
     primary = L.FP64 if args.form == "fp64" else L.FP32
     r = time_form(primary)
@@ -462,7 +485,7 @@ def main():
     sizes = r["sizes"]
 
     st = r["stages"]
-    roof = roofline(r, primary, False)
+    roof, stage_roofs = roofline(r, primary, False)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -482,6 +505,7 @@ def main():
                                    "FP64 sum all-reduce per E_MP2" if world > 1 else "one GPU")},
         "energy": {"E_d": ed, "E_x": ex, "E": ed + ex, "meV_per_atom": (ed + ex) * HARTREE_TO_MEV / s.n_atoms},
         "roofline": roof,
+        "stage_rooflines": stage_roofs,
         "stages": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] // args.steps}
                    for k, v in st.items()},
         "clocks": r["clocks"],
@@ -509,12 +533,14 @@ def main():
                "E_x": abs(d32[1] - d64[1]) * HARTREE_TO_MEV / s.n_atoms,
                "E": abs(sum(d32) - sum(d64)) * HARTREE_TO_MEV / s.n_atoms}
         so = ro["stages"]
+        ro_roof, ro_stages = roofline(ro, other, False)
         out["forms"] = {("fp32" if other == L.FP32 else "fp64"): {
             "value": pairs * n_tau / (ms_o / 1e3), "s_per_E_MP2": ms_o / 1e3,
             "speedup_vs_fp64": (ms_step / ms_o) if other == L.FP32 else (ms_o / ms_step),
             "err_vs_fp64_meV_per_atom": err, "within_0.1_meV_per_atom": max(err.values()) <= 0.1,
-            "gemm": "tcgen05 3xTF32" if other == L.FP32 else "SIMT FP64",
-            "roofline": roofline(ro, other, False),
+            "gemm": "tcgen05 3xTF32" if other == L.FP32 else "tcgen05, FP64-accurate exact slices",
+            "roofline": ro_roof,
+            "stage_rooflines": ro_stages,
             "stages": {k: {"ms_per_step": v["ms"] / args.steps} for k, v in so.items()},
             "gpu_launches": ro["launches"]}}
         if other == L.FP32:
@@ -824,6 +850,7 @@ def form_cfg3(L, torch, local, steps, warmup, alu=None):
     costs = stage_costs(sizes, n_prim, True, steps, aux_nxa(spec), nv_tau, w_virtual, s.n_orb - s.n_occ,
                         tuning["green_tc"] == 1)
     roof = roofline_of(st, costs, L.FP32, False, peaks, peak_kind, alu)
+    stage_roofs = stage_rooflines(st, costs, L.FP32, False, peaks, peak_kind, alu)
     # FP32 vs FP64 on the same inputs, over sampled G' ranges
     width = 6
     starts = [0, n_prim // 3, (2 * n_prim) // 3, n_prim - width]
@@ -857,6 +884,7 @@ def form_cfg3(L, torch, local, steps, warmup, alu=None):
                    "laplace_max_rel_err": qerr, "tuning": tuning},
         "energy": {"E_d": ed, "E_x": ex, "E": ed + ex, "meV_per_atom": (ed + ex) * per_atom},
         "roofline": roof,
+        "stage_rooflines": stage_roofs,
         "stages": {k: {"ms_per_step": v["ms"] / steps, "launches_per_step": v["launches"] // steps}
                    for k, v in st.items()},
         "clocks": clk.summary(), "gpu_launches": launches, "peaks_source": peak_kind,
