@@ -74,8 +74,10 @@ extern "C" {
  * Sec. II D, at k = 0).  Then w_j^{(-G')} = conj(w_j^{(G')}) in real space and only
  * half of the G' set is transformed; the library checks the property in setup.  */
 #define LTMP2_FLAG_REAL_ORBITALS 1
-/* Precision form only: run the transformed-state GEMM on the CUDA cores (FP32, two-level
- * summation) instead of the tcgen05 3xTF32 tensor-core kernel.  For comparisons.   */
+/* Run the dense products on the CUDA cores instead of the tcgen05 tensor cores: in
+ * LTMP2_FP32 the transformed-state GEMM in FP32 with two-level summation instead of the
+ * 3xTF32 kernel; in LTMP2_FP64 the Green's function and transformed-state GEMMs in FP64
+ * instead of the exact-slice products (see ltmp2_dgemm_nt).  For comparisons.       */
 #define LTMP2_FLAG_SIMT_GEMM 2
 
 typedef struct ltmp2_ctx ltmp2_ctx; /* opaque; owns all device memory of one system */
